@@ -1,0 +1,333 @@
+/*
+ * ew_oracle.c -- plain, slow, FP64 CPU oracle for the EigenWave filter operator.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library path may link or call this
+ * file; only the tests, the smoke check and the CPU-baseline leg of the bench
+ * use it.  It shares no code, header or table with the CUDA library.
+ *
+ * Everything here is written for a reader checking it against the paper
+ * (Appelo, Banks, Henshaw, Le, Schwendeman, "EigenWave", arXiv 2507.18282):
+ *   - grid functions live on a Cartesian box with homogeneous Dirichlet
+ *     conditions (eq. eigBVPdiscrete), vectors hold the active (interior)
+ *     points only, x fastest (Algorithm "matVec", Note 1);
+ *   - L_h is the 2nd-order (5/7-point) or 4th-order (9/13-point wide cross)
+ *     centred Laplacian.  The 4th-order boundary closure (the paper leaves the
+ *     compatibility conditions out) is the odd reflection u_{-j} = -u_{j}
+ *     about the boundary point, which is u = 0 and u_xx = 0 on the wall;
+ *   - the explicit scheme is eq. explicitScheme with the first step
+ *     eq. explicitStep1, the implicit one eq. implicitScheme with
+ *     M = I - (dt^2/2) L_h (eq. impMatrix) and first step eq. implicitStep1;
+ *   - the filter is the trapezoidal sum eq. filterQuadrature; the caller
+ *     passes the weights c_n = (2/T_f) sigma_n (cos(omega t^n) - alpha_d/2).
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so the
+ * rounding order is the order written below).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OG_G 2 /* ghost layers kept around the interior (enough for order 4) */
+
+typedef struct {
+    int dim;        /* 2 or 3 */
+    long n[3];      /* interior points per axis (n[2] = 1 in 2D) */
+    double h[3];    /* grid spacing per axis */
+    int order;      /* 2 or 4 */
+    long p[3];      /* padded extents */
+    long npad;      /* padded size */
+    long nact;      /* active size */
+} og_grid;
+
+static int og_init(og_grid* g, int dim, const long* n, const double* h, int order) {
+    if (dim != 2 && dim != 3) return -1;
+    if (order != 2 && order != 4) return -1;
+    g->dim = dim;
+    g->order = order;
+    g->npad = 1;
+    g->nact = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (a < dim) {
+            if (n[a] < 1) return -1;
+            g->n[a] = n[a];
+            g->h[a] = h[a];
+            g->p[a] = n[a] + 2 * OG_G;
+        } else {
+            g->n[a] = 1;
+            g->h[a] = 1.0;
+            g->p[a] = 1;
+        }
+        g->npad *= g->p[a];
+        g->nact *= g->n[a];
+    }
+    return 0;
+}
+
+/* padded index of interior point (i, j, k), 0-based interior coordinates;
+ * i = -1 and i = n are boundary points, i = -2 and i = n+1 ghosts. */
+static long og_at(const og_grid* g, long i, long j, long k) {
+    long gi = i + OG_G;
+    long gj = j + OG_G;
+    long gk = (g->dim == 3) ? k + OG_G : 0;
+    return (gk * g->p[1] + gj) * g->p[0] + gi;
+}
+
+/* copy the active vector into the padded grid function and fill the inactive
+ * points from the boundary conditions (Algorithm matVec: vector -> grid, then
+ * applyBoundaryConditions). */
+static void og_scatter(const og_grid* g, const double* v, double* U) {
+    memset(U, 0, sizeof(double) * (size_t)g->npad);
+    long m = 0;
+    for (long k = 0; k < g->n[2]; ++k)
+        for (long j = 0; j < g->n[1]; ++j)
+            for (long i = 0; i < g->n[0]; ++i) U[og_at(g, i, j, k)] = v[m++];
+}
+
+/* Dirichlet: boundary points are zero, ghosts are the odd reflection of the
+ * first interior points (only the 4th-order stencil reads them). */
+static void og_fill_bc(const og_grid* g, double* U) {
+    long n0 = g->n[0], n1 = g->n[1], n2 = g->n[2];
+    for (long k = 0; k < n2; ++k)
+        for (long j = 0; j < n1; ++j) {
+            U[og_at(g, -1, j, k)] = 0.0;
+            U[og_at(g, n0, j, k)] = 0.0;
+            U[og_at(g, -2, j, k)] = -U[og_at(g, 0, j, k)];
+            U[og_at(g, n0 + 1, j, k)] = -U[og_at(g, n0 - 1, j, k)];
+        }
+    for (long k = 0; k < n2; ++k)
+        for (long i = 0; i < n0; ++i) {
+            U[og_at(g, i, -1, k)] = 0.0;
+            U[og_at(g, i, n1, k)] = 0.0;
+            U[og_at(g, i, -2, k)] = -U[og_at(g, i, 0, k)];
+            U[og_at(g, i, n1 + 1, k)] = -U[og_at(g, i, n1 - 1, k)];
+        }
+    if (g->dim == 3)
+        for (long j = 0; j < n1; ++j)
+            for (long i = 0; i < n0; ++i) {
+                U[og_at(g, i, j, -1)] = 0.0;
+                U[og_at(g, i, j, n2)] = 0.0;
+                U[og_at(g, i, j, -2)] = -U[og_at(g, i, j, 0)];
+                U[og_at(g, i, j, n2 + 1)] = -U[og_at(g, i, j, n2 - 1)];
+            }
+}
+
+/* L_h at one interior point of a padded grid function whose inactive points
+ * are filled. */
+static double og_lap_point(const og_grid* g, const double* U, long i, long j, long k) {
+    long c = og_at(g, i, j, k);
+    long stride[3];
+    stride[0] = 1;
+    stride[1] = g->p[0];
+    stride[2] = g->p[0] * g->p[1];
+    double sum = 0.0;
+    for (int a = 0; a < g->dim; ++a) {
+        long s = stride[a];
+        double h2 = g->h[a] * g->h[a];
+        double d2;
+        if (g->order == 2) {
+            d2 = (U[c - s] - 2.0 * U[c] + U[c + s]) / h2;
+        } else {
+            d2 = (-U[c - 2 * s] + 16.0 * U[c - s] - 30.0 * U[c] + 16.0 * U[c + s] - U[c + 2 * s]) /
+                 (12.0 * h2);
+        }
+        sum += d2;
+    }
+    return sum;
+}
+
+/* Lu = L_h u on active vectors. */
+int og_apply_L(int dim, const long* n, const double* h, int order, const double* u, double* Lu) {
+    og_grid g;
+    if (og_init(&g, dim, n, h, order)) return -1;
+    double* U = (double*)malloc(sizeof(double) * (size_t)g.npad);
+    if (!U) return -2;
+    og_scatter(&g, u, U);
+    og_fill_bc(&g, U);
+    long m = 0;
+    for (long k = 0; k < g.n[2]; ++k)
+        for (long j = 0; j < g.n[1]; ++j)
+            for (long i = 0; i < g.n[0]; ++i) Lu[m++] = og_lap_point(&g, U, i, j, k);
+    free(U);
+    return 0;
+}
+
+/* One application of the discrete EigenWave operator with explicit
+ * leapfrog time stepping:
+ *   W^0 = V,  W^1 = V + (dt^2/2) L_h V                       (eq. explicitStep1)
+ *   W^{n+1} = 2 W^n - W^{n-1} + dt^2 L_h W^n,  n = 1..Nt-1   (eq. explicitScheme)
+ *   out = sum_{n=0}^{Nt} c_n W^n                             (eq. filterQuadrature)
+ * Arrays hold active points; c has Nt+1 entries. */
+int og_filter_explicit(int dim, const long* n, const double* h, int order, long Nt, double dt,
+                       const double* c, const double* v, double* out) {
+    og_grid g;
+    if (og_init(&g, dim, n, h, order) || Nt < 1) return -1;
+    size_t bytes = sizeof(double) * (size_t)g.npad;
+    double* Wm = (double*)malloc(bytes); /* W^{n-1} */
+    double* W0 = (double*)malloc(bytes); /* W^n     */
+    double* Wp = (double*)malloc(bytes); /* W^{n+1} */
+    if (!Wm || !W0 || !Wp) {
+        free(Wm);
+        free(W0);
+        free(Wp);
+        return -2;
+    }
+    double dt2 = dt * dt;
+    og_scatter(&g, v, Wm);
+    og_fill_bc(&g, Wm);
+    memcpy(W0, Wm, bytes);
+    for (long k = 0; k < g.n[2]; ++k)
+        for (long j = 0; j < g.n[1]; ++j)
+            for (long i = 0; i < g.n[0]; ++i) {
+                long q = og_at(&g, i, j, k);
+                W0[q] = Wm[q] + 0.5 * dt2 * og_lap_point(&g, Wm, i, j, k);
+            }
+    og_fill_bc(&g, W0);
+    long m = 0;
+    for (long k = 0; k < g.n[2]; ++k)
+        for (long j = 0; j < g.n[1]; ++j)
+            for (long i = 0; i < g.n[0]; ++i) {
+                long q = og_at(&g, i, j, k);
+                out[m++] = c[0] * Wm[q] + c[1] * W0[q];
+            }
+    for (long step = 1; step < Nt; ++step) {
+        memset(Wp, 0, bytes);
+        for (long k = 0; k < g.n[2]; ++k)
+            for (long j = 0; j < g.n[1]; ++j)
+                for (long i = 0; i < g.n[0]; ++i) {
+                    long q = og_at(&g, i, j, k);
+                    Wp[q] = 2.0 * W0[q] - Wm[q] + dt2 * og_lap_point(&g, W0, i, j, k);
+                }
+        og_fill_bc(&g, Wp);
+        m = 0;
+        for (long k = 0; k < g.n[2]; ++k)
+            for (long j = 0; j < g.n[1]; ++j)
+                for (long i = 0; i < g.n[0]; ++i) out[m++] += c[step + 1] * Wp[og_at(&g, i, j, k)];
+        double* t = Wm;
+        Wm = W0;
+        W0 = Wp;
+        Wp = t;
+    }
+    free(Wm);
+    free(W0);
+    free(Wp);
+    return 0;
+}
+
+/* y = M x with M = I - a L_h, a = dt^2/2 (eq. impMatrix), active vectors. */
+int og_apply_M(int dim, const long* n, const double* h, int order, double a, const double* x,
+               double* y) {
+    og_grid g;
+    if (og_init(&g, dim, n, h, order)) return -1;
+    double* L = (double*)malloc(sizeof(double) * (size_t)g.nact);
+    if (!L) return -2;
+    og_apply_L(dim, n, h, order, x, L);
+    for (long m = 0; m < g.nact; ++m) y[m] = x[m] - a * L[m];
+    free(L);
+    return 0;
+}
+
+static double og_dot(long N, const double* x, const double* y) {
+    double s = 0.0;
+    for (long m = 0; m < N; ++m) s += x[m] * y[m];
+    return s;
+}
+
+/* Conjugate gradients on the symmetric positive definite M = I - a L_h,
+ * started from x = 0, stopped when ||b - M x|| <= tol ||b||.  Returns the
+ * iteration count, or -1 on bad arguments / no convergence in maxit. */
+int og_cg_solve_M(int dim, const long* n, const double* h, int order, double a, const double* b,
+                  double* x, double tol, int maxit) {
+    og_grid g;
+    if (og_init(&g, dim, n, h, order)) return -1;
+    long N = g.nact;
+    double* r = (double*)malloc(sizeof(double) * (size_t)N);
+    double* p = (double*)malloc(sizeof(double) * (size_t)N);
+    double* Ap = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!r || !p || !Ap) {
+        free(r);
+        free(p);
+        free(Ap);
+        return -2;
+    }
+    for (long m = 0; m < N; ++m) {
+        x[m] = 0.0;
+        r[m] = b[m];
+        p[m] = b[m];
+    }
+    double bb = og_dot(N, b, b);
+    double rr = bb;
+    int it = 0;
+    if (bb == 0.0) goto done;
+    for (it = 1; it <= maxit; ++it) {
+        og_apply_M(dim, n, h, order, a, p, Ap);
+        double alpha = rr / og_dot(N, p, Ap);
+        for (long m = 0; m < N; ++m) {
+            x[m] += alpha * p[m];
+            r[m] -= alpha * Ap[m];
+        }
+        double rr_new = og_dot(N, r, r);
+        if (sqrt(rr_new) <= tol * sqrt(bb)) {
+            rr = rr_new;
+            goto done;
+        }
+        double beta = rr_new / rr;
+        rr = rr_new;
+        for (long m = 0; m < N; ++m) p[m] = r[m] + beta * p[m];
+    }
+    it = -1;
+done:
+    free(r);
+    free(p);
+    free(Ap);
+    return it;
+}
+
+/* One application of the discrete EigenWave operator with implicit
+ * (trapezoidal-in-time) stepping, each system solved by CG to tol:
+ *   M W^1 = W^0                                             (eq. implicitStep1)
+ *   M W^{n+1} = 2 W^n - M W^{n-1}, i.e. W^{n+1} = M^{-1}(2 W^n) - W^{n-1}
+ *                                                           (eq. implicitScheme)
+ *   out = sum_{n=0}^{Nt} c_n W^n                            (eq. filterQuadrature) */
+int og_filter_implicit(int dim, const long* n, const double* h, int order, long Nt, double dt,
+                       const double* c, const double* v, double* out, double tol) {
+    og_grid g;
+    if (og_init(&g, dim, n, h, order) || Nt < 1) return -1;
+    long N = g.nact;
+    size_t bytes = sizeof(double) * (size_t)N;
+    double a = 0.5 * dt * dt;
+    double* Wm = (double*)malloc(bytes);
+    double* W0 = (double*)malloc(bytes);
+    double* rhs = (double*)malloc(bytes);
+    double* y = (double*)malloc(bytes);
+    int rc = 0;
+    if (!Wm || !W0 || !rhs || !y) {
+        rc = -2;
+        goto out;
+    }
+    memcpy(Wm, v, bytes);
+    if (og_cg_solve_M(dim, n, h, order, a, Wm, W0, tol, 100000) < 0) {
+        rc = -3;
+        goto out;
+    }
+    for (long m = 0; m < N; ++m) out[m] = c[0] * Wm[m] + c[1] * W0[m];
+    for (long step = 1; step < Nt; ++step) {
+        for (long m = 0; m < N; ++m) rhs[m] = 2.0 * W0[m];
+        if (og_cg_solve_M(dim, n, h, order, a, rhs, y, tol, 100000) < 0) {
+            rc = -3;
+            goto out;
+        }
+        for (long m = 0; m < N; ++m) {
+            double wp = y[m] - Wm[m];
+            Wm[m] = W0[m];
+            W0[m] = wp;
+            out[m] += c[step + 1] * wp;
+        }
+    }
+out:
+    free(Wm);
+    free(W0);
+    free(rhs);
+    free(y);
+    return rc;
+}

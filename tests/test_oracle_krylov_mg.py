@@ -1,0 +1,116 @@
+"""Pins of the oracle's Krylov eigen-solver, multigrid and learned-smoother
+pieces (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+import ew_inputs
+from oracle import oracle as O
+
+
+def _nearest_levels(g, prm, n_wanted, scheme="explicit"):
+    """The n_wanted closed-form lambda with the largest beta~_d."""
+    lam = np.sqrt(O.spectrum(g)[0])
+    b = O.beta_tilde(lam, prm, scheme)
+    idx = np.argsort(-b)[:n_wanted]
+    return np.sort(lam[idx]), np.sort(b[idx])[::-1]
+
+
+@pytest.mark.parametrize("order,scheme", [(4, "explicit"), (2, "implicit")])
+def test_krylov_schur_finds_closed_form_eigenpairs(order, scheme):
+    g = O.Grid((31, 47), (1.0, 1.5), order)
+    omega = 25.0
+    if scheme == "explicit":
+        prm = O.filter_params(omega, 2, O.steps_per_period_cfl(g, omega, 0.8))
+    else:
+        prm = O.filter_params(omega, 4, 10, adjust=True)
+    v0 = ew_inputs.start_block(3, g.size, 2)
+    theta, X, nmv = O.krylov_schur_eigs(lambda v: O.filter_apply(g, prm, v, scheme), v0, 6, 30,
+                                        tol=1e-10, max_matvecs=400)
+    assert len(theta) == 6
+    want_lam, want_beta = _nearest_levels(g, prm, 6, scheme)
+    np.testing.assert_allclose(theta, want_beta, atol=1e-9)
+    lam = np.sort([O.rayleigh_lambda(g, X[:, j]) for j in range(6)])
+    np.testing.assert_allclose(lam, want_lam, rtol=1e-10)
+    for j in range(6):
+        l = O.rayleigh_lambda(g, X[:, j])
+        assert O.eig_res(g, l, X[:, j]) < 1e-7
+
+
+def test_eigenspace_distance_of_multiple_eigenvalue():
+    """evect-err by projection onto a multiple eigenspace: any combination of
+    the (3,1) and (1,3) square modes is at distance 0, another mode is not."""
+    g = O.Grid((15, 15), (1.0, 1.0), 2)
+    a, b = O.sine_mode(g, (3, 1)), O.sine_mode(g, (1, 3))
+    basis = np.column_stack([a, b])
+    assert O.eigenspace_distance(0.3 * a - 2.0 * b, basis) < 1e-13
+    assert O.eigenspace_distance(O.sine_mode(g, (2, 2)), basis) > 0.5
+
+
+@pytest.mark.parametrize("dim,order", [(2, 2), (3, 4), (3, 2)])
+def test_multigrid_converges_to_exact_solve(dim, order):
+    n = (31, 31, 31)[:dim]
+    g = O.Grid(n, (1.0,) * dim, order)
+    a = 0.5 * (2 * math.pi / (20.0 * 10)) ** 2
+    b = ew_inputs.uniform_pm1(7, g.size)
+    exact = O.implicit_solve_closed_form(g, a, b)
+    x, hist = O.mg_solve(g, a, b, ncycles=12)
+    rho = (hist[-1] / hist[0]) ** (1 / 12)
+    assert rho < 0.25
+    assert np.max(np.abs(x - exact)) < 1e-9 * np.max(np.abs(exact))
+
+
+def _jacobi_as_net(g, a, wJ=0.8):
+    """Learned weights that make the learned correction equal to damped Jacobi:
+    W1 = identity tap on channel 0, W2 = (wJ / D) centre tap on channel 0."""
+    d0 = 2.0 if g.order == 2 else 2.5
+    D = 1 + a * sum(d0 / h ** 2 for h in g.h)
+    w = np.zeros(O.NET_WEIGHTS)
+    w[13] = 1.0
+    w[8 * 27 + 13] = wJ / D
+    return w
+
+
+def test_learned_path_reduces_to_jacobi():
+    g = O.Grid((15, 15, 15), (1.0, 1.0, 1.0), 4)
+    a = 0.5 * (2 * math.pi / 800.0) ** 2
+    b = ew_inputs.uniform_pm1(9, g.size)
+    w = _jacobi_as_net(g, a)
+    nets = np.stack([w, _jacobi_as_net(O.Grid((7, 7, 7), (1.0,) * 3, 4), a)])
+    x1, h1 = O.mg_solve(g, a, b, ncycles=3)
+    x2, h2 = O.mg_solve(g, a, b, ncycles=3, net=nets)
+    assert np.max(np.abs(x1 - x2)) < 1e-13
+    np.testing.assert_allclose(h1, h2, rtol=0, atol=1e-13 * h1[0])
+
+
+def test_conv_net_forward_special_cases():
+    """Single-tap kernels act as shifts with zero fill: W1 tap (dz,dy,dx) =
+    (0,0,1) on channel 2, W2 tap (1,0,0) on channel 2 gives y(x) = r(x + ex + ez)."""
+    n3 = (5, 4, 3)
+    r = ew_inputs.uniform_pm1(4, 60).reshape(3, 4, 5)
+    w = np.zeros(O.NET_WEIGHTS)
+    tap = lambda dz, dy, dx: (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)
+    w[2 * 27 + tap(0, 0, 1)] = 1.0
+    w[8 * 27 + 2 * 27 + tap(1, 0, 0)] = 2.0
+    _, y = O.conv_net_forward(n3, w, r.reshape(-1))
+    ref = np.zeros_like(r)
+    ref[:-1, :, :-1] = 2.0 * r[1:, :, 1:]
+    np.testing.assert_allclose(y.reshape(r.shape), ref, atol=1e-15)
+
+
+def test_conv_net_gradient_matches_finite_differences():
+    """Backward of the smoother loss against central finite differences of the
+    oracle's own forward pass (FP64)."""
+    g = O.Grid((6, 5, 4), (1.0, 0.9, 0.8), 4)
+    a = 0.5 * 0.05 ** 2
+    r = ew_inputs.uniform_pm1(12, g.size)
+    w = ew_inputs.learned_init(13, 0.2)
+    loss, gw = O.smoother_loss(g, a, w, r)
+    eps = 1e-6
+    for idx in [0, 13, 26, 100, 216, 229, 300, 431]:
+        wp, wm = w.copy(), w.copy()
+        wp[idx] += eps
+        wm[idx] -= eps
+        fd = (O.smoother_loss(g, a, wp, r)[0] - O.smoother_loss(g, a, wm, r)[0]) / (2 * eps)
+        assert abs(fd - gw[idx]) < 1e-6 * max(1.0, abs(fd))
