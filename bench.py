@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Throughput of the fused FP32 filter step (EigenWave wave-solve) on GB300.
+
+Workload: 2D rectangle [0,1] x [0,1.5], homogeneous Dirichlet, 4th-order
+9-point-wide Laplacian on 2047 x 3071 active points, explicit leapfrog at CFL
+0.8 (176 steps per period), target omega = 150, FP32 fields.  One bench step
+is one wave-solve (one application of S, N_p = 1 period) of a seeded
+uniform[-1,1] start vector: the first step, 175 fused leapfrog + filter steps
+and the filter accumulation, all in the library's kernels.
+
+value   = whole-job Gcell-steps/s = ranks x active points x N_t x K / (max over
+          ranks of the summed device time of the K timed steps);
+e2e     = the same metric through the C ABI from pinned HOST buffers, the
+          host->device copy of v and the device->host copy of S v inside the
+          timed region;
+roofline= the dominant kernel (the temporally blocked fused step): its
+          algorithmic HBM bytes per launch (read W^{n-1}, W^n, the filter sum;
+          write W^{n+b-1}, W^{n+b}, the filter sum: 24 B per active point per
+          launch) over its mean launch time, timed with CUDA events on the
+          launching stream over the timed region;
+cpu_baseline = the FP64 CPU oracle timed on this host on a bounded sample of
+          the same workload (the first time steps of the same wave-solve).
+
+The L2 (129 MB) is flushed between timed steps by writing a 512 MB buffer.
+`--impl reference` times the CPU oracle on the same workload (bounded sample
+per step) and prints the same JSON line with "impl": "reference".
+Multi-GPU: replicas only (the filter operator is not sharded); with torchrun
+each rank runs the same workload and `value` counts all ranks' work.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="rect2d_2047x3071_order4_fp32_explicit", n=(2047, 3071), length=(1.0, 1.5),
+                order=4, omega=150.0, num_periods=1, cfl=0.8, precision="fp32", nvec=1)
+METRIC = "Gcell-steps/s of fused filter step"
+UNIT = "Gcell-steps/s"
+BYTES_PER_POINT_PER_LAUNCH = 24  # 6 x FP32: W^{n-1}, W^n, acc in; W^{n+b-1}, W^{n+b}, acc out
+DOMINANT_KERNEL = "k_step_tb2d"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2507_18282_gb300", "csrc", "ew_tb2d.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--temporal-block", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def traffic_for_kernel():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when the kernel source changed since it was taken."""
+    try:
+        t = json.load(open(TRAFFIC_FILE))
+        src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+        if t.get("kernel_source_sha256") != src:
+            return None
+        return t.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def cpu_baseline_sample(target_s):
+    """Time the FP64 oracle on the first time steps of the same wave-solve."""
+    import numpy as np
+
+    import ew_inputs
+    from oracle import oracle as O
+    w = WORKLOAD
+    og = O.Grid(w["n"], w["length"], w["order"])
+    spp = O.steps_per_period_cfl(og, w["omega"], w["cfl"])
+    prm = O.filter_params(w["omega"], w["num_periods"], spp)
+    v = ew_inputs.uniform_pm1(ew_inputs.BASE_SEED + 1, og.size)
+
+    def run(steps):
+        sub = dict(prm)
+        sub["Nt"] = steps
+        sub["c"] = prm["c"][:steps + 1]
+        t0 = time.perf_counter()
+        O.filter_explicit(og, sub, v)
+        return time.perf_counter() - t0
+
+    t1 = run(2)
+    steps = int(max(2, min(prm["Nt"], target_s / max(t1 / 2.0, 1e-6))))
+    t = run(steps)
+    value = og.size * steps / t / 1e9
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "FP64 oracle (plain C, one thread), first %d of %d time steps of the same "
+                      "2047x3071 order-4 wave-solve, %.1f s" % (steps, prm["Nt"], t)}, steps, t
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import ew_inputs  # noqa: F401
+    from oracle import oracle as O
+    O.build()
+    # each step: a bounded sample (first `s` time steps) of the wave-solve on the full grid
+    info, s_steps, t = cpu_baseline_sample(min(args.cpu_seconds, 8.0))
+    per_step = max(2, min(s_steps, 8))
+    import numpy as np
+
+    import ew_inputs as I
+    w = WORKLOAD
+    og = O.Grid(w["n"], w["length"], w["order"])
+    spp = O.steps_per_period_cfl(og, w["omega"], w["cfl"])
+    prm = O.filter_params(w["omega"], 1, spp)
+    sub = dict(prm)
+    sub["Nt"] = per_step
+    sub["c"] = prm["c"][:per_step + 1]
+    v = I.uniform_pm1(I.BASE_SEED + 1, og.size)
+    for _ in range(args.warmup):
+        O.filter_explicit(og, sub, v)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.filter_explicit(og, sub, v)
+    dt = time.perf_counter() - t0
+    value = og.size * per_step * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w["workload"], "sample_time_steps_per_step": per_step,
+                       "l2": "not applicable (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "first %d of %d time steps of the wave-solve per step" % (per_step, prm["Nt"])},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import ew_inputs
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2507_18282_gb300 as ew
+    w = WORKLOAD
+    g = ew.ew_grid_create(2, w["n"], w["length"], order=w["order"], prec=w["precision"])
+    p = ew.filter_params(w["omega"], num_periods=w["num_periods"], cfl=w["cfl"],
+                         temporal_block=args.temporal_block)
+    info, _ = ew.ew_filter_setup(g, p)
+    N, Nt = g.size, info["Nt"]
+    v_host = ew_inputs.uniform_pm1(ew_inputs.BASE_SEED + 1, N).astype(np.float32)
+    vin = torch.from_numpy(v_host).cuda()
+    vout = torch.empty_like(vin)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        ew.ew_filter_apply(g, p, vin, vout)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region ----------------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    ew.ew_profile_enable(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))            # L2 flush between timed steps (not timed)
+        ev[k][0].record(stream)
+        ew.ew_filter_apply(g, p, vin, vout)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    prof = ew.ew_profile_read()
+    ew.ew_profile_enable(False)
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    barrier()
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * N * Nt * args.steps / (total_ms / 1e3) / 1e9
+
+    # ---- end to end through the C ABI from pinned host buffers ------------------
+    h_in = torch.from_numpy(v_host).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_in = torch.empty_like(vin)
+    d_out = torch.empty_like(vin)
+    for _ in range(2):
+        d_in.copy_(h_in, non_blocking=True)
+        ew.ew_filter_apply(g, p, d_in, d_out)
+        h_out.copy_(d_out, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0.record(stream)
+        d_in.copy_(h_in, non_blocking=True)
+        ew.ew_filter_apply(g, p, d_in, d_out)
+        h_out.copy_(d_out, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = world * N * Nt * args.steps / (float(t.item()) / 1e3) / 1e9
+    # sanity: the result is finite and nonzero
+    outn = float(h_out.abs().max())
+    assert np.isfinite(outn) and outn > 0.0
+
+    # ---- roofline of the dominant kernel -------------------------------------
+    pk, pk_kind = peaks()
+    launches = prof["fused_launches"]
+    mean_launch_ms = prof["fused_ms"] / max(launches, 1)
+    points_per_launch = prof["fused_points"] / max(launches, 1)
+    bytes_per_launch = BYTES_PER_POINT_PER_LAUNCH * points_per_launch
+    achieved = bytes_per_launch / (mean_launch_ms / 1e3) / 1e9
+    peak = float(pk["hbm_gbs"])
+    roofline = {"bound": "hbm", "kernel": DOMINANT_KERNEL, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for_kernel(),
+                "peak_source": pk_kind, "bytes_per_launch": bytes_per_launch,
+                "mean_launch_ms": mean_launch_ms,
+                "cell_steps_per_launch": prof["fused_cell_steps"] / max(launches, 1),
+                "share_of_step_time": prof["fused_ms"] / max(total_ms, 1e-9)}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["workload"], "grid": list(w["n"]), "length": list(w["length"]),
+                       "order": w["order"], "omega": w["omega"], "num_periods": w["num_periods"],
+                       "time_steps_per_step": Nt, "temporal_block": args.temporal_block or "default",
+                       "nvec": 1, "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * 4),
+                    "d2h_bytes_per_step": int(N * 4)},
+            "gpu_launches": int(prof["launches"]),
+            "roofline": roofline,
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        cb, _, _ = cpu_baseline_sample(args.cpu_seconds)
+        line["cpu_baseline"] = cb
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

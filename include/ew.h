@@ -1,0 +1,194 @@
+/*
+ * ew.h -- C ABI of the GB300 (sm_103a) EigenWave filter-operator library.
+ *
+ * EigenWave (Appelo, Banks, Henshaw, Le, Schwendeman, arXiv 2507.18282)
+ * finds eigenpairs  L_h phi = -lambda^2 phi  of the discrete Dirichlet
+ * Laplacian near a target frequency omega by applying the filter operator S
+ * (one "wave-solve"): step the discrete wave equation w_tt = L_h w from
+ * w(0) = v, w_t(0) = 0 over T_f = N_p 2 pi / omega and accumulate the
+ * cos(omega t)-weighted trapezoidal time integral (eq. filterQuadrature).
+ * S has the eigenvectors of L_h and eigenvalues beta in [-1/2, 1] peaked at
+ * lambda = omega (Theorem "Eigenvalues of the EigenWave operator").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Vectors hold the ACTIVE (interior) points only, x fastest, then y, then
+ *    z, densely packed (Algorithm matVec, Note 1 of the Arnoldi section).  A
+ *    block of `nvec` vectors is nvec such vectors back to back.  Their element
+ *    type is the grid's precision (float for EW_FP32, double for EW_FP64)
+ *    unless an entry point says otherwise.
+ *  - Every pointer named *_dev is device memory owned by the caller; every
+ *    pointer named *_host is host memory owned by the caller.  The library
+ *    owns grid handles and the scratch it allocates for them (freed by
+ *    ew_grid_destroy).  A grid handle is not thread safe: calls that share
+ *    one handle must not overlap.
+ *  - All GPU work is issued on the caller's `stream`.  Calls return when the
+ *    work is queued, except where the comment says the call synchronises.
+ *  - Inner products are the unweighted Euclidean sums over active points
+ *    (simple Rayleigh quotient, eq. simpleRayleighQuotient).
+ *  - Errors: every call returns an ew_status; on failure ew_last_error()
+ *    returns a message for the calling thread.  No exception crosses the ABI.
+ *    Device-side waits are bounded and report EW_ETIMEOUT.
+ */
+#ifndef EW_H_
+#define EW_H_
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EW_OK = 0,
+    EW_EINVAL = 1,       /* bad argument (null pointer, size, unsupported combination) */
+    EW_ENOMEM = 2,       /* device or host allocation failed */
+    EW_ECUDA = 3,        /* a CUDA runtime call failed */
+    EW_ENOCONV = 4,      /* an iteration stopped before meeting its tolerance */
+    EW_EBREAKDOWN = 5,   /* Krylov breakdown (invariant subspace smaller than asked) */
+    EW_ETIMEOUT = 6,     /* a bounded device wait gave up */
+    EW_EUNSUPPORTED = 7  /* valid request this build does not implement */
+} ew_status;
+
+typedef enum { EW_BC_DIRICHLET = 0, EW_BC_NEUMANN = 1 /* reserved, not implemented */ } ew_bc;
+typedef enum { EW_FP32 = 0, EW_FP64 = 1 } ew_prec;
+typedef enum { EW_EXPLICIT = 0, EW_IMPLICIT = 1 } ew_scheme;
+
+typedef struct ew_grid ew_grid; /* opaque, library-owned */
+
+/* Create a Cartesian box grid (Section "Discrete approximations", eq.
+ * eigBVPdiscrete, restricted to one Cartesian component grid).
+ *   dim         2 or 3
+ *   n_interior  active points per axis (n_interior[2] ignored in 2D), each >= 1
+ *   length      box side lengths; h_i = length_i / (n_i + 1)
+ *   order       2: the 5/7-point Laplacian; 4: the fourth-order 9/13-point
+ *               wide cross, closed at the wall by the odd reflection
+ *               u_{-j} = -u_{j} (u = 0 and u_xx = 0 on the boundary; the
+ *               paper's compatibility conditions are not spelled out)
+ *   bc          six faces (-x, +x, -y, +y, -z, +z); only EW_BC_DIRICHLET is
+ *               implemented (EW_EUNSUPPORTED otherwise); NULL = all Dirichlet
+ *   prec        field precision of every kernel run on this grid
+ * The handle binds to the CUDA device current at creation (or, if none is
+ * visible then, to the device current at its first GPU call); later calls
+ * must run with that device current (EW_EINVAL otherwise).  No GPU memory is
+ * allocated here, so grids and ew_filter_setup work on a host without a GPU. */
+ew_status ew_grid_create(int dim, const int64_t n_interior[3], const double length[3], int order,
+                         const ew_bc bc[6], ew_prec prec, ew_grid** out);
+void ew_grid_destroy(ew_grid* grid);
+
+/* Multigrid options for the implicit systems M x = b, M = I - (dt^2/2) L_h
+ * (eq. impMatrix).  The cycle: damped Jacobi (weight jacobi_weight, constant
+ * interior diagonal) or the learned smoother on the finest `learned_levels`
+ * levels; full weighting; linear interpolation; coarsening n -> (n-1)/2 while
+ * every axis has odd n >= 5; the coarsest level smoothed to convergence. */
+typedef struct {
+    int pre, post;            /* smoothing steps before / after the coarse correction (V(pre,post)) */
+    int max_cycles;           /* cycles per solve (>= 1) */
+    double rtol;              /* stop early when ||b - M x||_2 <= rtol ||b||_2 (0: run max_cycles) */
+    double jacobi_weight;     /* damped-Jacobi weight (0: 0.8) */
+    int learned_levels;       /* 0: plain multigrid */
+    const float* weights_dev; /* learned weights, learned_levels x 432 FP32 values (device), each
+                                 rounded to BF16 by the kernels; layout [W1 8x27 | W2 8x27],
+                                 taps (dz,dy,dx) with dz slowest */
+} ew_mg_params;
+
+/* Filter parameters (Section "Discrete approximations").
+ *   omega             target frequency (> 0)
+ *   num_periods       N_p >= 1; T_f = N_p 2 pi / omega
+ *   steps_per_period  N_its; N_t = N_p * N_its, dt = T_f / N_t.  0 = derive
+ *                     from `cfl` (explicit only): the smallest N_its with
+ *                     dt <= cfl * 2 / sqrt(rho(-L_h)), rho the largest
+ *                     eigenvalue of -L_h (4 sum 1/h^2, or 16/3 sum 1/h^2)
+ *   cfl               used when steps_per_period == 0 (<= 0: 0.8)
+ *   scheme            EW_EXPLICIT (leapfrog, eqs. explicitScheme and
+ *                     explicitStep1) or EW_IMPLICIT (eqs. implicitScheme,
+ *                     implicitStep1, solved by multigrid with `mg`)
+ *   adjust_omega      1: replace omega by omega~ of eq. adjustedOmega (needs
+ *                     N_its > 4); the filter then peaks at lambda = omega for
+ *                     the implicit scheme
+ *   temporal_block    explicit steps fused per launch (0: library default)
+ *   mg                implicit scheme only */
+typedef struct {
+    double omega;
+    int num_periods;
+    int steps_per_period;
+    double cfl;
+    ew_scheme scheme;
+    int adjust_omega;
+    int temporal_block;
+    const ew_mg_params* mg;
+} ew_filter_params;
+
+/* The derived quantities of one wave-solve (eqs. filterQuadrature, alphad). */
+typedef struct {
+    double omega_used;   /* omega, or omega~ when adjust_omega */
+    double final_time;   /* T_f */
+    double dt;
+    double alpha_d;      /* tan(omega dt / 2) / tan(omega dt) */
+    int64_t num_steps;   /* N_t */
+    int steps_per_period;
+} ew_filter_info;
+
+/* Compute the wave-solve parameters on the host.  weights_host (may be NULL)
+ * receives the N_t + 1 filter weights c_n = (2/T_f) sigma_n (cos(omega t^n) -
+ * alpha_d / 2), sigma the trapezoid weights (dt/2 at both ends, dt inside);
+ * weights_cap is its capacity (EW_EINVAL if < N_t + 1). */
+ew_status ew_filter_setup(const ew_grid* grid, const ew_filter_params* params,
+                          ew_filter_info* info_host, double* weights_host, int64_t weights_cap);
+
+/* v_out = S v_in for each of `nvec` vectors: one wave-solve (Algorithm matVec
+ * with the explicit or implicit scheme and the trapezoidal filter).  v_in and
+ * v_out are device blocks of nvec vectors in the grid precision; they must not
+ * overlap.  Scratch (a few fields per vector) is allocated on first use and
+ * kept with the grid. */
+ew_status ew_filter_apply(const ew_grid* grid, const ew_filter_params* params, const void* v_in_dev,
+                          void* v_out_dev, int nvec, cudaStream_t stream);
+
+/* Lu = L_h u for nvec vectors (grid precision, device). */
+ew_status ew_apply_L(const ew_grid* grid, const void* u_dev, void* Lu_dev, int nvec,
+                     cudaStream_t stream);
+
+/* Stage 2 of the EigenWave approach (Arnoldi section): for each of nvec
+ * vectors phi, lambda = sqrt(-sum phi L phi / sum phi^2) (eq.
+ * simpleRayleighQuotient) and eig-res = ||L phi + lambda^2 phi||_inf /
+ * (lambda^2 ||phi||_inf) (accuracy metrics, Section "Numerical results").
+ * Reductions run on the device in FP64.  Synchronises `stream`.
+ * eig_res_host may be NULL. */
+ew_status ew_rayleigh(const ew_grid* grid, const void* phi_dev, int nvec, double* lambda_host,
+                      double* eig_res_host, cudaStream_t stream);
+
+/* Algorithm EigenWave (power iteration on S): v <- S v, beta = (S v, v),
+ * v <- S v / ||S v||, until ||v_new - sign(beta) v_old||_2 < tol or `iters`
+ * iterations; then lambda from the Rayleigh quotient of L_h.  v_dev (one
+ * vector, grid precision) is normalised first and holds the last iterate on
+ * return.  beta_host (may be NULL) receives one beta per iteration done.
+ * Synchronises `stream` once per iteration. */
+ew_status ew_power_iteration(const ew_grid* grid, const ew_filter_params* params, void* v_dev,
+                             int iters, double tol, double* beta_host, int* iters_done,
+                             double* lambda_host, cudaStream_t stream);
+
+/* Launch accounting, for benchmarks.  While enabled (process-wide), the
+ * library counts every kernel it launches and brackets each launch of its
+ * fused time-step kernels (the explicit leapfrog + filter kernels) with a
+ * pair of CUDA events recorded on the launching stream.  ew_profile_read
+ * waits for the recorded events, returns the totals since the last read and
+ * resets them.  Enabling or disabling also resets. */
+typedef struct {
+    int64_t launches;          /* all kernels launched by the library */
+    int64_t fused_launches;    /* launches of the fused time-step kernels */
+    double fused_ms;           /* summed event time of those launches */
+    int64_t fused_cell_steps;  /* active points x time steps they advanced */
+    int64_t fused_points;      /* active points they covered, summed over launches */
+} ew_profile;
+ew_status ew_profile_enable(int on);
+ew_status ew_profile_read(ew_profile* out_host);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* ew_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EW_H_ */

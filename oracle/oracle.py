@@ -18,13 +18,14 @@ from __future__ import annotations
 import ctypes
 import math
 import os
+import platform
 import subprocess
 import threading
 
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_BUILD = os.path.join(_HERE, "_build")
+_BUILD = os.path.join(_HERE, "_build", platform.machine())
 _SO = os.path.join(_BUILD, "libew_oracle.so")
 _SOURCES = ["ew_oracle.c", "ew_oracle_mg.c"]
 _lock = threading.Lock()

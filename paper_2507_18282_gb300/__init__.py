@@ -1,0 +1,168 @@
+"""GB300 (sm_103a) EigenWave filter-operator library: Python binding.
+
+The functions below carry the names of the C ABI entry points in
+include/ew.h and only marshal arguments: every step of the filter operator
+runs in the CUDA kernels of libew.so.  Device memory and streams come from
+PyTorch (CUDA tensors, torch's current stream).
+
+    g = ew_grid_create(2, (2047, 3071), (1.0, 1.5), order=4, prec="fp32")
+    p = filter_params(omega=150.0, num_periods=1)
+    ew_filter_apply(g, p, v_in, v_out)          # v_out = S v_in on the GPU
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (EW_EXPLICIT, EW_FP32, EW_FP64, EW_IMPLICIT, EWError, check, lib,
+                   ew_filter_info, ew_filter_params, ew_mg_params)
+
+__all__ = ["Grid", "EWError", "ew_grid_create", "ew_grid_destroy", "filter_params", "mg_params",
+           "ew_filter_setup", "ew_filter_apply", "ew_apply_L", "ew_rayleigh", "ew_power_iteration",
+           "ew_last_error", "LIB_PATH"]
+
+LIB_PATH = _lib.LIB_PATH
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t, dtype, numel=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA torch tensor")
+    if t.dtype != dtype:
+        raise TypeError("expected dtype %s, got %s" % (dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if numel is not None and t.numel() < numel:
+        raise ValueError("tensor holds %d elements, need %d" % (t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Grid:
+    """Owner of an ew_grid* handle (ew_grid_create / ew_grid_destroy)."""
+
+    def __init__(self, handle, dim, n, length, order, prec):
+        self.handle = handle
+        self.dim, self.n, self.length, self.order, self.prec = dim, tuple(n), tuple(length), order, prec
+        self.size = int(np.prod(self.n))
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float32 if self.prec == EW_FP32 else torch.float64
+
+    def close(self):
+        if self.handle:
+            lib.ew_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ew_grid_create(dim, n, length, order=2, prec="fp32"):
+    p = {"fp32": EW_FP32, "fp64": EW_FP64, EW_FP32: EW_FP32, EW_FP64: EW_FP64}[prec]
+    n3 = (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+    l3 = (ctypes.c_double * 3)(*(list(length) + [1.0] * (3 - len(length))))
+    h = ctypes.c_void_p()
+    check(lib.ew_grid_create(int(dim), n3, l3, int(order), None, p, ctypes.byref(h)))
+    return Grid(h, dim, n[:dim], length[:dim], order, p)
+
+
+def ew_grid_destroy(grid: Grid):
+    grid.close()
+
+
+def mg_params(pre=2, post=2, max_cycles=1, rtol=0.0, jacobi_weight=0.8, learned_levels=0, weights=None):
+    m = ew_mg_params(pre, post, max_cycles, rtol, jacobi_weight, learned_levels,
+                     ctypes.c_void_p(weights.data_ptr()) if weights is not None else None)
+    m._keep = weights
+    return m
+
+
+def filter_params(omega, num_periods=1, steps_per_period=0, cfl=0.8, scheme="explicit",
+                  adjust_omega=False, temporal_block=0, mg=None):
+    s = {"explicit": EW_EXPLICIT, "implicit": EW_IMPLICIT, EW_EXPLICIT: EW_EXPLICIT,
+         EW_IMPLICIT: EW_IMPLICIT}[scheme]
+    p = ew_filter_params(float(omega), int(num_periods), int(steps_per_period), float(cfl), s,
+                         int(bool(adjust_omega)), int(temporal_block),
+                         ctypes.pointer(mg) if mg is not None else None)
+    p._keep = mg
+    return p
+
+
+def ew_filter_setup(grid: Grid, params):
+    """(info dict, weights c_n as float64 numpy array) of one wave-solve."""
+    info = ew_filter_info()
+    check(lib.ew_filter_setup(grid.handle, ctypes.byref(params), ctypes.byref(info), None, 0))
+    w = np.empty(info.num_steps + 1, dtype=np.float64)
+    check(lib.ew_filter_setup(grid.handle, ctypes.byref(params), None,
+                              w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), w.size))
+    return dict(omega=info.omega_used, Tf=info.final_time, dt=info.dt, alpha_d=info.alpha_d,
+                Nt=info.num_steps, steps_per_period=info.steps_per_period), w
+
+
+def ew_filter_apply(grid: Grid, params, v_in, v_out, nvec=None, stream=None):
+    nvec = nvec if nvec is not None else max(1, v_in.numel() // grid.size)
+    a = _ptr(v_in, grid.dtype, nvec * grid.size)
+    b = _ptr(v_out, grid.dtype, nvec * grid.size)
+    check(lib.ew_filter_apply(grid.handle, ctypes.byref(params), a, b, int(nvec), _stream(stream)))
+    return v_out
+
+
+def ew_apply_L(grid: Grid, u, Lu, nvec=None, stream=None):
+    nvec = nvec if nvec is not None else max(1, u.numel() // grid.size)
+    check(lib.ew_apply_L(grid.handle, _ptr(u, grid.dtype, nvec * grid.size),
+                         _ptr(Lu, grid.dtype, nvec * grid.size), int(nvec), _stream(stream)))
+    return Lu
+
+
+def ew_rayleigh(grid: Grid, phi, nvec=None, stream=None):
+    """(lambda, eig-res) per vector, as float64 numpy arrays."""
+    nvec = nvec if nvec is not None else max(1, phi.numel() // grid.size)
+    lam = np.zeros(nvec)
+    res = np.zeros(nvec)
+    dp = ctypes.POINTER(ctypes.c_double)
+    check(lib.ew_rayleigh(grid.handle, _ptr(phi, grid.dtype, nvec * grid.size), int(nvec),
+                          lam.ctypes.data_as(dp), res.ctypes.data_as(dp), _stream(stream)))
+    return lam, res
+
+
+def ew_power_iteration(grid: Grid, params, v, iters, tol=0.0, stream=None):
+    """Algorithm EigenWave on the GPU.  v is updated in place; returns
+    (betas, iterations done, lambda)."""
+    betas = np.zeros(max(iters, 1))
+    done = ctypes.c_int(0)
+    lam = ctypes.c_double(0.0)
+    check(lib.ew_power_iteration(grid.handle, ctypes.byref(params), _ptr(v, grid.dtype, grid.size),
+                                 int(iters), float(tol),
+                                 betas.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 ctypes.byref(done), ctypes.byref(lam), _stream(stream)))
+    return betas[:done.value], done.value, lam.value
+
+
+def ew_profile_enable(on=True):
+    check(lib.ew_profile_enable(int(bool(on))))
+
+
+def ew_profile_read():
+    """Totals since the last read: launches, fused_launches, fused_ms, fused_cell_steps, fused_points."""
+    p = _lib.ew_profile()
+    check(lib.ew_profile_read(ctypes.byref(p)))
+    return dict(launches=p.launches, fused_launches=p.fused_launches, fused_ms=p.fused_ms,
+                fused_cell_steps=p.fused_cell_steps, fused_points=p.fused_points)
+
+
+def ew_last_error() -> str:
+    return _lib.last_error()

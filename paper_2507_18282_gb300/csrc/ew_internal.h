@@ -1,0 +1,150 @@
+// ew_internal.h -- shared declarations of the EigenWave CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ew.h"
+
+namespace ew {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+ew_status set_error(ew_status s, const std::string& msg);
+ew_status cuda_error(cudaError_t e, const char* what);
+void clear_error();
+
+#define EW_CUDA_TRY(call)                                   \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return ew::cuda_error(e_, #call); \
+    } while (0)
+
+#define EW_TRY(call)                          \
+    do {                                      \
+        ew_status s_ = (call);                \
+        if (s_ != EW_OK) return s_;           \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// launch accounting (ew_profile_*)
+// ---------------------------------------------------------------------------
+extern bool g_profile_on;
+void count_launch(int64_t k = 1);
+// brackets a fused-step launch: returns the start event (or null when off)
+cudaEvent_t fused_begin(cudaStream_t st);
+void fused_end(cudaEvent_t start, cudaStream_t st, int64_t points, int64_t cell_steps);
+
+// ---------------------------------------------------------------------------
+// stencil coefficients, already multiplied by a scale (dt^2, dt^2/2, -a, 1)
+//   scale * L_h u = c0 u + sum_axis c1[a] (u[-1] + u[+1]) + c2[a] (u[-2] + u[+2])
+// order 2: c1 = scale / h^2, c2 = 0,          c0 = -2 sum c1
+// order 4: c1 = scale 16 / (12 h^2), c2 = -scale / (12 h^2), c0 = -scale 30/12 sum 1/h^2
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Stencil {
+    T c0;
+    T c1[3];
+    T c2[3];
+};
+
+struct GridGeom {
+    int dim;
+    int order;
+    int64_t n[3];  // active points per axis (n[2] = 1 in 2D)
+    double h[3];
+    int64_t N;     // active points
+};
+
+template <typename T>
+Stencil<T> make_stencil(const GridGeom& g, double scale);
+
+// ---------------------------------------------------------------------------
+// device scratch owned by a grid handle
+// ---------------------------------------------------------------------------
+struct Scratch {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    ew_status reserve(size_t want);
+    void release();
+};
+
+}  // namespace ew
+
+struct ew_grid {
+    ew::GridGeom geom;
+    double length[3];
+    ew_prec prec;
+    int device;
+    ew::Scratch fields;    // wave-solve time levels
+    ew::Scratch reduce;    // reduction partials
+    ew::Scratch misc;      // small device tables (filter weights)
+    ew::Scratch mg;        // multigrid hierarchy
+    void* host_pinned = nullptr;  // small pinned staging for reductions
+    size_t host_pinned_bytes = 0;
+};
+
+namespace ew {
+
+// filter parameters (a1) on the host
+struct FilterPlan {
+    double omega;
+    double Tf;
+    double dt;
+    double alpha_d;
+    int64_t Nt;
+    int spp;
+    std::vector<double> c;  // N_t + 1 weights
+};
+ew_status plan_filter(const GridGeom& g, const ew_filter_params* p, FilterPlan* out);
+
+// --- kernels launchers (ew_stencil.cu) ------------------------------------
+template <typename T>
+ew_status launch_apply_L(const GridGeom& g, const T* u, T* Lu, int nvec, double scale,
+                         cudaStream_t st);
+
+// one explicit wave-solve for nvec vectors; fields = 4 * N * nvec elements
+// of scratch; cdev = N_t + 1 weights (device, type T).
+template <typename T>
+ew_status explicit_wave_solve(const GridGeom& g, const FilterPlan& plan, const T* cdev,
+                              const T* vin, T* vout, int nvec, T* fields, int temporal_block,
+                              cudaStream_t st);
+
+// --- temporally blocked 2D steps (ew_tb2d.cu) -----------------------------
+// choose (and cache) the tile / depth variant for this grid shape by timing
+// each candidate on the given buffers; writes F[2], F[3] and acc.
+template <typename T>
+ew_status tb2d_tune(const GridGeom& g, const FilterPlan& plan, const T* cdev, T* const* F, T* acc, int nvec,
+                    int64_t fstride, cudaStream_t st);
+// advance from level L (F[*cur], F[*prv] = level L-1) to level N_t; tb > 0
+// caps the steps per launch (and uses the default variant), tb == 0 uses the
+// tuned variant.
+template <typename T>
+ew_status tb2d_advance(const GridGeom& g, const FilterPlan& plan, const T* cdev, T* const* F, int* prv, int* cur,
+                       int64_t L, T* acc, int nvec, int64_t fstride, int tb, cudaStream_t st);
+template <typename T>
+int tb2d_choice(const GridGeom& g, int nvec, int* B, int* TX, int* TY);
+
+// --- reductions (ew_reduce.cu) ---------------------------------------------
+// out[j] = sum_i x_j[i] * y_j[i] for nvec pairs of vectors (FP64 accumulate),
+// partial sums in `part` (>= nvec * kReduceBlocks doubles), result on device.
+constexpr int kReduceBlocks = 304;
+template <typename T>
+ew_status launch_dots(const T* x, const T* y, int64_t N, int nvec, double* part, double* out,
+                      cudaStream_t st);
+// out[j] = max_i |x_j[i] + s_j y_j[i]| (s on device) and max_i |y_j[i]|
+template <typename T>
+ew_status launch_resid_inf(const T* Lx, const T* x, int64_t N, int nvec, const double* lam2,
+                           double* part, double* out_res, double* out_xinf, cudaStream_t st);
+template <typename T>
+ew_status launch_scale(T* x, int64_t N, int nvec, const double* s, cudaStream_t st);
+// y = a * x + y with device scalar: y_j -= s_j * x_j
+template <typename T>
+ew_status launch_diffnorm_sign(const T* xnew, const T* xold, int64_t N, const double* beta,
+                               double* part, double* out, cudaStream_t st);
+
+}  // namespace ew

@@ -1,0 +1,369 @@
+// ew_stencil.cu -- fused leapfrog + filter kernels for the explicit wave-solve.
+//
+// One wave-solve (Algorithm matVec with the explicit scheme):
+//   W^0 = V,  W^1 = V + (dt^2/2) L_h V                       (eq. explicitStep1)
+//   W^{n+1} = 2 W^n - W^{n-1} + dt^2 L_h W^n                 (eq. explicitScheme)
+//   V_out  = sum_{n=0}^{N_t} c_n W^n                          (eq. filterQuadrature)
+// The filter sum is accumulated inside the time loop, as the paper notes for
+// Algorithm EigenWave, so no time history is stored.
+//
+// Fields are stored in the active-point layout (x fastest, no padding): the
+// Dirichlet closure is applied on the fly.  A point one step outside the box
+// is a boundary point (value 0); for the fourth-order stencil the point two
+// steps outside is a ghost holding the odd reflection -u(mirror).
+//
+// Kernels:
+//   k_first_step      : a3, writes W^0, W^1 and V_out = c_0 W^0 + c_1 W^1.
+//   k_step_simple     : one time step per launch (any dim), reads W^n and its
+//                       neighbours from global memory, writes W^{n+1} over
+//                       W^{n-1} and V_out += c W^{n+1}.
+//   k_step_tb2d       : (ew_tb2d.cu) b time steps per launch on overlapped
+//                       tiles staged in shared memory (temporal blocking).
+//   k_resident2d      : the whole wave-solve of a small 2D grid inside one CTA
+//                       (grid + ghosts resident in shared memory).
+#include <algorithm>
+#include <utility>
+
+#include "ew_internal.h"
+
+namespace ew {
+
+template <typename T>
+Stencil<T> make_stencil(const GridGeom& g, double scale) {
+    Stencil<T> s;
+    double c0 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        s.c1[a] = T(0);
+        s.c2[a] = T(0);
+    }
+    for (int a = 0; a < g.dim; ++a) {
+        double ih2 = 1.0 / (g.h[a] * g.h[a]);
+        if (g.order == 2) {
+            s.c1[a] = T(scale * ih2);
+            c0 += -2.0 * scale * ih2;
+        } else {
+            s.c1[a] = T(scale * 16.0 / 12.0 * ih2);
+            s.c2[a] = T(-scale / 12.0 * ih2);
+            c0 += -scale * 30.0 / 12.0 * ih2;
+        }
+    }
+    s.c0 = T(c0);
+    return s;
+}
+template Stencil<float> make_stencil<float>(const GridGeom&, double);
+template Stencil<double> make_stencil<double>(const GridGeom&, double);
+
+// ---------------------------------------------------------------------------
+// global-memory stencil with the Dirichlet closure
+// ---------------------------------------------------------------------------
+// neighbour at offset `off` along an axis with stride `stride`; `i` is the
+// point's coordinate on that axis, `n` the axis length.
+template <typename T>
+__device__ __forceinline__ T ld_axis(const T* __restrict__ u, int64_t base, int64_t stride, int64_t i,
+                                     int64_t n, int off) {
+    int64_t p = i + off;
+    if (p >= 0 && p < n) return u[base + off * stride];
+    if (p == -1 || p == n) return T(0);
+    int64_t q = (p < 0) ? (-2 - p) : (2 * n - p);  // odd reflection about -1 / n
+    return -u[base + (q - i) * stride];
+}
+
+template <typename T, int DIM, int ORDER>
+__device__ __forceinline__ T lap_global(const T* __restrict__ u, const Stencil<T>& s, int64_t base,
+                                        int64_t i, int64_t j, int64_t k, int64_t nx, int64_t ny,
+                                        int64_t nz) {
+    T r = s.c0 * u[base];
+    r += s.c1[0] * (ld_axis(u, base, 1, i, nx, -1) + ld_axis(u, base, 1, i, nx, 1));
+    r += s.c1[1] * (ld_axis(u, base, nx, j, ny, -1) + ld_axis(u, base, nx, j, ny, 1));
+    if (DIM == 3)
+        r += s.c1[2] * (ld_axis(u, base, nx * ny, k, nz, -1) + ld_axis(u, base, nx * ny, k, nz, 1));
+    if (ORDER == 4) {
+        r += s.c2[0] * (ld_axis(u, base, 1, i, nx, -2) + ld_axis(u, base, 1, i, nx, 2));
+        r += s.c2[1] * (ld_axis(u, base, nx, j, ny, -2) + ld_axis(u, base, nx, j, ny, 2));
+        if (DIM == 3)
+            r += s.c2[2] * (ld_axis(u, base, nx * ny, k, nz, -2) + ld_axis(u, base, nx * ny, k, nz, 2));
+    }
+    return r;
+}
+
+template <typename T, int DIM, int ORDER>
+__global__ void k_apply_L(int64_t nx, int64_t ny, int64_t nz, const T* __restrict__ u,
+                          T* __restrict__ Lu, Stencil<T> s) {
+    const int64_t N = nx * ny * nz;
+    const int64_t v = blockIdx.y;
+    u += v * N;
+    Lu += v * N;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q % nx, t = q / nx, j = t % ny, k = t / ny;
+        Lu[q] = lap_global<T, DIM, ORDER>(u, s, q, i, j, k, nx, ny, nz);
+    }
+}
+
+// a3: W^0 = V (copied, the caller's input stays untouched), W^1 = V + (dt^2/2) L V,
+// V_out = c0 W^0 + c1 W^1.  `s` carries the dt^2/2 scale.
+template <typename T, int DIM, int ORDER>
+__global__ void k_first_step(int64_t nx, int64_t ny, int64_t nz, const T* __restrict__ vin,
+                             T* __restrict__ W0, T* __restrict__ W1, T* __restrict__ vout,
+                             Stencil<T> s, T c0, T c1, int64_t fstride) {
+    const int64_t N = nx * ny * nz;
+    const int64_t v = blockIdx.y;
+    vin += v * N;
+    vout += v * N;
+    W0 += v * fstride;
+    W1 += v * fstride;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q % nx, t = q / nx, j = t % ny, k = t / ny;
+        T x = vin[q];
+        T w1 = x + lap_global<T, DIM, ORDER>(vin, s, q, i, j, k, nx, ny, nz);
+        W0[q] = x;
+        W1[q] = w1;
+        vout[q] = c0 * x + c1 * w1;
+    }
+}
+
+// one step, in place: Wprev <- 2 W - Wprev + dt^2 L W ; acc += c Wprev
+template <typename T, int DIM, int ORDER>
+__global__ void k_step_simple(int64_t nx, int64_t ny, int64_t nz, const T* __restrict__ W,
+                              T* __restrict__ Wprev, T* __restrict__ acc, Stencil<T> s, T c,
+                              int64_t fstride) {
+    const int64_t N = nx * ny * nz;
+    const int64_t v = blockIdx.y;
+    W += v * fstride;
+    Wprev += v * fstride;
+    acc += v * N;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q % nx, t = q / nx, j = t % ny, k = t / ny;
+        T u = W[q];
+        T wn = T(2) * u - Wprev[q] + lap_global<T, DIM, ORDER>(W, s, q, i, j, k, nx, ny, nz);
+        Wprev[q] = wn;
+        acc[q] += c * wn;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// whole wave-solve of a small 2D grid in one CTA
+// ---------------------------------------------------------------------------
+// ghost fix-up of a whole padded 2D grid (pitch PX, 2 ghost layers), order 4 only
+template <typename T, int R>
+__device__ __forceinline__ void resident_fix(T* buf, int nx, int ny, int PX, int tid, int nthr) {
+    constexpr int G = 2;
+    if (R != 2) return;
+    for (int q = tid; q < 2 * ny + 2 * nx; q += nthr) {
+        if (q < 2 * ny) {
+            int y = q >> 1, side = q & 1;
+            int gx = side ? nx + 1 : -2, mx = side ? nx - 1 : 0;
+            buf[(y + G) * PX + gx + G] = -buf[(y + G) * PX + mx + G];
+        } else {
+            int r = q - 2 * ny;
+            int x = r >> 1, side = r & 1;
+            int gy = side ? ny + 1 : -2, my = side ? ny - 1 : 0;
+            buf[(gy + G) * PX + x + G] = -buf[(my + G) * PX + x + G];
+        }
+    }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(1024)
+    k_resident2d(int nx, int ny, const T* __restrict__ vin, T* __restrict__ vout,
+                 const T* __restrict__ cw, int64_t Nt, Stencil<T> st, Stencil<T> st_half) {
+    constexpr int G = 2;
+    const int PX = nx + 2 * G, PY = ny + 2 * G;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sA = reinterpret_cast<T*>(smem_raw);
+    T* sB = sA + PX * PY;
+    T* sAcc = sB + PX * PY;
+    const int64_t N = (int64_t)nx * ny;
+    vin += blockIdx.x * N;
+    vout += blockIdx.x * N;
+    const int nthr = blockDim.x;
+    const int tid = threadIdx.x;
+
+    auto fix = [&](T* buf) { resident_fix<T, R>(buf, nx, ny, PX, tid, nthr); };
+    auto lap = [&](const T* c, int p, const Stencil<T>& s) {
+        T r = s.c0 * c[p] + s.c1[0] * (c[p - 1] + c[p + 1]) + s.c1[1] * (c[p - PX] + c[p + PX]);
+        if (R == 2) r += s.c2[0] * (c[p - 2] + c[p + 2]) + s.c2[1] * (c[p - 2 * PX] + c[p + 2 * PX]);
+        return r;
+    };
+
+    for (int q = tid; q < PX * PY; q += nthr) {
+        sA[q] = T(0);
+        sB[q] = T(0);
+    }
+    __syncthreads();
+    for (int q = tid; q < N; q += nthr) {
+        int x = q % nx, y = q / nx;
+        sB[(y + G) * PX + x + G] = vin[q];
+    }
+    __syncthreads();
+    fix(sB);
+    __syncthreads();
+    // first step into A (eq. explicitStep1)
+    const T c0 = cw[0], c1 = cw[1];
+    for (int q = tid; q < N; q += nthr) {
+        int x = q % nx, y = q / nx;
+        int p = (y + G) * PX + x + G;
+        T w1 = sB[p] + lap(sB, p, st_half);
+        sA[p] = w1;
+        sAcc[q] = c0 * sB[p] + c1 * w1;
+    }
+    __syncthreads();
+    fix(sA);
+    __syncthreads();
+    T* cur = sA;
+    T* prv = sB;
+    for (int64_t n = 1; n < Nt; ++n) {
+        const T cn = cw[n + 1];
+        for (int q = tid; q < N; q += nthr) {
+            int x = q % nx, y = q / nx;
+            int p = (y + G) * PX + x + G;
+            T wn = T(2) * cur[p] - prv[p] + lap(cur, p, st);
+            prv[p] = wn;
+            sAcc[q] += cn * wn;
+        }
+        __syncthreads();
+        fix(prv);
+        __syncthreads();
+        T* t = cur;
+        cur = prv;
+        prv = t;
+    }
+    for (int q = tid; q < N; q += nthr) vout[q] = sAcc[q];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static int grid_blocks(int64_t N, int threads) {
+    int64_t b = (N + threads - 1) / threads;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <typename T>
+ew_status launch_apply_L(const GridGeom& g, const T* u, T* Lu, int nvec, double scale,
+                         cudaStream_t st) {
+    Stencil<T> s = make_stencil<T>(g, scale);
+    dim3 grid(grid_blocks(g.N, 256), nvec);
+    if (g.dim == 2 && g.order == 2)
+        k_apply_L<T, 2, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, u, Lu, s);
+    else if (g.dim == 2)
+        k_apply_L<T, 2, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, u, Lu, s);
+    else if (g.order == 2)
+        k_apply_L<T, 3, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], u, Lu, s);
+    else
+        k_apply_L<T, 3, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], u, Lu, s);
+    EW_CUDA_TRY(cudaGetLastError());
+    count_launch();
+    return EW_OK;
+}
+template ew_status launch_apply_L<float>(const GridGeom&, const float*, float*, int, double,
+                                         cudaStream_t);
+template ew_status launch_apply_L<double>(const GridGeom&, const double*, double*, int, double,
+                                          cudaStream_t);
+
+template <typename T>
+static size_t resident_smem(const GridGeom& g) {
+    return sizeof(T) * ((size_t)2 * (g.n[0] + 4) * (g.n[1] + 4) + (size_t)g.n[0] * g.n[1]);
+}
+
+template <typename T>
+static ew_status first_step(const GridGeom& g, const T* vin, T* W0, T* W1, T* vout,
+                            const FilterPlan& plan, int nvec, int64_t fstride, cudaStream_t st) {
+    Stencil<T> s = make_stencil<T>(g, 0.5 * plan.dt * plan.dt);
+    dim3 grid(grid_blocks(g.N, 256), nvec);
+    T c0 = T(plan.c[0]), c1 = T(plan.c[1]);
+    if (g.dim == 2 && g.order == 2)
+        k_first_step<T, 2, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, vin, W0, W1, vout, s, c0, c1, fstride);
+    else if (g.dim == 2)
+        k_first_step<T, 2, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, vin, W0, W1, vout, s, c0, c1, fstride);
+    else if (g.order == 2)
+        k_first_step<T, 3, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, W0, W1, vout, s, c0, c1, fstride);
+    else
+        k_first_step<T, 3, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, W0, W1, vout, s, c0, c1, fstride);
+    EW_CUDA_TRY(cudaGetLastError());
+    count_launch();
+    return EW_OK;
+}
+
+template <typename T>
+static ew_status step_simple(const GridGeom& g, const T* W, T* Wprev, T* acc, T c, const Stencil<T>& s,
+                             int nvec, int64_t fstride, cudaStream_t st) {
+    dim3 grid(grid_blocks(g.N, 256), nvec);
+    cudaEvent_t ev = fused_begin(st);
+    if (g.dim == 2 && g.order == 2)
+        k_step_simple<T, 2, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, W, Wprev, acc, s, c, fstride);
+    else if (g.dim == 2)
+        k_step_simple<T, 2, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, W, Wprev, acc, s, c, fstride);
+    else if (g.order == 2)
+        k_step_simple<T, 3, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], W, Wprev, acc, s, c, fstride);
+    else
+        k_step_simple<T, 3, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], W, Wprev, acc, s, c, fstride);
+    EW_CUDA_TRY(cudaGetLastError());
+    fused_end(ev, st, g.N * nvec, g.N * nvec);
+    return EW_OK;
+}
+
+template <typename T>
+static ew_status resident(const GridGeom& g, const T* vin, T* vout, const T* cw, const FilterPlan& plan,
+                          int nvec, cudaStream_t st) {
+    Stencil<T> s = make_stencil<T>(g, plan.dt * plan.dt);
+    Stencil<T> sh = make_stencil<T>(g, 0.5 * plan.dt * plan.dt);
+    size_t smem = resident_smem<T>(g);
+    int threads = (int)std::min<int64_t>(1024, ((g.N + 31) / 32) * 32);
+    cudaEvent_t ev = fused_begin(st);
+    if (g.order == 2) {
+        EW_CUDA_TRY(cudaFuncSetAttribute(k_resident2d<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        k_resident2d<T, 1><<<nvec, threads, smem, st>>>((int)g.n[0], (int)g.n[1], vin, vout, cw, plan.Nt, s, sh);
+    } else {
+        EW_CUDA_TRY(cudaFuncSetAttribute(k_resident2d<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        k_resident2d<T, 2><<<nvec, threads, smem, st>>>((int)g.n[0], (int)g.n[1], vin, vout, cw, plan.Nt, s, sh);
+    }
+    EW_CUDA_TRY(cudaGetLastError());
+    fused_end(ev, st, g.N * nvec, g.N * nvec * plan.Nt);
+    return EW_OK;
+}
+
+// Resident path: small 2D grids whose three fields fit in one CTA's shared
+// memory and would leave most SMs idle anyway.
+template <typename T>
+static bool use_resident(const GridGeom& g, int nvec) {
+    return g.dim == 2 && resident_smem<T>(g) <= 200 * 1024 && g.N <= 16384 && nvec <= 4 * 152;
+}
+
+template <typename T>
+ew_status explicit_wave_solve(const GridGeom& g, const FilterPlan& plan, const T* cdev, const T* vin, T* vout,
+                              int nvec, T* fields, int temporal_block, cudaStream_t st) {
+    if (temporal_block < 0) return set_error(EW_EINVAL, "temporal_block < 0");
+    if (use_resident<T>(g, nvec) && temporal_block == 0) return resident<T>(g, vin, vout, cdev, plan, nvec, st);
+    // fields are laid out [field][vector][point]
+    const int64_t fstride = g.N;
+    T* F[4];
+    for (int q = 0; q < 4; ++q) F[q] = fields + (int64_t)q * nvec * g.N;
+    const bool blocked = g.dim == 2 && temporal_block != 1;
+    // the tuner writes the spare fields and the filter sum, so it runs before the first step
+    if (blocked && temporal_block == 0) EW_TRY(tb2d_tune<T>(g, plan, cdev, F, vout, nvec, fstride, st));
+    EW_TRY(first_step<T>(g, vin, F[0], F[1], vout, plan, nvec, fstride, st));
+    if (blocked) {
+        int prv = 0, cur = 1;
+        return tb2d_advance<T>(g, plan, cdev, F, &prv, &cur, 1, vout, nvec, fstride, temporal_block, st);
+    }
+    Stencil<T> s = make_stencil<T>(g, plan.dt * plan.dt);
+    int prv = 0, cur = 1;
+    for (int64_t L = 1; L < plan.Nt; ++L) {
+        EW_TRY(step_simple<T>(g, F[cur], F[prv], vout, T(plan.c[L + 1]), s, nvec, fstride, st));
+        std::swap(prv, cur);
+    }
+    return EW_OK;
+}
+template ew_status explicit_wave_solve<float>(const GridGeom&, const FilterPlan&, const float*, const float*,
+                                              float*, int, float*, int, cudaStream_t);
+template ew_status explicit_wave_solve<double>(const GridGeom&, const FilterPlan&, const double*,
+                                               const double*, double*, int, double*, int, cudaStream_t);
+
+}  // namespace ew

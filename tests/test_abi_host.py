@@ -1,0 +1,92 @@
+"""Host-side checks of the C ABI (no GPU): every declared symbol is exported,
+the parameter math (a1) equals the oracle's, and bad arguments are refused."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ew():
+    import __graft_entry__
+    __graft_entry__._build_module().build()
+    import paper_2507_18282_gb300 as ew
+    return ew
+
+
+def _declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(ew_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(ew):
+    names = _declared_functions()
+    assert "ew_filter_apply" in names and "ew_grid_create" in names
+    lib = ctypes.CDLL(ew.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("dim,n,length,order,omega,spp,Np,adjust", [
+    (2, (63, 63), (1.0, 1.0), 2, 20.0, 0, 1, False),
+    (2, (2047, 3071), (1.0, 1.5), 4, 150.0, 0, 2, False),
+    (3, (511, 511, 511), (1.0, 1.0, 1.0), 2, 60.0, 0, 1, False),
+    (3, (255, 255, 255), (1.0, 1.0, 1.0), 4, 80.0, 10, 3, True),
+])
+def test_filter_parameters_match_oracle(ew, dim, n, length, order, omega, spp, Np, adjust):
+    from oracle import oracle as O
+    g = ew.ew_grid_create(dim, n, length, order=order, prec="fp32")
+    scheme = "implicit" if adjust else "explicit"
+    p = ew.filter_params(omega, num_periods=Np, steps_per_period=spp, scheme=scheme, adjust_omega=adjust)
+    info, c = ew.ew_filter_setup(g, p)
+    og = O.Grid(n, length, order)
+    s = spp if spp else O.steps_per_period_cfl(og, omega, 0.8)
+    ref = O.filter_params(omega, Np, s, adjust=adjust)
+    assert info["steps_per_period"] == s and info["Nt"] == ref["Nt"]
+    assert abs(info["dt"] - ref["dt"]) <= 1e-15 * ref["dt"]
+    assert abs(info["omega"] - ref["omega"]) <= 1e-14 * ref["omega"]
+    assert abs(info["alpha_d"] - ref["alpha_d"]) <= 1e-14
+    np.testing.assert_allclose(c, ref["c"], rtol=0, atol=1e-15 * np.max(np.abs(ref["c"])))
+    g.close()
+
+
+def test_config_steps_per_period(ew):
+    """Steps per period at CFL 0.8 of the explicit workloads."""
+    cases = [((63, 63), (1.0, 1.0), 2, 20.0, 36), ((2047, 3071), (1.0, 1.5), 4, 150.0, 176),
+             ((511, 511, 511), (1.0, 1.0, 1.0), 2, 60.0, 117)]
+    for n, L, o, w, want in cases:
+        g = ew.ew_grid_create(len(n), n, L, order=o)
+        info, _ = ew.ew_filter_setup(g, ew.filter_params(w))
+        assert info["steps_per_period"] == want
+        g.close()
+
+
+def test_bad_arguments_are_refused(ew):
+    with pytest.raises(ew.EWError) as e:
+        ew.ew_grid_create(4, (3, 3, 3), (1, 1, 1))
+    assert e.value.status == 1
+    with pytest.raises(ew.EWError):
+        ew.ew_grid_create(2, (0, 3), (1, 1))
+    with pytest.raises(ew.EWError):
+        ew.ew_grid_create(2, (3, 3), (1, -1))
+    with pytest.raises(ew.EWError):
+        ew.ew_grid_create(2, (3, 3), (1, 1), order=3)
+    g = ew.ew_grid_create(2, (31, 31), (1, 1))
+    for p in [ew.filter_params(-1.0), ew.filter_params(5.0, num_periods=0),
+              ew.filter_params(5.0, steps_per_period=3),  # beyond the leapfrog stability limit
+              ew.filter_params(5.0, steps_per_period=4, scheme="implicit", adjust_omega=True)]:
+        with pytest.raises(ew.EWError) as e:
+            ew.ew_filter_setup(g, p)
+        assert e.value.status == 1
+        assert ew.ew_last_error()
+    g.close()
