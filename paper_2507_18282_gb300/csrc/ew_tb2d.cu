@@ -105,6 +105,25 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) 
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Packed two-point arithmetic.  FP32 uses the sm_100+ paired instructions
+// (one instruction for both points); FP64 does the same operations one lane
+// at a time.  Explicit rounding-mode forms, so no operation is contracted
+// differently between the two points of a pair.
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float s_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double2 p_add(double2 a, double2 b) {
+    return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 p_mul(double2 a, double2 b) {
+    return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 p_fma(double2 a, double2 b, double2 c) {
+    return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double s_add(double a, double b) { return __dadd_rn(a, b); }
+
 // MINB: CTAs per SM the register budget is sized for.
 template <typename T, int R, int NWX, int NTY, int KY, int B, int MINB>
 __global__ void __launch_bounds__(32 * NWX * NTY, MINB)
@@ -166,30 +185,28 @@ __global__ void __launch_bounds__(32 * NWX * NTY, MINB)
     const int klo = max(0, H - sy0);
     const int khi = min(min(KY, H + TY - sy0), ny - gy0);
 
-    T acca[KY], accb[KY];
+    T2 accp[KY];  // filter sums of the thread's two columns
     {
         int64_t base = (int64_t)gy0 * nx + gx;
         asm volatile("" : "+l"(base));  // keep row addresses out of registers across the time loop
 #pragma unroll
         for (int k = 0; k < KY; ++k) {
             const bool oy = k >= klo && k < khi;
-            acca[k] = (own_a && oy) ? acc[base + (int64_t)k * nx] : T(0);
-            accb[k] = (own_b && oy) ? acc[base + (int64_t)k * nx + 1] : T(0);
+            accp[k].x = (own_a && oy) ? acc[base + (int64_t)k * nx] : T(0);
+            accp[k].y = (own_b && oy) ? acc[base + (int64_t)k * nx + 1] : T(0);
         }
     }
     cp_async_wait_all();
     __syncthreads();
 
     // W^{n-1} of the thread's own points lives in registers from here on
-    T pa[KY], pb[KY];
+    T2 pp[KY];
 #pragma unroll
-    for (int k = 0; k < KY; ++k) {
-        const T2 p2 = *reinterpret_cast<const T2*>(sP + (sy0 + k) * PX + cx);
-        pa[k] = p2.x;
-        pb[k] = p2.y;
-    }
+    for (int k = 0; k < KY; ++k) pp[k] = *reinterpret_cast<const T2*>(sP + (sy0 + k) * PX + cx);
 
-    const T c0 = st.c0, c1x = st.c1[0], c1y = st.c1[1], c2x = st.c2[0], c2y = st.c2[1];
+    const T2 C0{st.c0, st.c0}, C1X{st.c1[0], st.c1[0]}, C1Y{st.c1[1], st.c1[1]};
+    const T2 C2X{st.c2[0], st.c2[0]}, C2Y{st.c2[1], st.c2[1]};
+    const T2 TWO{T(2), T(2)}, MONE{T(-1), T(-1)};
     T* cur = sC;
     T* nxt = sP;  // its old content (W^{n-1}) is only ever read by the owning thread
     for (int s = 0; s < b; ++s) {
@@ -200,6 +217,7 @@ __global__ void __launch_bounds__(32 * NWX * NTY, MINB)
         T2 w2 = *reinterpret_cast<const T2*>(col + sy0 * PX);
         T2 w3 = *reinterpret_cast<const T2*>(col + (sy0 + 1) * PX);
         const T cs = cw[s];
+        const T2 CS{cs, cs};
 #pragma unroll
         for (int k = 0; k < KY; ++k) {
             const int row = (sy0 + k) * PX + cx;
@@ -207,21 +225,21 @@ __global__ void __launch_bounds__(32 * NWX * NTY, MINB)
                                                  : T2{T(0), T(0)};
             const T2 L = *reinterpret_cast<const T2*>(cur + row - 2);  // columns x-2, x-1
             const T2 Q = *reinterpret_cast<const T2*>(cur + row + 2);  // columns x+2, x+3
-            // point a at column x, point b at column x+1
-            T la = c0 * w2.x + c1x * (L.y + w2.y) + c1y * (w1.x + w3.x);
-            T lb = c0 * w2.y + c1x * (w2.x + Q.x) + c1y * (w1.y + w3.y);
+            // point a at column x, point b at column x+1; every sum is (left + right)
+            T2 sx1;
+            sx1.x = s_add(L.y, w2.y);
+            sx1.y = s_add(w2.x, Q.x);
+            T2 lap = p_mul(C0, w2);
+            lap = p_fma(C1X, sx1, lap);
+            lap = p_fma(C1Y, p_add(w1, w3), lap);
             if (R == 2) {
-                la += c2x * (L.x + Q.x) + c2y * (w0.x + w4.x);
-                lb += c2x * (L.y + Q.y) + c2y * (w0.y + w4.y);
+                lap = p_fma(C2X, p_add(L, Q), lap);
+                lap = p_fma(C2Y, p_add(w0, w4), lap);
             }
-            T2 nv;
-            nv.x = (T(2) * w2.x - pa[k]) + la;
-            nv.y = (T(2) * w2.y - pb[k]) + lb;
+            const T2 nv = p_fma(TWO, w2, p_fma(MONE, pp[k], lap));  // 2 W^n + (dt^2 L W^n - W^{n-1})
             *reinterpret_cast<T2*>(nxt + row) = nv;
-            pa[k] = w2.x;
-            pb[k] = w2.y;
-            acca[k] += cs * nv.x;  // only owned entries are stored
-            accb[k] += cs * nv.y;
+            pp[k] = w2;
+            accp[k] = p_fma(CS, nv, accp[k]);  // only owned entries are stored
             w0 = w1;
             w1 = w2;
             w2 = w3;
@@ -232,7 +250,7 @@ __global__ void __launch_bounds__(32 * NWX * NTY, MINB)
         cur = nxt;
         nxt = t;
     }
-    // cur = W^{n+b} (shared), pa/pb = W^{n+b-1} (registers)
+    // cur = W^{n+b} (shared), pp = W^{n+b-1} (registers)
     int64_t base = (int64_t)gy0 * nx + gx;
     asm volatile("" : "+l"(base));
 #pragma unroll
@@ -242,13 +260,13 @@ __global__ void __launch_bounds__(32 * NWX * NTY, MINB)
             const int64_t g = base + (int64_t)k * nx;
             if (own_a) {
                 Bout[g] = c2.x;
-                Aout[g] = pa[k];
-                acc[g] = acca[k];
+                Aout[g] = pp[k].x;
+                acc[g] = accp[k].x;
             }
             if (own_b) {
                 Bout[g + 1] = c2.y;
-                Aout[g + 1] = pb[k];
-                acc[g + 1] = accb[k];
+                Aout[g + 1] = pp[k].y;
+                acc[g + 1] = accp[k].y;
             }
         }
     }
