@@ -168,6 +168,65 @@ ew_status ew_power_iteration(const ew_grid* grid, const ew_filter_params* params
                              int iters, double tol, double* beta_host, int* iters_done,
                              double* lambda_host, cudaStream_t stream);
 
+/* Matrix-free eigen-solver on S (Arnoldi section; Algorithms arnoldi, IRAM,
+ * KrylovSchur): block Krylov-Schur with thick restarts.  Wave-solves run in
+ * the grid precision; the basis, classical Gram-Schmidt applied twice, the
+ * Rayleigh-Ritz projection and all reductions are FP64.  The wanted pairs
+ * are the n_wanted largest algebraic eigenvalues beta of S, i.e. the
+ * eigenvalues lambda of L_h nearest the filter peak at omega.  lambda is
+ * then taken from the Rayleigh quotient of L_h (eq. simpleRayleighQuotient).
+ * With refine_fp64 on an FP32 grid the result is refined in FP64 (mixed
+ * precision, see refine_fp64).  Convergence is fast when the filter peak holds about
+ * krylov_dim eigenvalues: choose num_periods N_p accordingly (the peak is
+ * about omega / N_p wide). */
+typedef struct {
+    int n_wanted;          /* N_r, 1..EW_MAX_EIGS */
+    int krylov_dim;        /* N_a: basis size at which the solver restarts (rounded up to a multiple of
+                              block); >= n_wanted + block, krylov_dim + 2 block <= 160; 0: 2 N_r + block */
+    int block;             /* vectors per expansion, 1..16 (at least the largest multiplicity near omega) */
+    double tol;            /* accept a Ritz pair when ||S x - theta x||_2 <= tol (||x|| = 1);
+                              0: 1e-4 on FP32 grids (about the FP32 wave-solve noise), 1e-10 on FP64 */
+    int max_wave_solves;   /* budget of first-stage filter applications (one per vector); 0: 2000 */
+    uint64_t seed;         /* start block from SplitMix64 uniform [-1,1) when start_dev is NULL:
+                              element q of the N x block column-major block is draw q of stream seed */
+    int refine_fp64;       /* FP32 grids, FP64 refinement of the result (0: none).
+                              1: mixed-precision iterative refinement of the invariant subspace: per
+                                 outer step (at most 6) one FP64 wave-solve per wanted (and guard)
+                                 vector X gives
+                                 the exact relation S X = X Theta + E; span[X, E] is extended by three
+                                 FP32 block expansions and Rayleigh-Ritz with S picks the new X; stops
+                                 when the FP64 Ritz residuals ||E_j|| <= refine_tol.  A final
+                                 Rayleigh-Ritz with L_h inside span[X] separates near-degenerate pairs.
+                              2: a second Krylov-Schur run with FP64 full-filter wave-solves started
+                                 from the FP32 vectors (block n_wanted, basis 3 n_wanted) */
+    double refine_tol;     /* FP64 Ritz residual target of the refinement; 0: 1e-10 */
+} ew_eigs_params;
+
+#define EW_MAX_EIGS 64
+typedef struct {
+    int n_converged;                       /* first-stage pairs that met tol */
+    int wave_solves;                       /* first-stage filter applications */
+    int wave_solves_fp64;                  /* FP64 refinement filter applications */
+    int restarts;
+    double seconds;                        /* wall time of the call */
+    double beta[EW_MAX_EIGS];              /* Ritz values of S, descending */
+    double eig_res[EW_MAX_EIGS];           /* final eig-res (accuracy metrics, Section "Numerical results") */
+    double lambda_stage1[EW_MAX_EIGS];     /* lambda from the first-stage vectors */
+    double eig_res_stage1[EW_MAX_EIGS];
+    double lambda_rel_change[EW_MAX_EIGS]; /* |lambda - nearest first-stage lambda| / lambda */
+} ew_eigs_report;
+
+/* lambda_host (n_wanted) receives lambda per pair in the order of descending
+ * beta; vecs_dev (may be NULL) receives the FP64 eigenvectors, N x n_wanted
+ * column-major, unit 2-norm.  start_dev (may be NULL) is an FP64 N x block
+ * start block.  Allocates its own workspace (basis N x (krylov_dim + 2 block)
+ * FP64) for the duration of the call and synchronises `stream`.  Returns
+ * EW_ENOCONV (results still filled) when the budget ran out first,
+ * EW_EBREAKDOWN when the Krylov space became invariant. */
+ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params* params, const ew_eigs_params* eigs,
+                          const double* start_dev, double* lambda_host, double* vecs_dev,
+                          ew_eigs_report* report_host, cudaStream_t stream);
+
 /* Launch accounting, for benchmarks.  While enabled (process-wide), the
  * library counts every kernel it launches and brackets each launch of its
  * fused time-step kernels (the explicit leapfrog + filter kernels) with a

@@ -152,6 +152,36 @@ def ew_power_iteration(grid: Grid, params, v, iters, tol=0.0, stream=None):
     return betas[:done.value], done.value, lam.value
 
 
+def eigs_params(n_wanted, krylov_dim=0, block=1, tol=0.0, max_wave_solves=0, seed=0, refine_fp64=False,
+                refine_tol=0.0):
+    return _lib.ew_eigs_params(int(n_wanted), int(krylov_dim), int(block), float(tol), int(max_wave_solves),
+                               int(seed), int(refine_fp64), float(refine_tol))
+
+
+def ew_arnoldi_eigs(grid: Grid, params, eigs, start=None, vecs=None, stream=None, allow_noconv=False):
+    """Block Krylov-Schur on S.  Returns (lambda (n_wanted,), report dict, status).
+    `start` (FP64 CUDA tensor, N x block column-major) and `vecs` (FP64 CUDA
+    tensor receiving N x n_wanted eigenvectors) are optional."""
+    nw = eigs.n_wanted
+    lam = np.zeros(nw)
+    rep = _lib.ew_eigs_report()
+    import torch
+    sp = _ptr(start, torch.float64, grid.size * max(eigs.block, 1)) if start is not None else None
+    vp = _ptr(vecs, torch.float64, grid.size * nw) if vecs is not None else None
+    st = lib.ew_arnoldi_eigs(grid.handle, ctypes.byref(params), ctypes.byref(eigs), sp,
+                             lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), vp, ctypes.byref(rep),
+                             _stream(stream))
+    if st != _lib.EW_OK and not (allow_noconv and st == _lib.EW_ENOCONV):
+        check(st)
+    report = dict(n_converged=rep.n_converged, wave_solves=rep.wave_solves,
+                  wave_solves_fp64=rep.wave_solves_fp64, restarts=rep.restarts, seconds=rep.seconds,
+                  beta=np.array(rep.beta[:nw]), eig_res=np.array(rep.eig_res[:nw]),
+                  lambda_stage1=np.array(rep.lambda_stage1[:nw]),
+                  eig_res_stage1=np.array(rep.eig_res_stage1[:nw]),
+                  lambda_rel_change=np.array(rep.lambda_rel_change[:nw]))
+    return lam, report, st
+
+
 def ew_profile_enable(on=True):
     check(lib.ew_profile_enable(int(bool(on))))
 

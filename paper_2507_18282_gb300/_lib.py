@@ -58,6 +58,25 @@ class ew_filter_info(ctypes.Structure):
                 ("num_steps", ctypes.c_int64), ("steps_per_period", ctypes.c_int)]
 
 
+EW_MAX_EIGS = 64
+
+
+class ew_eigs_params(ctypes.Structure):
+    _fields_ = [("n_wanted", ctypes.c_int), ("krylov_dim", ctypes.c_int), ("block", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_wave_solves", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("refine_fp64", ctypes.c_int), ("refine_tol", ctypes.c_double)]
+
+
+class ew_eigs_report(ctypes.Structure):
+    _fields_ = [("n_converged", ctypes.c_int), ("wave_solves", ctypes.c_int),
+                ("wave_solves_fp64", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("seconds", ctypes.c_double), ("beta", ctypes.c_double * EW_MAX_EIGS),
+                ("eig_res", ctypes.c_double * EW_MAX_EIGS),
+                ("lambda_stage1", ctypes.c_double * EW_MAX_EIGS),
+                ("eig_res_stage1", ctypes.c_double * EW_MAX_EIGS),
+                ("lambda_rel_change", ctypes.c_double * EW_MAX_EIGS)]
+
+
 class ew_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("fused_launches", ctypes.c_int64),
                 ("fused_ms", ctypes.c_double), ("fused_cell_steps", ctypes.c_int64),
@@ -79,8 +98,10 @@ lib.ew_rayleigh.argtypes = [_vp, _vp, _i, _dp, _dp, _vp]
 lib.ew_power_iteration.argtypes = [_vp, ctypes.POINTER(ew_filter_params), _vp, _i, _d, _dp, _ip, _dp, _vp]
 lib.ew_profile_enable.argtypes = [_i]
 lib.ew_profile_read.argtypes = [ctypes.POINTER(ew_profile)]
+lib.ew_arnoldi_eigs.argtypes = [_vp, ctypes.POINTER(ew_filter_params), ctypes.POINTER(ew_eigs_params), _vp, _dp,
+                                _vp, ctypes.POINTER(ew_eigs_report), _vp]
 for _name in ["ew_grid_create", "ew_filter_setup", "ew_filter_apply", "ew_apply_L", "ew_rayleigh",
-              "ew_power_iteration", "ew_profile_enable", "ew_profile_read"]:
+              "ew_power_iteration", "ew_profile_enable", "ew_profile_read", "ew_arnoldi_eigs"]:
     getattr(lib, _name).restype = ctypes.c_int
 
 

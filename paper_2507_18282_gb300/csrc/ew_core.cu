@@ -210,6 +210,12 @@ static ew_status filter_apply_t(ew_grid* g, const ew_filter_params* p, const Fil
     return explicit_wave_solve<T>(g->geom, plan, cdev, vin, vout, nvec, (T*)g->fields.ptr, p->temporal_block, st);
 }
 
+ew_status filter_apply_any(ew_grid* g, const ew_filter_params* p, const FilterPlan& plan, const void* vin,
+                           void* vout, int nvec, cudaStream_t st) {
+    if (g->prec == EW_FP32) return filter_apply_t<float>(g, p, plan, (const float*)vin, (float*)vout, nvec, st);
+    return filter_apply_t<double>(g, p, plan, (const double*)vin, (double*)vout, nvec, st);
+}
+
 }  // namespace ew
 
 using namespace ew;
@@ -451,6 +457,13 @@ static ew_status power_t(ew_grid* g, const ew_filter_params* p, T* v, int iters,
     return EW_OK;
 }
 
+}  // namespace ew
+
+namespace ew {
+ew_status rayleigh_any(ew_grid* g, const void* phi, int nvec, double* lam, double* res, cudaStream_t st) {
+    if (g->prec == EW_FP32) return rayleigh_t<float>(g, (const float*)phi, nvec, lam, res, st);
+    return rayleigh_t<double>(g, (const double*)phi, nvec, lam, res, st);
+}
 }  // namespace ew
 
 extern "C" {

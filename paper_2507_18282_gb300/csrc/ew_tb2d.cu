@@ -320,6 +320,9 @@ const std::vector<Tb2dVariant>& tb2d_variants<double, 2>() {
     static const std::vector<Tb2dVariant> v = {
         EW_TB2D_VARIANT(double, 2, 2, 8, 8, 4, 1), EW_TB2D_VARIANT(double, 2, 2, 8, 8, 2, 1),
         EW_TB2D_VARIANT(double, 2, 2, 4, 8, 4, 2), EW_TB2D_VARIANT(double, 2, 1, 16, 8, 4, 1),
+        // FP64 is ALU-bound on this part: shallow depths recompute fewer halo points
+        EW_TB2D_VARIANT(double, 2, 2, 8, 8, 1, 1), EW_TB2D_VARIANT(double, 2, 2, 4, 8, 1, 2),
+        EW_TB2D_VARIANT(double, 2, 2, 4, 8, 2, 2),
     };
     return v;
 }
@@ -328,6 +331,7 @@ const std::vector<Tb2dVariant>& tb2d_variants<double, 1>() {
     static const std::vector<Tb2dVariant> v = {
         EW_TB2D_VARIANT(double, 1, 2, 8, 8, 4, 1), EW_TB2D_VARIANT(double, 1, 2, 8, 8, 2, 1),
         EW_TB2D_VARIANT(double, 1, 2, 4, 8, 4, 2), EW_TB2D_VARIANT(double, 1, 2, 8, 8, 8, 1),
+        EW_TB2D_VARIANT(double, 1, 2, 8, 8, 1, 1), EW_TB2D_VARIANT(double, 1, 2, 4, 8, 1, 2),
     };
     return v;
 }
