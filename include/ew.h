@@ -227,6 +227,63 @@ ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params* params, c
                           const double* start_dev, double* lambda_host, double* vecs_dev,
                           ew_eigs_report* report_host, cudaStream_t stream);
 
+/* Multigrid solve of one implicit time-step system (eqs. impMatrix,
+ * implicitStep1):  (I - half_dt2 L_h) x = rhs.  x_dev holds the initial guess
+ * on entry and the result on return (grid precision, device).  Runs up to
+ * mg->max_cycles V-cycles (fewer once ||rhs - M x||_2 <= rtol ||rhs||_2 when
+ * rtol > 0).  conv_factor_host (may be NULL) receives the mean residual
+ * reduction per cycle, cycles_done_host (may be NULL) the cycles run.  Axis
+ * lengths must halve down (n -> (n-1)/2) to at most 2048 coarse points, e.g.
+ * n = 2^k - 1 (EW_EUNSUPPORTED otherwise).  Synchronises `stream`; EW_ENOCONV
+ * if rtol > 0 was not met. */
+ew_status ew_implicit_step_mg(const ew_grid* grid, double half_dt2, const void* rhs_dev, void* x_dev,
+                              const ew_mg_params* mg, double* conv_factor_host, int* cycles_done_host,
+                              cudaStream_t stream);
+
+/* Learned multigrid smoother (no counterpart in the paper; it replaces the
+ * damped-Jacobi step of the V-cycle on the finest levels, see ew_mg_params).
+ * The correction of a residual r on a 3D grid, zero outside the active box:
+ *   h_c(x) = sum_{o in {-1,0,1}^3} W1[c][o] r(x + o),  c = 0..7
+ *   N(r)(x) = sum_c sum_o W2[c][o] h_c(x + o)
+ * no bias, no activation (the smoothing step stays linear).  weights_dev: 432
+ * FP32 values [W1 8x27 | W2 8x27], taps (dz, dy, dx) with dz slowest; weights,
+ * r and h are rounded to BF16 and products accumulated in FP32.
+ * ew_smoother_forward: y = N(r).  ew_smoother_backward: grad_dev (432 FP32)
+ * = d(loss)/d(weights) for a loss with d(loss)/dy = gy (r, gy grid precision,
+ * device).  3D grids only. */
+ew_status ew_smoother_forward(const ew_grid* grid, const float* weights_dev, const void* r_dev, void* y_dev,
+                              cudaStream_t stream);
+ew_status ew_smoother_backward(const ew_grid* grid, const float* weights_dev, const void* r_dev,
+                               const void* gy_dev, float* grad_dev, cudaStream_t stream);
+
+/* Train the learned smoother for the system (I - half_dt2 L_h) x = b on this
+ * grid (FP32, 3D).  Residual samples come from plain multigrid solves of the
+ * same system (random right-hand sides, the residual at the start of the
+ * first three V-cycles); each of `steps` Adam steps minimises
+ *   1/2 ||M (e - N(r))||^2 = 1/2 ||r - M N(r)||^2    (M e = r)
+ * over one sample, with the library's forward and backward kernels.  Plain
+ * multigrid judges the result: the convergence factors of V(pre, post) cycles
+ * with the Jacobi smoother and with the learned one on the finest level are
+ * measured on the same system, and the weights are kept only if the learned
+ * factor is lower (else weights_dev is restored: plain-multigrid fallback).
+ * weights_dev (432 FP32, device) holds the initial weights on entry. */
+typedef struct {
+    int steps;             /* Adam steps */
+    int samples;           /* residual samples kept on the device */
+    double lr;             /* Adam learning rate */
+    int pre, post;         /* V-cycle shape of the sample generation and of the judgement */
+    double jacobi_weight;  /* plain smoother weight (0: 0.8) */
+    uint64_t seed;         /* right-hand sides: SplitMix64 streams seed, seed + 1, ... */
+    int judge_cycles;      /* V-cycles per convergence-factor measurement (0: 6) */
+} ew_train_params;
+typedef struct {
+    double loss_first, loss_last;    /* training loss of the first and the last step */
+    double conv_plain, conv_learned; /* residual reduction per V-cycle */
+    int accepted;                    /* 1: learned weights kept */
+} ew_train_report;
+ew_status ew_smoother_train(const ew_grid* grid, double half_dt2, const ew_train_params* params,
+                            float* weights_dev, ew_train_report* report_host, cudaStream_t stream);
+
 /* Launch accounting, for benchmarks.  While enabled (process-wide), the
  * library counts every kernel it launches and brackets each launch of its
  * fused time-step kernels (the explicit leapfrog + filter kernels) with a

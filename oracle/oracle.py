@@ -370,6 +370,26 @@ def mg_solve(g: Grid, a, b, x0=None, nu1=2, nu2=2, wJ=0.8, ncycles=1, net=None):
     return x, hist
 
 
+def filter_implicit_mg(g: Grid, prm, v, nu1=2, nu2=2, wJ=0.8, ncycles=2, net=None):
+    """S v with the implicit scheme (eqs. implicitScheme, implicitStep1) where
+    every system M y = rhs gets `ncycles` multigrid V-cycles (ew_oracle_mg.c)
+    from the initial guess y = rhs (so W^0 for the first step and 2 W^n
+    after).  With ncycles large this tends to filter_implicit."""
+    v = np.asarray(v, dtype=np.float64).reshape(-1)
+    a = 0.5 * prm["dt"] ** 2
+    c = prm["c"]
+    wm = v.copy()
+    w0, _ = mg_solve(g, a, wm, x0=wm, nu1=nu1, nu2=nu2, wJ=wJ, ncycles=ncycles, net=net)
+    out = c[0] * wm + c[1] * w0
+    for n in range(1, prm["Nt"]):
+        rhs = 2.0 * w0
+        y, _ = mg_solve(g, a, rhs, x0=rhs, nu1=nu1, nu2=nu2, wJ=wJ, ncycles=ncycles, net=net)
+        wp = y - wm
+        wm, w0 = w0, wp
+        out = out + c[n + 1] * wp
+    return out
+
+
 def conv_net_forward(n3, w, r):
     """Learned-smoother correction N(r) on a 3D active box of extents n3 = (nx, ny, nz).
     Returns (hidden 8 x N, y)."""

@@ -182,6 +182,46 @@ def ew_arnoldi_eigs(grid: Grid, params, eigs, start=None, vecs=None, stream=None
     return lam, report, st
 
 
+def ew_implicit_step_mg(grid: Grid, half_dt2, rhs, x, mg, stream=None):
+    """Multigrid solve of (I - half_dt2 L_h) x = rhs; x holds the initial guess
+    and receives the result.  Returns (convergence factor, cycles run)."""
+    conv = ctypes.c_double(0.0)
+    cyc = ctypes.c_int(0)
+    check(lib.ew_implicit_step_mg(grid.handle, float(half_dt2), _ptr(rhs, grid.dtype, grid.size),
+                                  _ptr(x, grid.dtype, grid.size), ctypes.byref(mg), ctypes.byref(conv),
+                                  ctypes.byref(cyc), _stream(stream)))
+    return conv.value, cyc.value
+
+
+def ew_smoother_forward(grid: Grid, weights, r, y, stream=None):
+    import torch
+    check(lib.ew_smoother_forward(grid.handle, _ptr(weights, torch.float32, 432), _ptr(r, grid.dtype, grid.size),
+                                  _ptr(y, grid.dtype, grid.size), _stream(stream)))
+    return y
+
+
+def ew_smoother_backward(grid: Grid, weights, r, gy, grad, stream=None):
+    import torch
+    check(lib.ew_smoother_backward(grid.handle, _ptr(weights, torch.float32, 432), _ptr(r, grid.dtype, grid.size),
+                                   _ptr(gy, grid.dtype, grid.size), _ptr(grad, torch.float32, 432),
+                                   _stream(stream)))
+    return grad
+
+
+def ew_smoother_train(grid: Grid, half_dt2, weights, steps=200, samples=6, lr=1e-3, pre=2, post=2,
+                      jacobi_weight=0.8, seed=1, judge_cycles=6, stream=None):
+    """Train the learned smoother in place (weights: 432 FP32 CUDA tensor).
+    Returns the report as a dict."""
+    import torch
+    tp = _lib.ew_train_params(int(steps), int(samples), float(lr), int(pre), int(post), float(jacobi_weight),
+                              int(seed), int(judge_cycles))
+    rep = _lib.ew_train_report()
+    check(lib.ew_smoother_train(grid.handle, float(half_dt2), ctypes.byref(tp), _ptr(weights, torch.float32, 432),
+                                ctypes.byref(rep), _stream(stream)))
+    return dict(loss_first=rep.loss_first, loss_last=rep.loss_last, conv_plain=rep.conv_plain,
+                conv_learned=rep.conv_learned, accepted=bool(rep.accepted))
+
+
 def ew_profile_enable(on=True):
     check(lib.ew_profile_enable(int(bool(on))))
 

@@ -77,6 +77,18 @@ class ew_eigs_report(ctypes.Structure):
                 ("lambda_rel_change", ctypes.c_double * EW_MAX_EIGS)]
 
 
+class ew_train_params(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("samples", ctypes.c_int), ("lr", ctypes.c_double),
+                ("pre", ctypes.c_int), ("post", ctypes.c_int), ("jacobi_weight", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("judge_cycles", ctypes.c_int)]
+
+
+class ew_train_report(ctypes.Structure):
+    _fields_ = [("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double),
+                ("conv_plain", ctypes.c_double), ("conv_learned", ctypes.c_double),
+                ("accepted", ctypes.c_int)]
+
+
 class ew_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("fused_launches", ctypes.c_int64),
                 ("fused_ms", ctypes.c_double), ("fused_cell_steps", ctypes.c_int64),
@@ -100,8 +112,14 @@ lib.ew_profile_enable.argtypes = [_i]
 lib.ew_profile_read.argtypes = [ctypes.POINTER(ew_profile)]
 lib.ew_arnoldi_eigs.argtypes = [_vp, ctypes.POINTER(ew_filter_params), ctypes.POINTER(ew_eigs_params), _vp, _dp,
                                 _vp, ctypes.POINTER(ew_eigs_report), _vp]
+lib.ew_implicit_step_mg.argtypes = [_vp, _d, _vp, _vp, ctypes.POINTER(ew_mg_params), _dp, _ip, _vp]
+lib.ew_smoother_forward.argtypes = [_vp, _vp, _vp, _vp, _vp]
+lib.ew_smoother_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+lib.ew_smoother_train.argtypes = [_vp, _d, ctypes.POINTER(ew_train_params), _vp, ctypes.POINTER(ew_train_report),
+                                  _vp]
 for _name in ["ew_grid_create", "ew_filter_setup", "ew_filter_apply", "ew_apply_L", "ew_rayleigh",
-              "ew_power_iteration", "ew_profile_enable", "ew_profile_read", "ew_arnoldi_eigs"]:
+              "ew_power_iteration", "ew_profile_enable", "ew_profile_read", "ew_arnoldi_eigs",
+              "ew_implicit_step_mg", "ew_smoother_forward", "ew_smoother_backward", "ew_smoother_train"]:
     getattr(lib, _name).restype = ctypes.c_int
 
 

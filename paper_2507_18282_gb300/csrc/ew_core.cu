@@ -309,6 +309,7 @@ void ew_grid_destroy(ew_grid* g) {
     g->reduce.release();
     g->misc.release();
     g->mg.release();
+    g->mgh.release();
     if (g->host_pinned) cudaFreeHost(g->host_pinned);
     delete g;
 }

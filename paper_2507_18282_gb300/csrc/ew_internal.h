@@ -83,7 +83,8 @@ struct ew_grid {
     ew::Scratch fields;    // wave-solve time levels
     ew::Scratch reduce;    // reduction partials
     ew::Scratch misc;      // small device tables (filter weights)
-    ew::Scratch mg;        // multigrid hierarchy
+    ew::Scratch mg;        // power-iteration iterate
+    ew::Scratch mgh;       // multigrid hierarchy
     void* host_pinned = nullptr;  // small pinned staging for reductions
     size_t host_pinned_bytes = 0;
 };
@@ -142,6 +143,8 @@ ew_status launch_resid_inf(const T* Lx, const T* x, int64_t N, int nvec, const d
                            double* part, double* out_res, double* out_xinf, cudaStream_t st);
 template <typename T>
 ew_status launch_scale(T* x, int64_t N, int nvec, const double* s, cudaStream_t st);
+// y += alpha x (FP32)
+ew_status axpy_f(int64_t n, float alpha, const float* x, float* y, cudaStream_t st);
 // y = a * x + y with device scalar: y_j -= s_j * x_j
 template <typename T>
 ew_status launch_diffnorm_sign(const T* xnew, const T* xold, int64_t N, const double* beta,

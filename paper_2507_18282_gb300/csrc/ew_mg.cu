@@ -1,0 +1,570 @@
+// ew_mg.cu -- geometric multigrid for the implicit time-step systems and the
+// implicit wave-solve (eqs. implicitScheme, impMatrix, implicitStep1).
+//
+//   M x = b,   M = I - a L_h,   a = dt^2 / 2
+//
+// One V(pre, post) cycle (the paper solves these systems with its multigrid
+// solver and names red-black / line smoothers; this is the plain geometric
+// cycle for Cartesian boxes):
+//   levels      n_c = (n - 1) / 2 per axis while every axis has odd n >= 5
+//               (coarse point I on fine point 2I + 1, h_c = 2 h)
+//   smoother    damped Jacobi x <- x + w (b - M x) / D with the constant
+//               interior diagonal D = 1 + a sum_i d0 / h_i^2 (d0 = 2 or 5/2),
+//               or the learned correction x <- x + N(b - M x) on the finest
+//               `learned_levels` levels (ew_smoother.cu)
+//   restriction full weighting, tensor product of (1/4, 1/2, 1/4)
+//   prolongation (multi)linear interpolation, zero on the boundary
+//   coarsest    conjugate gradients in one CTA (M is SPD)
+//
+// Implicit wave-solve (one application of S):
+//   M W^1 = W^0;  M y = 2 W^n, W^{n+1} = y - W^{n-1};  V_out = sum c_n W^n
+// Each system gets `max_cycles` V-cycles from the initial guess y = 2 W^n
+// (W^1 = W^0 for the first step).
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ew_internal.h"
+#include "ew_stencil_dev.cuh"
+
+namespace ew {
+
+// learned correction x += N(r) (ew_smoother.cu)
+template <typename T>
+ew_status smoother_apply(const GridGeom& g, const float* weights, const T* r, T* x, cudaStream_t st);
+
+struct MGLevel {
+    GridGeom geom;
+};
+
+int mg_levels(const GridGeom& g, GridGeom* lv, int maxlev) {
+    int L = 0;
+    lv[0] = g;
+    for (;;) {
+        bool ok = L + 1 < maxlev;
+        for (int a = 0; a < g.dim; ++a)
+            if (lv[L].n[a] < 5 || (lv[L].n[a] % 2) == 0) ok = false;
+        if (!ok) break;
+        GridGeom c = lv[L];
+        c.N = 1;
+        for (int a = 0; a < 3; ++a) {
+            if (a < g.dim) {
+                c.n[a] = (lv[L].n[a] - 1) / 2;
+                c.h[a] = 2.0 * lv[L].h[a];
+            }
+            c.N *= c.n[a];
+        }
+        lv[++L] = c;
+    }
+    return L + 1;
+}
+
+static int grid_blocks(int64_t N, int threads) {
+    int64_t b = (N + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+// r = b - M x = b - x + a L x   (sa carries the scale a)
+template <typename T, int DIM, int ORDER>
+__global__ void k_mg_resid(int64_t nx, int64_t ny, int64_t nz, const T* __restrict__ x, const T* __restrict__ b,
+                           T* __restrict__ r, Stencil<T> sa) {
+    const int64_t N = nx * ny * nz;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q % nx, t = q / nx, j = t % ny, k = t / ny;
+        r[q] = (b[q] - x[q]) + lap_global<T, DIM, ORDER>(x, sa, q, i, j, k, nx, ny, nz);
+    }
+}
+
+// x_out = x_in + wd (b - M x_in), wd = w / D
+template <typename T, int DIM, int ORDER>
+__global__ void k_mg_jacobi(int64_t nx, int64_t ny, int64_t nz, const T* __restrict__ x, const T* __restrict__ b,
+                            T* __restrict__ xo, Stencil<T> sa, T wd) {
+    const int64_t N = nx * ny * nz;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q % nx, t = q / nx, j = t % ny, k = t / ny;
+        T r = (b[q] - x[q]) + lap_global<T, DIM, ORDER>(x, sa, q, i, j, k, nx, ny, nz);
+        xo[q] = x[q] + wd * r;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T get0(const T* __restrict__ v, int64_t i, int64_t j, int64_t k, int64_t nx, int64_t ny,
+                                  int64_t nz) {
+    if (i < 0 || j < 0 || k < 0 || i >= nx || j >= ny || k >= nz) return T(0);
+    return v[(k * ny + j) * nx + i];
+}
+
+// full weighting: bc(I) = sum_o w(o) r(2I + 1 + o); x_c = 0
+template <typename T, int DIM>
+__global__ void k_mg_restrict(int64_t fx, int64_t fy, int64_t fz, int64_t cx, int64_t cy, int64_t cz,
+                              const T* __restrict__ r, T* __restrict__ bc, T* __restrict__ xc) {
+    const int64_t N = cx * cy * cz;
+    const T w[3] = {T(0.25), T(0.5), T(0.25)};
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t I = q % cx, t = q / cx, J = t % cy, K = t / cy;
+        int64_t fi = 2 * I + 1, fj = 2 * J + 1, fk = DIM == 3 ? 2 * K + 1 : 0;
+        T s = T(0);
+        for (int oz = (DIM == 3 ? -1 : 0); oz <= (DIM == 3 ? 1 : 0); ++oz)
+            for (int oy = -1; oy <= 1; ++oy)
+                for (int ox = -1; ox <= 1; ++ox) {
+                    T wt = w[ox + 1] * w[oy + 1] * (DIM == 3 ? w[oz + 1] : T(1));
+                    s += wt * get0(r, fi + ox, fj + oy, fk + oz, fx, fy, fz);
+                }
+        bc[q] = s;
+        xc[q] = T(0);
+    }
+}
+
+// x_f += P e_c (linear interpolation per axis)
+template <typename T, int DIM>
+__global__ void k_mg_prolong(int64_t fx, int64_t fy, int64_t fz, int64_t cx, int64_t cy, int64_t cz,
+                             const T* __restrict__ ec, T* __restrict__ xf) {
+    const int64_t N = fx * fy * fz;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q % fx, t = q / fx, j = t % fy, k = t / fy;
+        int64_t ci[2], cj[2], ck[2];
+        T wi[2], wj[2], wk[2];
+        int ni, nj, nk;
+        if (i & 1) { ci[0] = (i - 1) / 2; wi[0] = T(1); ni = 1; }
+        else { ci[0] = i / 2 - 1; ci[1] = i / 2; wi[0] = wi[1] = T(0.5); ni = 2; }
+        if (j & 1) { cj[0] = (j - 1) / 2; wj[0] = T(1); nj = 1; }
+        else { cj[0] = j / 2 - 1; cj[1] = j / 2; wj[0] = wj[1] = T(0.5); nj = 2; }
+        if (DIM == 2) { ck[0] = 0; wk[0] = T(1); nk = 1; }
+        else if (k & 1) { ck[0] = (k - 1) / 2; wk[0] = T(1); nk = 1; }
+        else { ck[0] = k / 2 - 1; ck[1] = k / 2; wk[0] = wk[1] = T(0.5); nk = 2; }
+        T s = T(0);
+        for (int c3 = 0; c3 < nk; ++c3)
+            for (int c2 = 0; c2 < nj; ++c2)
+                for (int c1 = 0; c1 < ni; ++c1)
+                    s += wi[c1] * wj[c2] * wk[c3] * get0(ec, ci[c1], cj[c2], ck[c3], cx, cy, cz);
+        xf[q] += s;
+    }
+}
+
+// coarsest level: CG in one CTA, all vectors in shared memory (N <= kCoarseMax)
+constexpr int kCoarseMax = 2048;
+constexpr int kCoarseThreads = 512;
+
+template <typename T>
+__device__ T block_dot(const T* a, const T* b, int N, T* red) {
+    T s = T(0);
+    for (int q = threadIdx.x; q < N; q += blockDim.x) s += a[q] * b[q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    T t = T(0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+template <typename T, int DIM, int ORDER>
+__global__ void __launch_bounds__(kCoarseThreads)
+    k_mg_coarse_cg(int nx, int ny, int nz, const T* __restrict__ b, T* __restrict__ x, Stencil<T> sa, T rtol,
+                   int maxit) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = nx * ny * nz;
+    T* sx = reinterpret_cast<T*>(smem_raw);
+    T* sr = sx + N;
+    T* sp = sr + N;
+    T* sq = sp + N;
+    T* red = sq + N;
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+        sx[q] = T(0);
+        sr[q] = b[q];
+        sp[q] = b[q];
+    }
+    __syncthreads();
+    T rr = block_dot(sr, sr, N, red);
+    const T stop = rtol * rtol * rr;
+    for (int it = 0; it < maxit && rr > stop && rr > T(0); ++it) {
+        for (int q = threadIdx.x; q < N; q += blockDim.x) {
+            int i = q % nx, t = q / nx, j = t % ny, k = t / ny;
+            sq[q] = sp[q] - lap_global<T, DIM, ORDER>(sp, sa, q, i, j, k, nx, ny, nz);  // M p
+        }
+        __syncthreads();
+        T pq = block_dot(sp, sq, N, red);
+        if (!(pq > T(0))) break;
+        T alpha = rr / pq;
+        for (int q = threadIdx.x; q < N; q += blockDim.x) {
+            sx[q] += alpha * sp[q];
+            sr[q] -= alpha * sq[q];
+        }
+        __syncthreads();
+        T rr2 = block_dot(sr, sr, N, red);
+        T beta = rr2 / rr;
+        rr = rr2;
+        for (int q = threadIdx.x; q < N; q += blockDim.x) sp[q] = sr[q] + beta * sp[q];
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < N; q += blockDim.x) x[q] = sx[q];
+}
+
+template <typename T>
+__global__ void k_guess_rhs(int64_t N, const T* __restrict__ w, T* __restrict__ b, T* __restrict__ x, T sc) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
+        T v = sc * w[q];
+        b[q] = v;
+        x[q] = v;
+    }
+}
+
+// W^{n+1} = y - W^{n-1} (stored over W^{n-1}); acc += c W^{n+1}; first: acc = c0 W^0 + c1 W^1
+template <typename T>
+__global__ void k_implicit_update(int64_t N, const T* __restrict__ y, T* __restrict__ wprev, T* __restrict__ acc, T c) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
+        T wn = y[q] - wprev[q];
+        wprev[q] = wn;
+        acc[q] += c * wn;
+    }
+}
+template <typename T>
+__global__ void k_implicit_first(int64_t N, const T* __restrict__ w0, const T* __restrict__ w1, T* __restrict__ acc,
+                                 T c0, T c1) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
+        acc[q] = c0 * w0[q] + c1 * w1[q];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+template <typename T>
+struct MGSolver {
+    GridGeom lv[16];
+    int nlev = 0;
+    T* X[16];  // iterate (two buffers per level, X points at the current one)
+    T* Tm[16];
+    T* B[16];
+    T* R[16];
+    double a = 0.0;
+    const ew_mg_params* p = nullptr;
+    double wJ = 0.8;
+    cudaStream_t st = nullptr;
+
+    ew_status setup(ew_grid* g, double a_, const ew_mg_params* params, cudaStream_t s) {
+        a = a_;
+        p = params;
+        st = s;
+        wJ = params->jacobi_weight > 0 ? params->jacobi_weight : 0.8;
+        nlev = mg_levels(g->geom, lv, 16);
+        if (lv[nlev - 1].N > kCoarseMax)
+            return set_error(EW_EUNSUPPORTED, "multigrid needs axes that halve down to at most 2048 coarse points "
+                                              "(n = 2^k - 1 per axis, for example)");
+        if (params->learned_levels > 0 && g->geom.dim != 3)
+            return set_error(EW_EUNSUPPORTED, "the learned smoother is three-dimensional");
+        if (params->learned_levels > 0 && !params->weights_dev)
+            return set_error(EW_EINVAL, "learned_levels > 0 needs weights_dev");
+        size_t total = 0;
+        for (int L = 0; L < nlev; ++L) total += 4 * (size_t)lv[L].N;
+        EW_TRY(g->mgh.reserve(total * sizeof(T)));
+        T* base = (T*)g->mgh.ptr;
+        for (int L = 0; L < nlev; ++L) {
+            X[L] = base;
+            Tm[L] = base + lv[L].N;
+            B[L] = base + 2 * lv[L].N;
+            R[L] = base + 3 * lv[L].N;
+            base += 4 * lv[L].N;
+        }
+        return EW_OK;
+    }
+
+    double diag(int L) const {
+        double d0 = lv[L].order == 2 ? 2.0 : 2.5, s = 0.0;
+        for (int q = 0; q < lv[L].dim; ++q) s += d0 / (lv[L].h[q] * lv[L].h[q]);
+        return 1.0 + a * s;
+    }
+
+#define EW_MG_DISPATCH(KERN, GEOM, ...)                                                                  \
+    do {                                                                                                 \
+        const GridGeom& g_ = (GEOM);                                                                     \
+        dim3 grid_(grid_blocks(g_.N, 256));                                                              \
+        if (g_.dim == 2 && g_.order == 2) KERN<T, 2, 2><<<grid_, 256, 0, st>>>(g_.n[0], g_.n[1], 1, __VA_ARGS__); \
+        else if (g_.dim == 2) KERN<T, 2, 4><<<grid_, 256, 0, st>>>(g_.n[0], g_.n[1], 1, __VA_ARGS__);             \
+        else if (g_.order == 2) KERN<T, 3, 2><<<grid_, 256, 0, st>>>(g_.n[0], g_.n[1], g_.n[2], __VA_ARGS__);     \
+        else KERN<T, 3, 4><<<grid_, 256, 0, st>>>(g_.n[0], g_.n[1], g_.n[2], __VA_ARGS__);                        \
+        count_launch();                                                                                  \
+    } while (0)
+
+    ew_status smooth(int L, int steps) {
+        Stencil<T> sa = make_stencil<T>(lv[L], a);
+        for (int s = 0; s < steps; ++s) {
+            if (L < p->learned_levels) {
+                EW_MG_DISPATCH(k_mg_resid, lv[L], X[L], B[L], R[L], sa);
+                EW_TRY(smoother_apply<T>(lv[L], p->weights_dev + (size_t)L * 432, R[L], X[L], st));
+            } else {
+                T wd = (T)(wJ / diag(L));
+                EW_MG_DISPATCH(k_mg_jacobi, lv[L], X[L], B[L], Tm[L], sa, wd);
+                std::swap(X[L], Tm[L]);
+            }
+        }
+        return EW_OK;
+    }
+
+    ew_status coarse(int L) {
+        Stencil<T> sa = make_stencil<T>(lv[L], a);
+        const GridGeom& c = lv[L];
+        size_t smem = sizeof(T) * (4 * (size_t)c.N + 32);
+        T rtol = sizeof(T) == 4 ? T(1e-7) : T(1e-14);
+        int maxit = (int)std::min<int64_t>(4 * c.N + 10, 4000);
+        if (c.dim == 2 && c.order == 2)
+            k_mg_coarse_cg<T, 2, 2><<<1, kCoarseThreads, smem, st>>>((int)c.n[0], (int)c.n[1], 1, B[L], X[L], sa, rtol, maxit);
+        else if (c.dim == 2)
+            k_mg_coarse_cg<T, 2, 4><<<1, kCoarseThreads, smem, st>>>((int)c.n[0], (int)c.n[1], 1, B[L], X[L], sa, rtol, maxit);
+        else if (c.order == 2)
+            k_mg_coarse_cg<T, 3, 2><<<1, kCoarseThreads, smem, st>>>((int)c.n[0], (int)c.n[1], (int)c.n[2], B[L], X[L], sa, rtol, maxit);
+        else
+            k_mg_coarse_cg<T, 3, 4><<<1, kCoarseThreads, smem, st>>>((int)c.n[0], (int)c.n[1], (int)c.n[2], B[L], X[L], sa, rtol, maxit);
+        count_launch();
+        EW_CUDA_TRY(cudaGetLastError());
+        return EW_OK;
+    }
+
+    ew_status vcycle(int L) {
+        if (L == nlev - 1) return coarse(L);
+        EW_TRY(smooth(L, p->pre));
+        Stencil<T> sa = make_stencil<T>(lv[L], a);
+        EW_MG_DISPATCH(k_mg_resid, lv[L], X[L], B[L], R[L], sa);
+        const GridGeom &f = lv[L], &c = lv[L + 1];
+        if (f.dim == 2)
+            k_mg_restrict<T, 2><<<grid_blocks(c.N, 256), 256, 0, st>>>(f.n[0], f.n[1], f.n[2], c.n[0], c.n[1], c.n[2],
+                                                                      R[L], B[L + 1], X[L + 1]);
+        else
+            k_mg_restrict<T, 3><<<grid_blocks(c.N, 256), 256, 0, st>>>(f.n[0], f.n[1], f.n[2], c.n[0], c.n[1], c.n[2],
+                                                                      R[L], B[L + 1], X[L + 1]);
+        count_launch();
+        EW_TRY(vcycle(L + 1));
+        if (f.dim == 2)
+            k_mg_prolong<T, 2><<<grid_blocks(f.N, 256), 256, 0, st>>>(f.n[0], f.n[1], f.n[2], c.n[0], c.n[1], c.n[2],
+                                                                     X[L + 1], X[L]);
+        else
+            k_mg_prolong<T, 3><<<grid_blocks(f.N, 256), 256, 0, st>>>(f.n[0], f.n[1], f.n[2], c.n[0], c.n[1], c.n[2],
+                                                                     X[L + 1], X[L]);
+        count_launch();
+        EW_TRY(smooth(L, p->post));
+        EW_CUDA_TRY(cudaGetLastError());
+        return EW_OK;
+    }
+
+    // the current top-level iterate lives in X[0]; callers load b into B[0]
+    // and the initial guess into X[0]
+    ew_status cycles(int ncyc) {
+        for (int c = 0; c < ncyc; ++c) EW_TRY(vcycle(0));
+        return EW_OK;
+    }
+};
+
+template <typename T>
+static ew_status coarse_smem_attr() {
+    size_t smem = sizeof(T) * (4 * (size_t)kCoarseMax + 32);
+    EW_CUDA_TRY(cudaFuncSetAttribute(k_mg_coarse_cg<T, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    EW_CUDA_TRY(cudaFuncSetAttribute(k_mg_coarse_cg<T, 2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    EW_CUDA_TRY(cudaFuncSetAttribute(k_mg_coarse_cg<T, 3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    EW_CUDA_TRY(cudaFuncSetAttribute(k_mg_coarse_cg<T, 3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return EW_OK;
+}
+
+static ew_status check_mg(const ew_mg_params* mg) {
+    if (!mg) return set_error(EW_EINVAL, "the implicit scheme needs multigrid parameters (params->mg)");
+    if (mg->pre < 0 || mg->post < 0 || mg->pre + mg->post < 1) return set_error(EW_EINVAL, "bad smoothing counts");
+    if (mg->max_cycles < 1) return set_error(EW_EINVAL, "max_cycles must be >= 1");
+    if (mg->learned_levels < 0) return set_error(EW_EINVAL, "learned_levels < 0");
+    return EW_OK;
+}
+
+template <typename T>
+static ew_status implicit_wave_solve_t(ew_grid* g, const FilterPlan& plan, const ew_filter_params* p, const T* vin,
+                                       T* vout, int nvec, cudaStream_t st) {
+    EW_TRY(check_mg(p->mg));
+    EW_TRY(coarse_smem_attr<T>());
+    const int64_t N = g->geom.N;
+    MGSolver<T> mg;
+    EW_TRY(mg.setup(g, 0.5 * plan.dt * plan.dt, p->mg, st));
+    EW_TRY(g->fields.reserve(2 * (size_t)N * sizeof(T)));
+    T* Wm = (T*)g->fields.ptr;  // W^{n-1}
+    T* W0 = Wm + N;             // W^n
+    const int blocks = grid_blocks(N, 256);
+    for (int v = 0; v < nvec; ++v) {
+        const T* x = vin + (size_t)v * N;
+        T* acc = vout + (size_t)v * N;
+        // W^0 = V; M W^1 = W^0 (initial guess W^0)
+        EW_CUDA_TRY(cudaMemcpyAsync(Wm, x, N * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        k_guess_rhs<T><<<blocks, 256, 0, st>>>(N, x, mg.B[0], mg.X[0], T(1));
+        count_launch();
+        EW_TRY(mg.cycles(p->mg->max_cycles));
+        EW_CUDA_TRY(cudaMemcpyAsync(W0, mg.X[0], N * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        k_implicit_first<T><<<blocks, 256, 0, st>>>(N, Wm, W0, acc, (T)plan.c[0], (T)plan.c[1]);
+        count_launch();
+        for (int64_t n = 1; n < plan.Nt; ++n) {
+            // M y = 2 W^n from y = 2 W^n; W^{n+1} = y - W^{n-1} over W^{n-1}
+            k_guess_rhs<T><<<blocks, 256, 0, st>>>(N, W0, mg.B[0], mg.X[0], T(2));
+            count_launch();
+            EW_TRY(mg.cycles(p->mg->max_cycles));
+            k_implicit_update<T><<<blocks, 256, 0, st>>>(N, mg.X[0], Wm, acc, (T)plan.c[(size_t)n + 1]);
+            count_launch();
+            std::swap(Wm, W0);
+        }
+    }
+    EW_CUDA_TRY(cudaGetLastError());
+    return EW_OK;
+}
+
+ew_status implicit_wave_solve_any(ew_grid* g, const FilterPlan& plan, const ew_filter_params* p, const void* vin,
+                                  void* vout, int nvec, cudaStream_t st) {
+    if (g->prec == EW_FP32)
+        return implicit_wave_solve_t<float>(g, plan, p, (const float*)vin, (float*)vout, nvec, st);
+    return implicit_wave_solve_t<double>(g, plan, p, (const double*)vin, (double*)vout, nvec, st);
+}
+
+template <typename T>
+ew_status launch_dots(const T* x, const T* y, int64_t N, int nvec, double* part, double* out, cudaStream_t st);
+
+template <typename T>
+static ew_status step_mg_t(ew_grid* g, double a, const T* rhs, T* x, const ew_mg_params* mp, double* conv,
+                           int* cycles_done, cudaStream_t st) {
+    EW_TRY(check_mg(mp));
+    EW_TRY(coarse_smem_attr<T>());
+    const int64_t N = g->geom.N;
+    MGSolver<T> mg;
+    EW_TRY(mg.setup(g, a, mp, st));
+    EW_TRY(g->reduce.reserve(sizeof(double) * (kReduceBlocks + 8)));
+    double* dpart = (double*)g->reduce.ptr;
+    double* dres = dpart + kReduceBlocks;
+    EW_CUDA_TRY(cudaMemcpyAsync(mg.B[0], rhs, N * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    EW_CUDA_TRY(cudaMemcpyAsync(mg.X[0], x, N * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    Stencil<T> sa = make_stencil<T>(g->geom, a);
+    auto resid_norm = [&](double* out) -> ew_status {
+        T* r = mg.R[0];
+        {
+            const GridGeom& gg = g->geom;
+            dim3 grid_(grid_blocks(gg.N, 256));
+            if (gg.dim == 2 && gg.order == 2) k_mg_resid<T, 2, 2><<<grid_, 256, 0, st>>>(gg.n[0], gg.n[1], 1, mg.X[0], mg.B[0], r, sa);
+            else if (gg.dim == 2) k_mg_resid<T, 2, 4><<<grid_, 256, 0, st>>>(gg.n[0], gg.n[1], 1, mg.X[0], mg.B[0], r, sa);
+            else if (gg.order == 2) k_mg_resid<T, 3, 2><<<grid_, 256, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
+            else k_mg_resid<T, 3, 4><<<grid_, 256, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
+            count_launch();
+        }
+        EW_TRY(launch_dots<T>(r, r, N, 1, dpart, dres, st));
+        double h = 0.0;
+        EW_CUDA_TRY(cudaMemcpyAsync(&h, dres, sizeof(double), cudaMemcpyDeviceToHost, st));
+        EW_CUDA_TRY(cudaStreamSynchronize(st));
+        *out = sqrt(h);
+        return EW_OK;
+    };
+    double bnorm = 0.0, r0 = 0.0, rk = 0.0;
+    EW_TRY(launch_dots<T>(rhs, rhs, N, 1, dpart, dres, st));
+    EW_CUDA_TRY(cudaMemcpyAsync(&bnorm, dres, sizeof(double), cudaMemcpyDeviceToHost, st));
+    EW_CUDA_TRY(cudaStreamSynchronize(st));
+    bnorm = sqrt(bnorm);
+    EW_TRY(resid_norm(&r0));
+    rk = r0;
+    int c = 0;
+    for (c = 0; c < mp->max_cycles; ++c) {
+        if (mp->rtol > 0 && rk <= mp->rtol * bnorm) break;
+        EW_TRY(mg.vcycle(0));
+        if (mp->rtol > 0 || c + 1 == mp->max_cycles) EW_TRY(resid_norm(&rk));
+    }
+    EW_CUDA_TRY(cudaMemcpyAsync(x, mg.X[0], N * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    EW_CUDA_TRY(cudaStreamSynchronize(st));
+    if (conv) *conv = (c > 0 && r0 > 0) ? pow(rk / r0, 1.0 / c) : 0.0;
+    if (cycles_done) *cycles_done = c;
+    if (mp->rtol > 0 && rk > mp->rtol * bnorm) return set_error(EW_ENOCONV, "multigrid did not reach rtol");
+    return EW_OK;
+}
+
+ew_status splitmix_uniform(int64_t n, uint64_t seed, double* out, cudaStream_t st);
+template <typename S, typename D>
+ew_status convert(int64_t n, const S* x, D* y, cudaStream_t st);
+
+// Residual samples for training the learned smoother: for rhs number q
+// (uniform [-1,1) from SplitMix64 stream seed + q) plain V-cycles run from
+// x = 0, and the residual b - M x the finest-level smoother sees at the start
+// of cycles 0, 1, 2 is recorded, until nsamples residuals (FP32) are stored.
+ew_status mg_collect_residuals(ew_grid* g, double a, const ew_mg_params* mp, int nsamples, uint64_t seed, float* out,
+                               cudaStream_t st) {
+    EW_TRY(check_mg(mp));
+    EW_TRY(coarse_smem_attr<float>());
+    const int64_t N = g->geom.N;
+    MGSolver<float> mg;
+    EW_TRY(mg.setup(g, a, mp, st));
+    double* tmp = nullptr;
+    EW_CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * (size_t)N));
+    Stencil<float> sa = make_stencil<float>(g->geom, a);
+    ew_status s = EW_OK;
+    int k = 0;
+    for (uint64_t q = 0; k < nsamples && s == EW_OK; ++q) {
+        s = splitmix_uniform(N, seed + q, tmp, st);
+        if (s == EW_OK) s = convert<double, float>(N, tmp, mg.B[0], st);
+        if (s != EW_OK) break;
+        cudaMemsetAsync(mg.X[0], 0, sizeof(float) * N, st);
+        for (int c = 0; c < 3 && k < nsamples && s == EW_OK; ++c) {
+            float* r = out + (size_t)k * N;
+            const GridGeom& gg = g->geom;
+            dim3 grid_(grid_blocks(gg.N, 256));
+            if (gg.order == 2)
+                k_mg_resid<float, 3, 2><<<grid_, 256, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
+            else
+                k_mg_resid<float, 3, 4><<<grid_, 256, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
+            count_launch();
+            ++k;
+            s = mg.vcycle(0);
+        }
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(tmp);
+    return s;
+}
+
+// Convergence factor of ncycles V-cycles on M x = b, b uniform [-1,1) from
+// stream seed, x = 0: (||r_n|| / ||r_1||)^(1 / (n - 1)), skipping the first
+// cycle's transient.
+ew_status mg_convergence(ew_grid* g, double a, const ew_mg_params* mp, int ncycles, uint64_t seed, double* rho,
+                         cudaStream_t st) {
+    const int64_t N = g->geom.N;
+    float *b = nullptr, *x = nullptr;
+    double* tmp = nullptr;
+    EW_CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * (size_t)N));
+    EW_CUDA_TRY(cudaMalloc(&b, sizeof(float) * (size_t)N));
+    EW_CUDA_TRY(cudaMalloc(&x, sizeof(float) * (size_t)N));
+    ew_status s = splitmix_uniform(N, seed, tmp, st);
+    if (s == EW_OK) s = convert<double, float>(N, tmp, b, st);
+    cudaMemsetAsync(x, 0, sizeof(float) * N, st);
+    ew_mg_params one = *mp;
+    one.max_cycles = 1;
+    one.rtol = 0.0;
+    double c1 = 0.0;
+    if (s == EW_OK) s = step_mg_t<float>(g, a, b, x, &one, &c1, nullptr, st);  // r_1 / r_0
+    ew_mg_params rest = *mp;
+    rest.max_cycles = std::max(1, ncycles - 1);
+    rest.rtol = 0.0;
+    double cr = 0.0;
+    if (s == EW_OK) s = step_mg_t<float>(g, a, b, x, &rest, &cr, nullptr, st);
+    cudaStreamSynchronize(st);
+    cudaFree(tmp);
+    cudaFree(b);
+    cudaFree(x);
+    *rho = cr;
+    return s;
+}
+
+}  // namespace ew
+
+using namespace ew;
+
+extern "C" ew_status ew_implicit_step_mg(const ew_grid* grid, double half_dt2, const void* rhs, void* x,
+                                         const ew_mg_params* mg, double* conv_factor, int* cycles_done,
+                                         cudaStream_t stream) {
+    clear_error();
+    if (!grid || !rhs || !x || !mg) return set_error(EW_EINVAL, "null argument");
+    if (!(half_dt2 >= 0.0)) return set_error(EW_EINVAL, "half_dt2 must be >= 0");
+    int dev = -1;
+    EW_CUDA_TRY(cudaGetDevice(&dev));
+    if (grid->device >= 0 && grid->device != dev) return set_error(EW_EINVAL, "grid was created on another device");
+    ew_grid* g = const_cast<ew_grid*>(grid);
+    if (g->prec == EW_FP32)
+        return step_mg_t<float>(g, half_dt2, (const float*)rhs, (float*)x, mg, conv_factor, cycles_done, stream);
+    return step_mg_t<double>(g, half_dt2, (const double*)rhs, (double*)x, mg, conv_factor, cycles_done, stream);
+}

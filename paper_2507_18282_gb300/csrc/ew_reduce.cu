@@ -135,6 +135,18 @@ ew_status launch_scale(T* x, int64_t N, int nvec, const double* s, cudaStream_t 
 template ew_status launch_scale<float>(float*, int64_t, int, const double*, cudaStream_t);
 template ew_status launch_scale<double>(double*, int64_t, int, const double*, cudaStream_t);
 
+__global__ void k_axpy_f(int64_t n, float alpha, const float* __restrict__ x, float* __restrict__ y) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        y[q] += alpha * x[q];
+}
+
+ew_status axpy_f(int64_t n, float alpha, const float* x, float* y, cudaStream_t st) {
+    k_axpy_f<<<kReduceBlocks * 4, 256, 0, st>>>(n, alpha, x, y);
+    EW_CUDA_TRY(cudaGetLastError());
+    count_launch();
+    return EW_OK;
+}
+
 // ||xnew - sign(beta) xold||_2^2 (one vector)
 template <typename T>
 __global__ void __launch_bounds__(256) k_diff_sign(const T* __restrict__ a, const T* __restrict__ b, int64_t N,

@@ -114,3 +114,15 @@ def test_conv_net_gradient_matches_finite_differences():
         wm[idx] -= eps
         fd = (O.smoother_loss(g, a, wp, r)[0] - O.smoother_loss(g, a, wm, r)[0]) / (2 * eps)
         assert abs(fd - gw[idx]) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_implicit_filter_with_multigrid_tends_to_exact():
+    """The multigrid-based implicit wave-solve converges to the exactly solved
+    one as the V-cycles per system grow."""
+    g = O.Grid((15, 15, 15), (1.0, 1.0, 1.0), 4)
+    prm = O.filter_params(12.0, 1, 10, adjust=True)
+    v = ew_inputs.uniform_pm1(41, g.size)
+    exact = O.filter_implicit(g, prm, v)
+    e2 = np.max(np.abs(O.filter_implicit_mg(g, prm, v, ncycles=2) - exact))
+    e12 = np.max(np.abs(O.filter_implicit_mg(g, prm, v, ncycles=12) - exact))
+    assert e12 < 1e-9 and e12 < e2 / 1e5
