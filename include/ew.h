@@ -145,6 +145,19 @@ ew_status ew_filter_setup(const ew_grid* grid, const ew_filter_params* params,
 ew_status ew_filter_apply(const ew_grid* grid, const ew_filter_params* params, const void* v_in_dev,
                           void* v_out_dev, int nvec, cudaStream_t stream);
 
+/* v_out[q] = S_q v_in[q] for nprob independent problems (each with its own
+ * grid and filter parameters: uneven boxes, their own omega, time step and
+ * N_t).  nvec (may be NULL = all 1) gives the vectors per problem.  2D
+ * explicit problems of one precision and one order run together: the work of
+ * every problem is cut into rounds of a few time steps, each round is one
+ * persistent launch over all unfinished problems' tiles, and the whole
+ * sequence is one CUDA graph replayed on `stream`; the tile shape is
+ * autotuned once per batch shape.  Other mixes run one ew_filter_apply per
+ * problem.  The batched workspace is process-wide: calls must not overlap. */
+ew_status ew_filter_apply_batched(int nprob, const ew_grid* const* grids, const ew_filter_params* params,
+                                  const void* const* v_in_dev, void* const* v_out_dev, const int* nvec,
+                                  cudaStream_t stream);
+
 /* Lu = L_h u for nvec vectors (grid precision, device). */
 ew_status ew_apply_L(const ew_grid* grid, const void* u_dev, void* Lu_dev, int nvec,
                      cudaStream_t stream);

@@ -121,6 +121,18 @@ def ew_filter_apply(grid: Grid, params, v_in, v_out, nvec=None, stream=None):
     return v_out
 
 
+def ew_filter_apply_batched(grids, params, v_in, v_out, nvec=None, stream=None):
+    """v_out[q] = S_q v_in[q] for every problem q in one graph-captured launch sequence."""
+    n = len(grids)
+    G = (ctypes.c_void_p * n)(*[g.handle.value if hasattr(g.handle, "value") else g.handle for g in grids])
+    P = (ew_filter_params * n)(*params)
+    vi = (ctypes.c_void_p * n)(*[_ptr(v_in[q], grids[q].dtype, grids[q].size).value for q in range(n)])
+    vo = (ctypes.c_void_p * n)(*[_ptr(v_out[q], grids[q].dtype, grids[q].size).value for q in range(n)])
+    nv = (ctypes.c_int * n)(*(nvec if nvec is not None else [1] * n))
+    check(lib.ew_filter_apply_batched(n, G, P, vi, vo, nv, _stream(stream)))
+    return v_out
+
+
 def ew_apply_L(grid: Grid, u, Lu, nvec=None, stream=None):
     nvec = nvec if nvec is not None else max(1, u.numel() // grid.size)
     check(lib.ew_apply_L(grid.handle, _ptr(u, grid.dtype, nvec * grid.size),

@@ -240,7 +240,7 @@ static size_t resident_smem(const GridGeom& g) {
 }
 
 template <typename T>
-static ew_status first_step(const GridGeom& g, const T* vin, T* W0, T* W1, T* vout,
+ew_status first_step(const GridGeom& g, const T* vin, T* W0, T* W1, T* vout,
                             const FilterPlan& plan, int nvec, int64_t fstride, cudaStream_t st) {
     Stencil<T> s = make_stencil<T>(g, 0.5 * plan.dt * plan.dt);
     dim3 grid(grid_blocks(g.N, 256), nvec);
@@ -335,4 +335,11 @@ template ew_status explicit_wave_solve<float>(const GridGeom&, const FilterPlan&
 template ew_status explicit_wave_solve<double>(const GridGeom&, const FilterPlan&, const double*,
                                                const double*, double*, int, double*, int, cudaStream_t);
 
+}  // namespace ew
+
+namespace ew {
+template ew_status first_step<float>(const GridGeom&, const float*, float*, float*, float*, const FilterPlan&, int,
+                                     int64_t, cudaStream_t);
+template ew_status first_step<double>(const GridGeom&, const double*, double*, double*, double*, const FilterPlan&,
+                                      int, int64_t, cudaStream_t);
 }  // namespace ew
