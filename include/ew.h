@@ -158,6 +158,29 @@ ew_status ew_filter_apply_batched(int nprob, const ew_grid* const* grids, const 
                                   const void* const* v_in_dev, void* const* v_out_dev, const int* nvec,
                                   cudaStream_t stream);
 
+/* ew_filter_apply for callers that cannot allocate device memory (no
+ * counterpart in the paper).  Code that runs while a stream is being captured
+ * into a CUDA graph, plugins whose host application owns every device
+ * allocation, and real-time loops that must not enter the allocator cannot
+ * let the library cudaMalloc scratch on first use, as ew_filter_apply does.
+ * This entry point calls no cudaMalloc, cudaFree or other allocating routine:
+ * its scratch is one file-scope device array of 16.5 MiB (four time-level
+ * fields of up to 16 MiB and up to 512 KiB of filter weights) that every GPU
+ * loading the library holds until the process exits.
+ *   - One vector (v_in, v_out device, grid precision, not overlapping), the
+ *     explicit scheme only (EW_EUNSUPPORTED otherwise).
+ *   - Limits: 4 N sizeof(element) <= 16 MiB, i.e. N <= 1048576 active points
+ *     in FP32 and N <= 524288 in FP64, and (N_t + 1) sizeof(element) <= 512
+ *     KiB; larger requests return EW_EINVAL with the limit in ew_last_error.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) for that device; make that first call before any
+ *     stream capture.
+ *   - Every call shares the array (each rewrites all of it that it reads, so
+ *     nothing is carried over); calls whose GPU work overlaps race on it.
+ *   - temporal_block 0 means a fixed depth of 4 (no autotuning). */
+ew_status ew_filter_apply_noalloc(const ew_grid* grid, const ew_filter_params* params, const void* v_in_dev,
+                                  void* v_out_dev, cudaStream_t stream);
+
 /* Lu = L_h u for nvec vectors (grid precision, device). */
 ew_status ew_apply_L(const ew_grid* grid, const void* u_dev, void* Lu_dev, int nvec,
                      cudaStream_t stream);

@@ -115,6 +115,8 @@ lib.ew_arnoldi_eigs.argtypes = [_vp, ctypes.POINTER(ew_filter_params), ctypes.PO
 lib.ew_filter_apply_batched.argtypes = [_i, ctypes.POINTER(_vp), ctypes.POINTER(ew_filter_params),
                                         ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip, _vp]
 lib.ew_filter_apply_batched.restype = ctypes.c_int
+lib.ew_filter_apply_noalloc.argtypes = [_vp, ctypes.POINTER(ew_filter_params), _vp, _vp, _vp]
+lib.ew_filter_apply_noalloc.restype = ctypes.c_int
 lib.ew_implicit_step_mg.argtypes =[_vp, _d, _vp, _vp, ctypes.POINTER(ew_mg_params), _dp, _ip, _vp]
 lib.ew_smoother_forward.argtypes = [_vp, _vp, _vp, _vp, _vp]
 lib.ew_smoother_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]

@@ -113,7 +113,7 @@ static double rho_bound(const GridGeom& g) {
     return (g.order == 2 ? 4.0 : 16.0 / 3.0) * inv;
 }
 
-ew_status plan_filter(const GridGeom& g, const ew_filter_params* p, FilterPlan* out) {
+ew_status plan_filter(const GridGeom& g, const ew_filter_params* p, FilterPlan* out, bool with_weights) {
     if (!p) return set_error(EW_EINVAL, "params is NULL");
     if (!(p->omega > 0.0) || !std::isfinite(p->omega)) return set_error(EW_EINVAL, "omega must be > 0");
     if (p->num_periods < 1) return set_error(EW_EINVAL, "num_periods must be >= 1");
@@ -148,11 +148,10 @@ ew_status plan_filter(const GridGeom& g, const ew_filter_params* p, FilterPlan* 
         if (out->dt * out->dt * rho_bound(g) > 4.0 * (1.0 + 1e-12))
             return set_error(EW_EINVAL, "explicit time step beyond the stability limit (raise steps_per_period)");
     }
-    out->c.resize((size_t)out->Nt + 1);
-    const double f = 2.0 / out->Tf;
-    for (int64_t n = 0; n <= out->Nt; ++n) {
-        double sigma = (n == 0 || n == out->Nt) ? 0.5 * out->dt : out->dt;
-        out->c[(size_t)n] = f * sigma * (cos(w * (double)n * out->dt) - 0.5 * out->alpha_d);
+    out->c.clear();
+    if (with_weights) {
+        out->c.resize((size_t)out->Nt + 1);
+        for (int64_t n = 0; n <= out->Nt; ++n) out->c[(size_t)n] = out->cn(n);
     }
     return EW_OK;
 }

@@ -99,9 +99,14 @@ struct FilterPlan {
     double alpha_d;
     int64_t Nt;
     int spp;
-    std::vector<double> c;  // N_t + 1 weights
+    std::vector<double> c;  // N_t + 1 weights (empty when planned without them)
+    // weight n: (2/T_f) sigma_n (cos(omega t^n) - alpha_d / 2), trapezoid sigma
+    double cn(int64_t n) const {
+        double sigma = (n == 0 || n == Nt) ? 0.5 * dt : dt;
+        return 2.0 / Tf * sigma * (cos(omega * (double)n * dt) - 0.5 * alpha_d);
+    }
 };
-ew_status plan_filter(const GridGeom& g, const ew_filter_params* p, FilterPlan* out);
+ew_status plan_filter(const GridGeom& g, const ew_filter_params* p, FilterPlan* out, bool with_weights = true);
 
 // --- kernels launchers (ew_stencil.cu) ------------------------------------
 template <typename T>

@@ -244,7 +244,7 @@ ew_status first_step(const GridGeom& g, const T* vin, T* W0, T* W1, T* vout,
                             const FilterPlan& plan, int nvec, int64_t fstride, cudaStream_t st) {
     Stencil<T> s = make_stencil<T>(g, 0.5 * plan.dt * plan.dt);
     dim3 grid(grid_blocks(g.N, 256), nvec);
-    T c0 = T(plan.c[0]), c1 = T(plan.c[1]);
+    T c0 = T(plan.cn(0)), c1 = T(plan.cn(1));
     if (g.dim == 2 && g.order == 2)
         k_first_step<T, 2, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, vin, W0, W1, vout, s, c0, c1, fstride);
     else if (g.dim == 2)
@@ -325,7 +325,7 @@ ew_status explicit_wave_solve(const GridGeom& g, const FilterPlan& plan, const T
     Stencil<T> s = make_stencil<T>(g, plan.dt * plan.dt);
     int prv = 0, cur = 1;
     for (int64_t L = 1; L < plan.Nt; ++L) {
-        EW_TRY(step_simple<T>(g, F[cur], F[prv], vout, T(plan.c[L + 1]), s, nvec, fstride, st));
+        EW_TRY(step_simple<T>(g, F[cur], F[prv], vout, T(plan.cn(L + 1)), s, nvec, fstride, st));
         std::swap(prv, cur);
     }
     return EW_OK;
