@@ -49,7 +49,8 @@ UNIT = "Gcell-steps/s"
 BYTES_PER_POINT_PER_LAUNCH = 24  # 6 x FP32: W^{n-1}, W^n, acc in; W^{n+b-1}, W^{n+b}, acc out
 DOMINANT_KERNEL = "k_step_tb2d"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_2507_18282_gb300", "csrc", "ew_tb2d.cu")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2507_18282_gb300", "csrc", f)
+                  for f in ("ew_tb2d_dev.cuh", "ew_tb2d.cu")]
 
 
 def parse():
@@ -61,6 +62,9 @@ def parse():
     ap.add_argument("--temporal-block", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--workload", choices=["rect2d", "cube3d", "batched", "implicit3d", "eigs2d"], default="rect2d",
+                    help="rect2d is the headline line; the others print their own line")
+    ap.add_argument("--num-periods", type=int, default=256, help="N_p of the eigs2d workload")
     return ap.parse_args()
 
 
@@ -129,12 +133,19 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
 def traffic_for_kernel():
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, or None when the kernel source changed since it was taken."""
     try:
         t = json.load(open(TRAFFIC_FILE))
-        src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+        src = kernel_source_hash()
         if t.get("kernel_source_sha256") != src:
             return None
         return t.get("dram_bytes_per_launch")
@@ -338,10 +349,135 @@ def run_ours(args):
     return 0
 
 
+def _timed(fn, steps, warmup, flush):
+    """Device time (ms) of `steps` calls of fn, L2 flushed before each."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    total = 0.0
+    for k in range(steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b)
+    return total
+
+
+def run_extra(args):
+    """The other workloads, one JSON line each (reported beside the default line)."""
+    import numpy as np
+    import torch
+
+    import ew_inputs
+    import paper_2507_18282_gb300 as ew
+    torch.cuda.set_device(0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    pk, pk_kind = peaks()
+    w = args.workload
+    if w == "cube3d":
+        n, L = (511, 511, 511), (1.0, 1.0, 1.0)
+        g = ew.ew_grid_create(3, n, L, order=2, prec="fp32")
+        p = ew.filter_params(60.0, num_periods=1)
+        info, _ = ew.ew_filter_setup(g, p)
+        v = torch.tensor(ew_inputs.uniform_pm1(ew_inputs.BASE_SEED + 2, g.size), dtype=torch.float32, device="cuda")
+        o = torch.empty_like(v)
+        ew.ew_profile_enable(True)
+        ms = _timed(lambda: ew.ew_filter_apply(g, p, v, o), args.steps, args.warmup, flush)
+        prof = ew.ew_profile_read()
+        ew.ew_profile_enable(False)
+        cells = g.size * info["Nt"] * args.steps
+        launches = max(prof["fused_launches"], 1)
+        mean = prof["fused_ms"] / launches
+        bytes_launch = 20 * prof["fused_points"] / launches  # one step per launch: W^{n-1}, W^n, acc in; W^{n+1}, acc out
+        line = dict(workload="cube3d_511_order2_fp32_explicit", metric=METRIC, unit=UNIT,
+                    value=cells / (ms / 1e3) / 1e9, ms_per_step=ms / args.steps, time_steps_per_step=info["Nt"],
+                    roofline=dict(bound="hbm", kernel="k_step_simple<float,3,2>", bytes_per_launch=bytes_launch,
+                                  achieved=bytes_launch / (mean / 1e3) / 1e9, peak=pk["hbm_gbs"], unit="GB/s",
+                                  frac=bytes_launch / (mean / 1e3) / 1e9 / pk["hbm_gbs"], peak_source=pk_kind))
+    elif w == "batched":
+        boxes = ew_inputs.batched_boxes(ew_inputs.BASE_SEED + 3)
+        grids, params, vin, vout = [], [], [], []
+        cells = 0
+        for q, b in enumerate(boxes):
+            g = ew.ew_grid_create(2, b["n"], b["length"], order=2, prec="fp32")
+            p = ew.filter_params(b["omega"], num_periods=1)
+            info, _ = ew.ew_filter_setup(g, p)
+            cells += g.size * info["Nt"]
+            grids.append(g)
+            params.append(p)
+            vin.append(torch.tensor(ew_inputs.uniform_pm1(200 + q, g.size), dtype=torch.float32, device="cuda"))
+            vout.append(torch.empty_like(vin[-1]))
+        ms = _timed(lambda: ew.ew_filter_apply_batched(grids, params, vin, vout), args.steps, args.warmup, flush)
+        line = dict(workload="batched_64_boxes_255_to_2047_order2_fp32", metric=METRIC, unit=UNIT,
+                    value=cells * args.steps / (ms / 1e3) / 1e9, ms_per_step=ms / args.steps,
+                    problems=len(boxes), cell_steps_per_step=cells)
+    elif w == "implicit3d":
+        from oracle import oracle as O  # noqa: F401  (not used on the timed path)
+        n, L = (255, 255, 255), (1.0, 1.0, 1.0)
+        g = ew.ew_grid_create(3, n, L, order=4, prec="fp32")
+        res = {}
+        wts = torch.tensor(ew_inputs.learned_init(36, 0.05), dtype=torch.float32, device="cuda")
+        probe = ew.filter_params(80.0, num_periods=1, steps_per_period=10, scheme="implicit", adjust_omega=True,
+                                 mg=ew.mg_params())
+        info, _ = ew.ew_filter_setup(g, probe)
+        a = 0.5 * info["dt"] ** 2
+        t0 = time.time()
+        rep = ew.ew_smoother_train(g, a, wts, steps=600, samples=12, lr=5e-3, seed=5)
+        train_s = time.time() - t0
+        v = torch.tensor(ew_inputs.uniform_pm1(ew_inputs.BASE_SEED + 4, g.size), dtype=torch.float32, device="cuda")
+        o = torch.empty_like(v)
+        for name, learned, cyc in [("plain", 0, 4), ("learned", 1 if rep["accepted"] else 0, 2)]:
+            mg = ew.mg_params(pre=2, post=2, max_cycles=cyc, learned_levels=learned,
+                              weights=wts if learned else None)
+            p = ew.filter_params(80.0, num_periods=1, steps_per_period=10, scheme="implicit", adjust_omega=True, mg=mg)
+            ms = _timed(lambda: ew.ew_filter_apply(g, p, v, o), max(1, args.steps // 4), 1, flush)
+            x = torch.zeros_like(v)
+            one = ew.mg_params(pre=2, post=2, max_cycles=1, learned_levels=learned, weights=wts if learned else None)
+            t = _timed(lambda: ew.ew_implicit_step_mg(g, a, v, x, one), 5, 1, flush)
+            res[name] = dict(ms_per_wave_solve=ms / max(1, args.steps // 4), cycles_per_system=cyc,
+                             ms_per_vcycle=t / 5,
+                             gcell_steps_per_s=g.size * info["Nt"] / (ms / max(1, args.steps // 4) / 1e3) / 1e9)
+        line = dict(workload="implicit3d_255_order4_fp32_mg_v22", unit="ms", train=rep, train_seconds=train_s,
+                    plain=res["plain"], learned=res["learned"])
+    elif w == "eigs2d":
+        # time to the 8 eigenpairs nearest omega = 150 on the 2047 x 3071 order-4 rectangle:
+        # FP32 wave-solves + FP64 refinement against FP64 wave-solves throughout
+        n, L = (2047, 3071), (1.0, 1.5)
+        runs = {}
+        for name, prec, refine, tol in [("fp32_fp64_refine", "fp32", 1, 0.0), ("plain_fp64", "fp64", 0, 1e-10)]:
+            g = ew.ew_grid_create(2, n, L, order=4, prec=prec)
+            p = ew.filter_params(150.0, num_periods=args.num_periods)
+            e = ew.eigs_params(8, krylov_dim=32, block=4, tol=tol, seed=7, refine_fp64=refine,
+                               max_wave_solves=600)
+            torch.cuda.synchronize()
+            t0 = time.time()
+            lam, rep, st = ew.ew_arnoldi_eigs(g, p, e, allow_noconv=True)
+            torch.cuda.synchronize()
+            runs[name] = dict(seconds=time.time() - t0, status=int(st), wave_solves=rep["wave_solves"],
+                              wave_solves_fp64=rep["wave_solves_fp64"], max_eig_res=float(rep["eig_res"].max()),
+                              lambda_=sorted(float(x) for x in lam))
+            g.close()
+        line = dict(workload="eigs_rect2d_2047x3071_order4_8_nearest_omega150", unit="s",
+                    num_periods=args.num_periods, metric="s to 8 eigenpairs at 1e-8 resid vs plain", runs=runs,
+                    speedup=runs["plain_fp64"]["seconds"] / runs["fp32_fp64_refine"]["seconds"])
+    else:
+        raise SystemExit("unknown workload %s" % w)
+    line.update(dict(n_gpus=1, steps=args.steps, warmup=args.warmup, dtype="f32", data="synthetic",
+                     l2="flushed between timed steps (512 MB write)"))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "rect2d":
+        return run_extra(args)
     return run_ours(args)
 
 
