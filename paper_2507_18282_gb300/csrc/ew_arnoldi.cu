@@ -428,36 +428,68 @@ static double filter_beta(const FilterPlan& plan, ew_scheme scheme, double lam) 
 // extreme ones) improves X by several digits per outer step.  A last
 // Rayleigh-Ritz with L_h inside span[X] separates near-degenerate pairs.
 // kr is an FP32 Krylov-Schur run with block nw and basis (1 + p) nw.
-static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, int p, int max_outer, double ritz_tol,
+static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, int p, int max_outer, double res_tol,
                            std::vector<double>& lam_out, std::vector<double>& beta_out,
                            std::vector<double>& res_out, int* ws64, int* outer_done) {
     const int64_t N = ks.N;
-    const int nw = kr.nw;  // wanted + guard vectors refined together
+    const int nw = kr.nw;      // wanted + guard vectors refined together
+    const int nwant = ks.nw;
     EW_CUDA_TRY(cudaMemcpyAsync(kr.V, ks.V, sizeof(double) * (size_t)N * nw, cudaMemcpyDeviceToDevice, kr.st));
     double* W64 = nullptr;
     EW_TRY(kr.alloc((void**)&W64, sizeof(double) * (size_t)N * nw));
+    std::vector<double> sc(nw), lam(nw);
+    // Rayleigh-Ritz with L_h inside span[X] (separates pairs that S cannot),
+    // rank by beta_d(lambda) of the filter, then eig-res of the wanted pairs:
+    // all FP64 and no wave-solve, so it doubles as the stopping test
+    auto lrr_check = [&](double* worst) -> ew_status {
+        EW_TRY(launch_apply_L<double>(g64->geom, kr.V, W64, nw, 1.0, kr.st));
+        std::vector<double> G, Z, w;
+        EW_TRY(kr.gram_host(kr.V, nw, W64, nw, G));
+        for (int i = 0; i < nw; ++i)
+            for (int j = 0; j < i; ++j) {
+                double a = 0.5 * (G[(size_t)i * nw + j] + G[(size_t)j * nw + i]);
+                G[(size_t)i * nw + j] = G[(size_t)j * nw + i] = a;
+            }
+        jacobi_eig(nw, G, Z, w);
+        std::vector<double> l(nw), scr(nw);
+        for (int i = 0; i < nw; ++i) {
+            l[i] = sqrt(std::max(-w[i], 0.0));
+            scr[i] = filter_beta(ks.plan, ks.p->scheme, l[i]);
+        }
+        std::vector<int> ord(nw);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::sort(ord.begin(), ord.end(), [&](int a, int c) { return scr[a] > scr[c]; });
+        std::vector<double> Zo((size_t)nw * nw);
+        for (int rr = 0; rr < nw; ++rr)
+            for (int c = 0; c < nw; ++c) Zo[(size_t)rr * nw + c] = Z[(size_t)rr * nw + ord[c]];
+        // X <- X Z (through W64, then back)
+        EW_TRY(kr.update_host(kr.V, nw, nullptr, nw, Zo, 1.0, 0.0, W64));
+        EW_CUDA_TRY(cudaMemcpyAsync(kr.V, W64, sizeof(double) * (size_t)N * nw, cudaMemcpyDeviceToDevice, kr.st));
+        for (int c = 0; c < nw; ++c) sc[c] = scr[ord[c]];
+        lam_out.resize(nwant);
+        res_out.resize(nwant);
+        EW_TRY(rayleigh_any(g64, kr.V, nwant, lam_out.data(), res_out.data(), kr.st));
+        *worst = *std::max_element(res_out.begin(), res_out.end());
+        if (getenv("EW_KS_LOG")) fprintf(stderr, "[ew refine] eig-res of the wanted pairs %.3e\n", *worst);
+        return EW_OK;
+    };
     std::vector<double> theta, Y, resid;
     *outer_done = 0;
     for (int outer = 0; outer < max_outer; ++outer) {
-        // exact image of X in FP64
+        double worst = 0.0;
+        EW_TRY(lrr_check(&worst));
+        if (worst <= res_tol) break;
+        // exact image of X in FP64: S X = X Theta + E
         for (int c0 = 0; c0 < nw; c0 += 16) {
             int nb = std::min(16, nw - c0);
             EW_TRY(filter_apply_any(g64, ks.p, ks.plan, kr.V + (size_t)c0 * N, W64 + (size_t)c0 * N, nb, kr.st));
         }
         *ws64 += nw;
-        std::vector<double> T1, T2, G;
+        std::vector<double> T1, T2;
         EW_TRY(kr.gram_host(kr.V, nw, W64, nw, T1));
         EW_TRY(kr.update_host(kr.V, nw, W64, nw, T1, -1.0, 1.0, W64));
         EW_TRY(kr.gram_host(kr.V, nw, W64, nw, T2));
         EW_TRY(kr.update_host(kr.V, nw, W64, nw, T2, -1.0, 1.0, W64));
-        EW_TRY(kr.gram_host(W64, nw, W64, nw, G));
-        // stop on the wanted pairs (the first ks.nw columns, by theta); the guard
-        // vectors sit further down the filter and converge more slowly
-        double worst = 0.0;
-        for (int j = 0; j < ks.nw; ++j) worst = std::max(worst, sqrt(std::max(G[(size_t)j * nw + j], 0.0)));
-        if (getenv("EW_KS_LOG")) fprintf(stderr, "[ew refine] outer %d: FP64 Ritz residual %.3e\n", outer, worst);
-        *outer_done = outer;
-        if (worst <= ritz_tol) break;
         // E = Q R with Q in V[:, nw : 2 nw]
         double* Q = kr.V + (size_t)nw * N;
         EW_CUDA_TRY(cudaMemcpyAsync(Q, W64, sizeof(double) * (size_t)N * nw, cudaMemcpyDeviceToDevice, kr.st));
@@ -498,38 +530,14 @@ static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, int p, int max_ou
         kr.ritz(theta, Y, resid);
         EW_TRY(kr.update_host(kr.V, kr.mcur, nullptr, kr.mcur, Y, 1.0, 0.0, kr.V));
         *outer_done = outer + 1;
-    }
-    // separate near-degenerate pairs inside span[X] with L_h, then report
-    double* LX = W64;
-    EW_CUDA_TRY(cudaMemcpyAsync(ks.V, kr.V, sizeof(double) * (size_t)N * nw, cudaMemcpyDeviceToDevice, kr.st));
-    EW_TRY(launch_apply_L<double>(g64->geom, ks.V, LX, nw, 1.0, kr.st));
-    std::vector<double> G, Z, w;
-    EW_TRY(kr.gram_host(ks.V, nw, LX, nw, G));
-    for (int i = 0; i < nw; ++i)
-        for (int j = 0; j < i; ++j) {
-            double a = 0.5 * (G[(size_t)i * nw + j] + G[(size_t)j * nw + i]);
-            G[(size_t)i * nw + j] = G[(size_t)j * nw + i] = a;
+        if (outer + 1 == max_outer) {
+            double w2 = 0.0;
+            EW_TRY(lrr_check(&w2));
         }
-    jacobi_eig(nw, G, Z, w);
-    std::vector<double> l(nw), sc(nw);
-    for (int i = 0; i < nw; ++i) {
-        l[i] = sqrt(std::max(-w[i], 0.0));
-        sc[i] = filter_beta(ks.plan, ks.p->scheme, l[i]);
     }
-    std::vector<int> ord(nw);
-    std::iota(ord.begin(), ord.end(), 0);
-    std::sort(ord.begin(), ord.end(), [&](int a, int c) { return sc[a] > sc[c]; });
-    std::vector<double> Zo((size_t)nw * nw);
-    for (int rr = 0; rr < nw; ++rr)
-        for (int c = 0; c < nw; ++c) Zo[(size_t)rr * nw + c] = Z[(size_t)rr * nw + ord[c]];
-    EW_TRY(kr.update_host(ks.V, nw, nullptr, nw, Zo, 1.0, 0.0, kr.V));
-    EW_CUDA_TRY(cudaMemcpyAsync(ks.V, kr.V, sizeof(double) * (size_t)N * nw, cudaMemcpyDeviceToDevice, kr.st));
-    const int nwant = ks.nw;
-    lam_out.resize(nwant);
-    res_out.resize(nwant);
-    EW_TRY(rayleigh_any(g64, ks.V, nwant, lam_out.data(), res_out.data(), kr.st));
-    beta_out.resize(nwant);
-    for (int c = 0; c < nwant; ++c) beta_out[c] = sc[ord[c]];
+    EW_CUDA_TRY(cudaMemcpyAsync(ks.V, kr.V, sizeof(double) * (size_t)N * nwant, cudaMemcpyDeviceToDevice, kr.st));
+    beta_out.assign(sc.begin(), sc.begin() + nwant);
+    (void)lam;
     return EW_OK;
 }
 
@@ -559,8 +567,8 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
     m = ((m + b - 1) / b) * b;
     if (m < nw + b) return set_error(EW_EINVAL, "krylov_dim must be >= n_wanted + block");
     if (m + 2 * b > 160) return set_error(EW_EINVAL, "krylov_dim too large (krylov_dim + 2 block <= 160)");
-    if (ep->refine_fp64 && grid->prec == EW_FP32 && 6 * (nw + std::max(2, nw / 4)) > 160)
-        return set_error(EW_EINVAL, "n_wanted too large for the FP64 refinement (n_wanted <= 21)");
+    if (ep->refine_fp64 && grid->prec == EW_FP32 && 7 * (nw + std::max(2, nw / 4)) > 160)
+        return set_error(EW_EINVAL, "n_wanted too large for the FP64 refinement (n_wanted <= 18)");
     if ((int64_t)m > grid->geom.N) return set_error(EW_EINVAL, "krylov_dim exceeds the number of active points");
     ew_grid* g = const_cast<ew_grid*>(grid);
 
@@ -613,14 +621,14 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
         kr.N = ks.N;
         kr.b = nr;
         kr.nw = nr;
-        kr.m = 4 * nr;
+        kr.m = 5 * nr;
         kr.tol = 0.0;
         kr.max_ws = 0;
         kr.st = st;
         int ws64 = 0, outer = 0;
-        double ritz_tol = ep->refine_tol > 0 ? ep->refine_tol : 1e-10;
+        double res_tol = ep->refine_tol > 0 ? ep->refine_tol : 5e-9;
         ew_status s = kr.setup();
-        if (s == EW_OK) s = refine_ir(ks, kr, g64, 3, 6, ritz_tol, lam, beta, res, &ws64, &outer);
+        if (s == EW_OK) s = refine_ir(ks, kr, g64, 4, 6, res_tol, lam, beta, res, &ws64, &outer);
         if (s != EW_OK) {
             ew_grid_destroy(g64);
             return s;

@@ -240,6 +240,10 @@ static size_t resident_smem(const GridGeom& g) {
 }
 
 template <typename T>
+ew_status step3d(const GridGeom& g, const T* W, T* Wprev, T* acc, T c, const Stencil<T>& s, int nvec, int64_t fstride,
+                 cudaStream_t st);
+
+template <typename T>
 ew_status first_step(const GridGeom& g, const T* vin, T* W0, T* W1, T* vout,
                             const FilterPlan& plan, int nvec, int64_t fstride, cudaStream_t st) {
     Stencil<T> s = make_stencil<T>(g, 0.5 * plan.dt * plan.dt);
@@ -325,7 +329,10 @@ ew_status explicit_wave_solve(const GridGeom& g, const FilterPlan& plan, const T
     Stencil<T> s = make_stencil<T>(g, plan.dt * plan.dt);
     int prv = 0, cur = 1;
     for (int64_t L = 1; L < plan.Nt; ++L) {
-        EW_TRY(step_simple<T>(g, F[cur], F[prv], vout, T(plan.cn(L + 1)), s, nvec, fstride, st));
+        if (g.dim == 3)
+            EW_TRY(step3d<T>(g, F[cur], F[prv], vout, T(plan.cn(L + 1)), s, nvec, fstride, st));
+        else
+            EW_TRY(step_simple<T>(g, F[cur], F[prv], vout, T(plan.cn(L + 1)), s, nvec, fstride, st));
         std::swap(prv, cur);
     }
     return EW_OK;
