@@ -14,9 +14,9 @@ e2e     = the same metric through the C ABI from pinned HOST buffers, the
           host->device copy of v and the device->host copy of S v inside the
           timed region;
 roofline= the dominant kernel (the temporally blocked fused step): its
-          algorithmic HBM bytes per launch (read W^{n-1}, W^n, the filter sum;
-          write W^{n+b-1}, W^{n+b}, the filter sum: 24 B per active point per
-          launch) over its mean launch time, timed with CUDA events on the
+          algorithmic HBM bytes per launch (read D^n = W^n - W^{n-1}, W^n, the
+          filter sum; write D^{n+b}, W^{n+b}, the filter sum: 24 B per active
+          point per launch) over its mean launch time, timed with CUDA events on the
           launching stream over the timed region;
 cpu_baseline = the FP64 CPU oracle timed on this host on a bounded sample of
           the same workload (the first time steps of the same wave-solve).
@@ -46,7 +46,7 @@ WORKLOAD = dict(workload="rect2d_2047x3071_order4_fp32_explicit", n=(2047, 3071)
                 order=4, omega=150.0, num_periods=1, cfl=0.8, precision="fp32", nvec=1)
 METRIC = "Gcell-steps/s of fused filter step"
 UNIT = "Gcell-steps/s"
-BYTES_PER_POINT_PER_LAUNCH = 24  # 6 x FP32: W^{n-1}, W^n, acc in; W^{n+b-1}, W^{n+b}, acc out
+BYTES_PER_POINT_PER_LAUNCH = 24  # 6 x FP32: D^n, W^n, acc in; D^{n+b}, W^{n+b}, acc out
 DOMINANT_KERNEL = "k_step_tb2d"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2507_18282_gb300", "csrc", f)
@@ -413,7 +413,7 @@ def run_extra(args):
         cells = g.size * info["Nt"] * args.steps
         launches = max(prof["fused_launches"], 1)
         mean = prof["fused_ms"] / launches
-        bytes_launch = 20 * prof["fused_points"] / launches  # one step per launch: W^{n-1}, W^n, acc in; W^{n+1}, acc out
+        bytes_launch = 24 * prof["fused_points"] / launches  # one step per launch: W^n, D^n, acc in; W^{n+1}, D^{n+1}, acc out
         line = dict(workload="cube3d_511_order2_fp32_explicit", metric=METRIC, unit=UNIT,
                     value=cells / (ms / 1e3) / 1e9, ms_per_step=ms / args.steps, time_steps_per_step=info["Nt"],
                     roofline=dict(bound="hbm", kernel="k_step3d<float,1>", bytes_per_launch=bytes_launch,

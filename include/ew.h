@@ -226,16 +226,19 @@ typedef struct {
     uint64_t seed;         /* start block from SplitMix64 uniform [-1,1) when start_dev is NULL:
                               element q of the N x block column-major block is draw q of stream seed */
     int refine_fp64;       /* FP32 grids, FP64 refinement of the result (0: none).
-                              1: mixed-precision iterative refinement of the invariant subspace: per
-                                 outer step (at most 6) one FP64 wave-solve per wanted (and guard)
-                                 vector X gives
-                                 the exact relation S X = X Theta + E; span[X, E] is extended by three
-                                 FP32 block expansions and Rayleigh-Ritz with S picks the new X; stops
-                                 when the FP64 Ritz residuals ||E_j|| <= refine_tol.  A final
-                                 Rayleigh-Ritz with L_h inside span[X] separates near-degenerate pairs.
+                              1: mixed-precision iterative refinement of the invariant subspace of the
+                                 n_wanted pairs plus g guard vectors (the next Ritz vectors by beta).
+                                 Each outer step (at most 6): a Rayleigh-Ritz with L_h inside span[X]
+                                 (separates near-degenerate pairs; pairs ranked by beta_d(lambda));
+                                 stop when every wanted eig-res <= refine_tol; else one FP64 wave-solve
+                                 per vector gives the exact relation S X = X Theta + E, span[X, E] is
+                                 extended by p FP32 block expansions and Rayleigh-Ritz with S picks the
+                                 new X.  p = 6 and g = n_wanted where they fit ((p + 2)(n_wanted + g)
+                                 <= 128 basis columns), fewer for large n_wanted (n_wanted <= 23).
                               2: a second Krylov-Schur run with FP64 full-filter wave-solves started
                                  from the FP32 vectors (block n_wanted, basis 3 n_wanted) */
-    double refine_tol;     /* FP64 Ritz residual target of the refinement; 0: 1e-10 */
+    double refine_tol;     /* refine_fp64 1: eig-res target of every wanted pair, 0: 5e-9;
+                              refine_fp64 2: FP64 Ritz residual target, 0: 1e-10 */
 } ew_eigs_params;
 
 #define EW_MAX_EIGS 64

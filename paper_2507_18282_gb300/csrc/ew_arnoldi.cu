@@ -382,7 +382,7 @@ struct KSRun {
             if (getenv("EW_KS_LOG")) {
                 fprintf(stderr, "[ew ks] %s b=%d m=%d ws=%d restarts=%d conv=%d | theta/resid:",
                         g->prec == EW_FP32 ? "fp32" : "fp64", b, mcur, wave_solves, restarts, nc);
-                for (int c = 0; c < std::min(nw + 2, mcur); ++c) fprintf(stderr, " %.9f/%.1e", theta[c], resid[c]);
+                for (int c = 0; c < std::min(nw + 8, mcur); ++c) fprintf(stderr, " %.9f/%.1e", theta[c], resid[c]);
                 fprintf(stderr, "\n");
             }
             bool done = nc >= nw || wave_solves + b > max_ws;
@@ -428,6 +428,23 @@ static double filter_beta(const FilterPlan& plan, ew_scheme scheme, double lam) 
 // extreme ones) improves X by several digits per outer step.  A last
 // Rayleigh-Ritz with L_h inside span[X] separates near-degenerate pairs.
 // kr is an FP32 Krylov-Schur run with block nw and basis (1 + p) nw.
+// Shape of the mixed-precision refinement for n_wanted nw: p FP32 block
+// expansions per outer step and up to nw guard vectors, as many as fit the
+// Rayleigh-Ritz rotation of the (p + 2)(nw + guard) basis columns in the
+// update kernel (<= 128 columns); p drops from 6 to 3 for large nw.  False
+// if not even two guards fit.
+static bool refine_shape(int nw, int* p, int* guard) {
+    for (int pe = 6; pe >= 3; --pe) {
+        int gd = std::min(nw, 128 / (pe + 2) - nw);
+        if (gd >= 2) {
+            *p = pe;
+            *guard = gd;
+            return true;
+        }
+    }
+    return false;
+}
+
 static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, int p, int max_outer, double res_tol,
                            std::vector<double>& lam_out, std::vector<double>& beta_out,
                            std::vector<double>& res_out, int* ws64, int* outer_done) {
@@ -528,6 +545,17 @@ static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, int p, int max_ou
                 for (int j = 0; j < nw; ++j) kr.h(i, col0 + j) = (e == 0 && j < r) ? R[(size_t)j * nw + i] : 0.0;
         }
         kr.ritz(theta, Y, resid);
+        if (getenv("EW_KS_LOG")) {
+            fprintf(stderr, "[ew refine] outer %d rank %d |E_j|:", outer, r);
+            for (int j = 0; j < nw; ++j) {
+                double s = 0.0;
+                for (int i = 0; i < r; ++i) s += R[(size_t)i * nw + j] * R[(size_t)i * nw + j];
+                fprintf(stderr, " %.2e", sqrt(s));
+            }
+            fprintf(stderr, "\n[ew refine]   theta/resid:");
+            for (int j = 0; j < nw + 2 && j < kr.mcur; ++j) fprintf(stderr, " %.9f/%.1e", theta[j], resid[j]);
+            fprintf(stderr, "\n");
+        }
         EW_TRY(kr.update_host(kr.V, kr.mcur, nullptr, kr.mcur, Y, 1.0, 0.0, kr.V));
         *outer_done = outer + 1;
         if (outer + 1 == max_outer) {
@@ -567,8 +595,9 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
     m = ((m + b - 1) / b) * b;
     if (m < nw + b) return set_error(EW_EINVAL, "krylov_dim must be >= n_wanted + block");
     if (m + 2 * b > 160) return set_error(EW_EINVAL, "krylov_dim too large (krylov_dim + 2 block <= 160)");
-    if (ep->refine_fp64 && grid->prec == EW_FP32 && 7 * (nw + std::max(2, nw / 4)) > 160)
-        return set_error(EW_EINVAL, "n_wanted too large for the FP64 refinement (n_wanted <= 18)");
+    int ref_p = 0, ref_guard = 0;
+    if (ep->refine_fp64 == 1 && grid->prec == EW_FP32 && !refine_shape(nw, &ref_p, &ref_guard))
+        return set_error(EW_EINVAL, "n_wanted too large for the FP64 refinement (n_wanted <= 23)");
     if ((int64_t)m > grid->geom.N) return set_error(EW_EINVAL, "krylov_dim exceeds the number of active points");
     ew_grid* g = const_cast<ew_grid*>(grid);
 
@@ -611,8 +640,10 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
         EW_TRY(make_twin_fp64(g, &g64));
         // guard vectors: a pair just outside the wanted set can share beta with
         // one inside (lambda on the other side of the peak); refining both and
-        // ranking by beta_d(lambda) after the L_h projection keeps the right one
-        const int guard = std::max(2, nw / 4);
+        // ranking by beta_d(lambda) after the L_h projection keeps the right one.
+        // On dense spectra the guards also widen the gap between the refined
+        // block and the rest, which sets the contraction of each outer step.
+        const int guard = ref_guard, pexp = ref_p;
         const int nr = std::min(nw + guard, (int)theta.size());
         KSRun kr;
         kr.g = g;
@@ -621,14 +652,14 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
         kr.N = ks.N;
         kr.b = nr;
         kr.nw = nr;
-        kr.m = 5 * nr;
+        kr.m = (pexp + 1) * nr;
         kr.tol = 0.0;
         kr.max_ws = 0;
         kr.st = st;
         int ws64 = 0, outer = 0;
         double res_tol = ep->refine_tol > 0 ? ep->refine_tol : 5e-9;
         ew_status s = kr.setup();
-        if (s == EW_OK) s = refine_ir(ks, kr, g64, 4, 6, res_tol, lam, beta, res, &ws64, &outer);
+        if (s == EW_OK) s = refine_ir(ks, kr, g64, pexp, 6, res_tol, lam, beta, res, &ws64, &outer);
         if (s != EW_OK) {
             ew_grid_destroy(g64);
             return s;

@@ -26,7 +26,7 @@
 namespace ew {
 
 template <typename T>
-ew_status first_step(const GridGeom& g, const T* vin, T* W0, T* W1, T* vout, const FilterPlan& plan, int nvec,
+ew_status first_step(const GridGeom& g, const T* vin, T* D1, T* W1, T* vout, const FilterPlan& plan, int nvec,
                      int64_t fstride, cudaStream_t st);
 
 template <typename T>

@@ -205,7 +205,7 @@ static ew_status filter_apply_t(ew_grid* g, const ew_filter_params* p, const Fil
     if (p->scheme == EW_IMPLICIT) return implicit_wave_solve_any(g, plan, p, vin, vout, nvec, st);
     const T* cdev = nullptr;
     EW_TRY(upload_weights<T>(g, plan, st, &cdev));
-    EW_TRY(g->fields.reserve((size_t)4 * nvec * g->geom.N * sizeof(T)));
+    EW_TRY(g->fields.reserve((size_t)4 * nvec * field_stride(g->geom.N) * sizeof(T)));
     return explicit_wave_solve<T>(g->geom, plan, cdev, vin, vout, nvec, (T*)g->fields.ptr, p->temporal_block, st);
 }
 

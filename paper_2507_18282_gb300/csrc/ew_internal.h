@@ -115,6 +115,24 @@ ew_status launch_apply_L(const GridGeom& g, const T* u, T* Lu, int nvec, double 
 
 // one explicit wave-solve for nvec vectors; fields = 4 * N * nvec elements
 // of scratch; cdev = N_t + 1 weights (device, type T).
+// register-blocked persistent form of the 2D FP32 blocked step (ew_rb2d.cu)
+struct Rb2dDesc {
+    void* fn;
+    int nty, ky, B, TX, TY, threads;
+    size_t smem;
+};
+const std::vector<Rb2dDesc>& rb2d_variants(int R);
+ew_status rb2d_launch(const Rb2dDesc& d, const GridGeom& g, const float* Ain, const float* Bin, float* Aout,
+                      float* Bout, float* acc, const float* cw, int b, const Stencil<float>& s, int nvec,
+                      int64_t fstride, cudaStream_t st);
+// reads (and clears) the flag a staging wait sets when it gives up: EW_ETIMEOUT if set
+ew_status rb2d_check_timeout();
+
+// distance between consecutive vectors of a wave-solve's time-level fields:
+// N rounded up to 64 points, so every vector starts on a 256-byte boundary
+// (bulk copies need 16-byte aligned rows)
+inline int64_t field_stride(int64_t N) { return (N + 63) & ~(int64_t)63; }
+
 template <typename T>
 ew_status explicit_wave_solve(const GridGeom& g, const FilterPlan& plan, const T* cdev,
                               const T* vin, T* vout, int nvec, T* fields, int temporal_block,

@@ -62,7 +62,7 @@ template <typename T>
 static ew_status noalloc_t(const ew_grid* g, const ew_filter_params* p, const FilterPlan& plan, const T* vin, T* vout,
                            cudaStream_t st) {
     const int64_t N = g->geom.N;
-    if ((size_t)4 * N * sizeof(T) > kFieldBytes)
+    if ((size_t)4 * field_stride(N) * sizeof(T) > kFieldBytes)
         return set_error(EW_EINVAL, "grid too large for ew_filter_apply_noalloc: at most " +
                                         std::to_string(kFieldBytes / (4 * sizeof(T))) + " active points in this precision");
     if ((size_t)(plan.Nt + 1) * sizeof(T) > kWeightBytes)

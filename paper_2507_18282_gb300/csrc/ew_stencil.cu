@@ -7,21 +7,35 @@
 // The filter sum is accumulated inside the time loop, as the paper notes for
 // Algorithm EigenWave, so no time history is stored.
 //
+// Summed (velocity-difference) form.  Every kernel carries D^n = W^n - W^{n-1}
+// instead of W^{n-1}:
+//   D^1 = (dt^2/2) L_h V,  W^1 = V + D^1
+//   D^{n+1} = D^n + dt^2 L_h W^n,  W^{n+1} = W^n + D^{n+1}
+// which is the same recurrence.  In FP32 it matters: dt^2 L_h W^n is about
+// (lambda dt)^2 |W| (1e-5 .. 1e-3 of |W| for the low and middle modes of fine
+// grids), and added to 2 W^n - W^{n-1} it keeps only eps32 / (lambda dt)^2 of
+// its relative precision; added to D^n (about lambda dt |W|) it keeps
+// eps32 / (lambda dt).  The low modes of a 2047 x 3071 grid lose a factor
+// 30 .. 300 of accuracy in the first form.
+//
 // Fields are stored in the active-point layout (x fastest, no padding): the
 // Dirichlet closure is applied on the fly.  A point one step outside the box
 // is a boundary point (value 0); for the fourth-order stencil the point two
 // steps outside is a ghost holding the odd reflection -u(mirror).
 //
 // Kernels:
-//   k_first_step      : a3, writes W^0, W^1 and V_out = c_0 W^0 + c_1 W^1.
+//   k_first_step      : a3, writes D^1, W^1 and V_out = c_0 W^0 + c_1 W^1.
 //   k_step_simple     : one time step per launch (any dim), reads W^n and its
-//                       neighbours from global memory, writes W^{n+1} over
-//                       W^{n-1} and V_out += c W^{n+1}.
+//                       neighbours from global memory, updates D in place,
+//                       writes W^{n+1} to a second W buffer and
+//                       V_out += c W^{n+1}.
 //   k_step_tb2d       : (ew_tb2d.cu) b time steps per launch on overlapped
 //                       tiles staged in shared memory (temporal blocking).
 //   k_resident2d      : the whole wave-solve of a small 2D grid inside one CTA
 //                       (grid + ghosts resident in shared memory).
 #include <algorithm>
+#include <cmath>
+#include <limits>
 #include <utility>
 
 #include "ew_internal.h"
@@ -29,27 +43,55 @@
 
 namespace ew {
 
+// Stencil coefficients, pre-multiplied by `scale` (dt^2 or dt^2/2) and stored
+// in T.  Rounded one by one they would no longer sum to zero: the discrete
+// operator would gain a mass term of about eps_T |c0| -- for FP32 on a
+// 2047 x 3071 grid about 1e-7 of W per step against a force of 1e-5 .. 1e-3
+// of W for the low and middle modes, i.e. a frequency error of up to 1e-2
+// that builds up as phase drift over the wave-solve.  So the off-centre
+// coefficients are rounded to a common grid q/2 (q = the ulp of T at twice
+// their total weight) and c0 is minus their exact sum: the stencil stays
+// exactly consistent (L_h 1 = 0 in the stored coefficients), the
+// coefficients move by at most about 4 ulps relative.
 template <typename T>
 Stencil<T> make_stencil(const GridGeom& g, double scale) {
     Stencil<T> s;
-    double c0 = 0.0;
-    for (int a = 0; a < 3; ++a) {
-        s.c1[a] = T(0);
-        s.c2[a] = T(0);
-    }
+    double a1[3] = {0, 0, 0}, a2[3] = {0, 0, 0};
+    double tot = 0.0;
     for (int a = 0; a < g.dim; ++a) {
         double ih2 = 1.0 / (g.h[a] * g.h[a]);
         if (g.order == 2) {
-            s.c1[a] = T(scale * ih2);
-            c0 += -2.0 * scale * ih2;
+            a1[a] = scale * ih2;
         } else {
-            s.c1[a] = T(scale * 16.0 / 12.0 * ih2);
-            s.c2[a] = T(-scale / 12.0 * ih2);
-            c0 += -scale * 30.0 / 12.0 * ih2;
+            a1[a] = scale * 16.0 / 12.0 * ih2;
+            a2[a] = -scale / 12.0 * ih2;
         }
+        tot += 2.0 * (fabs(a1[a]) + fabs(a2[a]));
     }
-    s.c0 = T(c0);
-    return s;
+    const int mant = std::numeric_limits<T>::digits;  // 24 or 53
+    int e = 0;
+    frexp(2.0 * tot, &e);                               // 2 tot < 2^e
+    double q = ldexp(1.0, e - mant);                    // ulp of T just below 2^e
+    for (;;) {
+        double c1[3], c2[3], sum = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            c1[a] = nearbyint(a1[a] / (0.5 * q)) * (0.5 * q);
+            c2[a] = nearbyint(a2[a] / (0.5 * q)) * (0.5 * q);
+            sum += 2.0 * (c1[a] + c2[a]);
+        }
+        const double c0 = -sum;
+        bool exact = (double)(T)c0 == c0;
+        for (int a = 0; a < 3; ++a) exact = exact && (double)(T)c1[a] == c1[a] && (double)(T)c2[a] == c2[a];
+        if (exact || q > 1.0) {
+            for (int a = 0; a < 3; ++a) {
+                s.c1[a] = T(c1[a]);
+                s.c2[a] = T(c2[a]);
+            }
+            s.c0 = T(c0);
+            return s;
+        }
+        q *= 2.0;
+    }
 }
 template Stencil<float> make_stencil<float>(const GridGeom&, double);
 template Stencil<double> make_stencil<double>(const GridGeom&, double);
@@ -69,45 +111,48 @@ __global__ void k_apply_L(int64_t nx, int64_t ny, int64_t nz, const T* __restric
     }
 }
 
-// a3: W^0 = V (copied, the caller's input stays untouched), W^1 = V + (dt^2/2) L V,
-// V_out = c0 W^0 + c1 W^1.  `s` carries the dt^2/2 scale.
+// a3: D^1 = (dt^2/2) L V, W^1 = V + D^1, V_out = c0 W^0 + c1 W^1.  `s`
+// carries the dt^2/2 scale.
 template <typename T, int DIM, int ORDER>
 __global__ void k_first_step(int64_t nx, int64_t ny, int64_t nz, const T* __restrict__ vin,
-                             T* __restrict__ W0, T* __restrict__ W1, T* __restrict__ vout,
+                             T* __restrict__ D1, T* __restrict__ W1, T* __restrict__ vout,
                              Stencil<T> s, T c0, T c1, int64_t fstride) {
     const int64_t N = nx * ny * nz;
     const int64_t v = blockIdx.y;
     vin += v * N;
     vout += v * N;
-    W0 += v * fstride;
+    D1 += v * fstride;
     W1 += v * fstride;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N;
          q += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = q % nx, t = q / nx, j = t % ny, k = t / ny;
         T x = vin[q];
-        T w1 = x + lap_global<T, DIM, ORDER>(vin, s, q, i, j, k, nx, ny, nz);
-        W0[q] = x;
+        T d = lap_global<T, DIM, ORDER>(vin, s, q, i, j, k, nx, ny, nz);
+        T w1 = x + d;
+        D1[q] = d;
         W1[q] = w1;
         vout[q] = c0 * x + c1 * w1;
     }
 }
 
-// one step, in place: Wprev <- 2 W - Wprev + dt^2 L W ; acc += c Wprev
+// one step: D <- D + dt^2 L W (in place), Wout <- W + D, acc += c Wout
 template <typename T, int DIM, int ORDER>
 __global__ void k_step_simple(int64_t nx, int64_t ny, int64_t nz, const T* __restrict__ W,
-                              T* __restrict__ Wprev, T* __restrict__ acc, Stencil<T> s, T c,
+                              T* __restrict__ D, T* __restrict__ Wout, T* __restrict__ acc, Stencil<T> s, T c,
                               int64_t fstride) {
     const int64_t N = nx * ny * nz;
     const int64_t v = blockIdx.y;
     W += v * fstride;
-    Wprev += v * fstride;
+    D += v * fstride;
+    Wout += v * fstride;
     acc += v * N;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N;
          q += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = q % nx, t = q / nx, j = t % ny, k = t / ny;
-        T u = W[q];
-        T wn = T(2) * u - Wprev[q] + lap_global<T, DIM, ORDER>(W, s, q, i, j, k, nx, ny, nz);
-        Wprev[q] = wn;
+        T d = D[q] + lap_global<T, DIM, ORDER>(W, s, q, i, j, k, nx, ny, nz);
+        T wn = W[q] + d;
+        D[q] = d;
+        Wout[q] = wn;
         acc[q] += c * wn;
     }
 }
@@ -157,6 +202,7 @@ __global__ void __launch_bounds__(1024)
         return r;
     };
 
+    // sA: W^n with its boundary and ghost layers; sB: D^n (same layout)
     for (int q = tid; q < PX * PY; q += nthr) {
         sA[q] = T(0);
         sB[q] = T(0);
@@ -164,40 +210,49 @@ __global__ void __launch_bounds__(1024)
     __syncthreads();
     for (int q = tid; q < N; q += nthr) {
         int x = q % nx, y = q / nx;
-        sB[(y + G) * PX + x + G] = vin[q];
-    }
-    __syncthreads();
-    fix(sB);
-    __syncthreads();
-    // first step into A (eq. explicitStep1)
-    const T c0 = cw[0], c1 = cw[1];
-    for (int q = tid; q < N; q += nthr) {
-        int x = q % nx, y = q / nx;
-        int p = (y + G) * PX + x + G;
-        T w1 = sB[p] + lap(sB, p, st_half);
-        sA[p] = w1;
-        sAcc[q] = c0 * sB[p] + c1 * w1;
+        sA[(y + G) * PX + x + G] = vin[q];
     }
     __syncthreads();
     fix(sA);
     __syncthreads();
-    T* cur = sA;
-    T* prv = sB;
+    // first step (eq. explicitStep1): D^1 = (dt^2/2) L W^0, then W^1 = W^0 + D^1
+    const T c0 = cw[0], c1 = cw[1];
+    for (int q = tid; q < N; q += nthr) {
+        int x = q % nx, y = q / nx;
+        int p = (y + G) * PX + x + G;
+        sB[p] = lap(sA, p, st_half);
+    }
+    __syncthreads();
+    for (int q = tid; q < N; q += nthr) {
+        int x = q % nx, y = q / nx;
+        int p = (y + G) * PX + x + G;
+        T x0 = sA[p];
+        T w1 = x0 + sB[p];
+        sA[p] = w1;
+        sAcc[q] = c0 * x0 + c1 * w1;
+    }
+    __syncthreads();
+    fix(sA);
+    __syncthreads();
     for (int64_t n = 1; n < Nt; ++n) {
         const T cn = cw[n + 1];
+        // D^{n+1} = D^n + dt^2 L W^n everywhere, then W^{n+1} = W^n + D^{n+1} pointwise
         for (int q = tid; q < N; q += nthr) {
             int x = q % nx, y = q / nx;
             int p = (y + G) * PX + x + G;
-            T wn = T(2) * cur[p] - prv[p] + lap(cur, p, st);
-            prv[p] = wn;
+            sB[p] = sB[p] + lap(sA, p, st);
+        }
+        __syncthreads();
+        for (int q = tid; q < N; q += nthr) {
+            int x = q % nx, y = q / nx;
+            int p = (y + G) * PX + x + G;
+            T wn = sA[p] + sB[p];
+            sA[p] = wn;
             sAcc[q] += cn * wn;
         }
         __syncthreads();
-        fix(prv);
+        fix(sA);
         __syncthreads();
-        T* t = cur;
-        cur = prv;
-        prv = t;
     }
     for (int q = tid; q < N; q += nthr) vout[q] = sAcc[q];
 }
@@ -240,41 +295,41 @@ static size_t resident_smem(const GridGeom& g) {
 }
 
 template <typename T>
-ew_status step3d(const GridGeom& g, const T* W, T* Wprev, T* acc, T c, const Stencil<T>& s, int nvec, int64_t fstride,
-                 cudaStream_t st);
+ew_status step3d(const GridGeom& g, const T* W, T* D, T* Wout, T* acc, T c, const Stencil<T>& s, int nvec,
+                 int64_t fstride, cudaStream_t st);
 
 template <typename T>
-ew_status first_step(const GridGeom& g, const T* vin, T* W0, T* W1, T* vout,
+ew_status first_step(const GridGeom& g, const T* vin, T* D1, T* W1, T* vout,
                             const FilterPlan& plan, int nvec, int64_t fstride, cudaStream_t st) {
     Stencil<T> s = make_stencil<T>(g, 0.5 * plan.dt * plan.dt);
     dim3 grid(grid_blocks(g.N, 256), nvec);
     T c0 = T(plan.cn(0)), c1 = T(plan.cn(1));
     if (g.dim == 2 && g.order == 2)
-        k_first_step<T, 2, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, vin, W0, W1, vout, s, c0, c1, fstride);
+        k_first_step<T, 2, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, vin, D1, W1, vout, s, c0, c1, fstride);
     else if (g.dim == 2)
-        k_first_step<T, 2, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, vin, W0, W1, vout, s, c0, c1, fstride);
+        k_first_step<T, 2, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, vin, D1, W1, vout, s, c0, c1, fstride);
     else if (g.order == 2)
-        k_first_step<T, 3, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, W0, W1, vout, s, c0, c1, fstride);
+        k_first_step<T, 3, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, D1, W1, vout, s, c0, c1, fstride);
     else
-        k_first_step<T, 3, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, W0, W1, vout, s, c0, c1, fstride);
+        k_first_step<T, 3, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, D1, W1, vout, s, c0, c1, fstride);
     EW_CUDA_TRY(cudaGetLastError());
     count_launch();
     return EW_OK;
 }
 
 template <typename T>
-static ew_status step_simple(const GridGeom& g, const T* W, T* Wprev, T* acc, T c, const Stencil<T>& s,
+static ew_status step_simple(const GridGeom& g, const T* W, T* D, T* Wout, T* acc, T c, const Stencil<T>& s,
                              int nvec, int64_t fstride, cudaStream_t st) {
     dim3 grid(grid_blocks(g.N, 256), nvec);
     cudaEvent_t ev = fused_begin(st);
     if (g.dim == 2 && g.order == 2)
-        k_step_simple<T, 2, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, W, Wprev, acc, s, c, fstride);
+        k_step_simple<T, 2, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, W, D, Wout, acc, s, c, fstride);
     else if (g.dim == 2)
-        k_step_simple<T, 2, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, W, Wprev, acc, s, c, fstride);
+        k_step_simple<T, 2, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, W, D, Wout, acc, s, c, fstride);
     else if (g.order == 2)
-        k_step_simple<T, 3, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], W, Wprev, acc, s, c, fstride);
+        k_step_simple<T, 3, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], W, D, Wout, acc, s, c, fstride);
     else
-        k_step_simple<T, 3, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], W, Wprev, acc, s, c, fstride);
+        k_step_simple<T, 3, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], W, D, Wout, acc, s, c, fstride);
     EW_CUDA_TRY(cudaGetLastError());
     fused_end(ev, st, g.N * nvec, g.N * nvec);
     return EW_OK;
@@ -315,25 +370,26 @@ ew_status explicit_wave_solve(const GridGeom& g, const FilterPlan& plan, const T
     if (temporal_block < 0) return set_error(EW_EINVAL, "temporal_block < 0");
     if (use_resident<T>(g, nvec) && temporal_block == 0) return resident<T>(g, vin, vout, cdev, plan, nvec, st);
     // fields are laid out [field][vector][point]
-    const int64_t fstride = g.N;
+    const int64_t fstride = field_stride(g.N);
     T* F[4];
-    for (int q = 0; q < 4; ++q) F[q] = fields + (int64_t)q * nvec * g.N;
+    for (int q = 0; q < 4; ++q) F[q] = fields + (int64_t)q * nvec * fstride;
     const bool blocked = g.dim == 2 && temporal_block != 1;
     // the tuner writes the spare fields and the filter sum, so it runs before the first step
     if (blocked && temporal_block == 0) EW_TRY(tb2d_tune<T>(g, plan, cdev, F, vout, nvec, fstride, st));
+    // F[0] = D^n, F[1] = W^n; the unblocked steps write W^{n+1} to F[2] and swap
     EW_TRY(first_step<T>(g, vin, F[0], F[1], vout, plan, nvec, fstride, st));
     if (blocked) {
         int prv = 0, cur = 1;
         return tb2d_advance<T>(g, plan, cdev, F, &prv, &cur, 1, vout, nvec, fstride, temporal_block, st);
     }
     Stencil<T> s = make_stencil<T>(g, plan.dt * plan.dt);
-    int prv = 0, cur = 1;
+    int cur = 1, nxt = 2;
     for (int64_t L = 1; L < plan.Nt; ++L) {
         if (g.dim == 3)
-            EW_TRY(step3d<T>(g, F[cur], F[prv], vout, T(plan.cn(L + 1)), s, nvec, fstride, st));
+            EW_TRY(step3d<T>(g, F[cur], F[0], F[nxt], vout, T(plan.cn(L + 1)), s, nvec, fstride, st));
         else
-            EW_TRY(step_simple<T>(g, F[cur], F[prv], vout, T(plan.cn(L + 1)), s, nvec, fstride, st));
-        std::swap(prv, cur);
+            EW_TRY(step_simple<T>(g, F[cur], F[0], F[nxt], vout, T(plan.cn(L + 1)), s, nvec, fstride, st));
+        std::swap(cur, nxt);
     }
     return EW_OK;
 }

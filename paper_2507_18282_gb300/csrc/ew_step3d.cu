@@ -1,7 +1,8 @@
 // ew_step3d.cu -- one fused leapfrog + filter step on 3D grids, streamed
 // along z (eqs. explicitScheme, filterQuadrature).
 //
-//   W^{n+1} = 2 W^n - W^{n-1} + dt^2 L_h W^n  (stored over W^{n-1}),  acc += c W^{n+1}
+//   D^{n+1} = D^n + dt^2 L_h W^n (in place),  W^{n+1} = W^n + D^{n+1},  acc += c W^{n+1}
+//   (D^n = W^n - W^{n-1}: the summed form of the leapfrog recurrence)
 //
 // A thread owns one (x, y) column of a z-chunk and marches up z, keeping the
 // column's z-neighbours of W^n in a register queue (one new load per point);
@@ -10,8 +11,8 @@
 // are fixed for the whole march, each x/y neighbour is "offset o with sign s"
 // (s = 1 inside, 0 on a boundary line, -1 for the odd-reflected ghost of the
 // fourth-order stencil), so the step has no branch.  Per point and step the
-// kernel moves W^n, W^{n-1} and the filter sum in and W^{n+1} and the sum out:
-// 20 B (FP32), the unblocked algorithmic traffic.
+// kernel moves W^n, D^n and the filter sum in and D^{n+1}, W^{n+1} and the sum
+// out: 24 B (FP32), the unblocked algorithmic traffic.
 #include <algorithm>
 
 #include "ew_internal.h"
@@ -42,8 +43,8 @@ __device__ __forceinline__ void nb(int i, int d, int n, int& j, int& s) {
 
 template <typename T, int R>
 __global__ void __launch_bounds__(kS3X* kS3Y)
-    k_step3d(int nx, int ny, int nz, const T* __restrict__ W, T* __restrict__ Wprev, T* __restrict__ acc, Stencil<T> st,
-             T c, int64_t fstride) {
+    k_step3d(int nx, int ny, int nz, const T* __restrict__ W, T* __restrict__ D, T* __restrict__ Wout,
+             T* __restrict__ acc, Stencil<T> st, T c) {
     const int x = blockIdx.x * kS3X + threadIdx.x;
     const int y = blockIdx.y * kS3Y + threadIdx.y;
     const int z0 = blockIdx.z * kS3Z;
@@ -85,8 +86,10 @@ __global__ void __launch_bounds__(kS3X* kS3Y)
         if (R == 2)
             lap += st.c2[0] * (fx_m2 * W[p + ox_m2] + fx_p2 * W[p + ox_p2]) +
                    st.c2[1] * (fy_m2 * W[p + oy_m2] + fy_p2 * W[p + oy_p2]) + st.c2[2] * (q[0] + q[4]);
-        const T wn = (T(2) * u - Wprev[p]) + lap;
-        Wprev[p] = wn;
+        const T d = D[p] + lap;
+        const T wn = u + d;
+        D[p] = d;
+        Wout[p] = wn;
         acc[p] += c * wn;
 #pragma unroll
         for (int k = 0; k < 2 * R; ++k) q[k] = q[k + 1];
@@ -95,26 +98,28 @@ __global__ void __launch_bounds__(kS3X* kS3Y)
 }
 
 template <typename T>
-ew_status step3d(const GridGeom& g, const T* W, T* Wprev, T* acc, T c, const Stencil<T>& s, int nvec, int64_t fstride,
-                 cudaStream_t st) {
+ew_status step3d(const GridGeom& g, const T* W, T* D, T* Wout, T* acc, T c, const Stencil<T>& s, int nvec,
+                 int64_t fstride, cudaStream_t st) {
     dim3 grid((unsigned)((g.n[0] + kS3X - 1) / kS3X), (unsigned)((g.n[1] + kS3Y - 1) / kS3Y),
               (unsigned)((g.n[2] + kS3Z - 1) / kS3Z));
     for (int v = 0; v < nvec; ++v) {
         cudaEvent_t ev = fused_begin(st);
         if (g.order == 2)
             k_step3d<T, 1><<<grid, dim3(kS3X, kS3Y), 0, st>>>((int)g.n[0], (int)g.n[1], (int)g.n[2], W + v * fstride,
-                                                              Wprev + v * fstride, acc + v * g.N, s, c, fstride);
+                                                              D + v * fstride, Wout + v * fstride, acc + v * g.N, s,
+                                                              c);
         else
             k_step3d<T, 2><<<grid, dim3(kS3X, kS3Y), 0, st>>>((int)g.n[0], (int)g.n[1], (int)g.n[2], W + v * fstride,
-                                                              Wprev + v * fstride, acc + v * g.N, s, c, fstride);
+                                                              D + v * fstride, Wout + v * fstride, acc + v * g.N, s,
+                                                              c);
         EW_CUDA_TRY(cudaGetLastError());
         fused_end(ev, st, g.N, g.N);
     }
     return EW_OK;
 }
-template ew_status step3d<float>(const GridGeom&, const float*, float*, float*, float, const Stencil<float>&, int,
-                                 int64_t, cudaStream_t);
-template ew_status step3d<double>(const GridGeom&, const double*, double*, double*, double, const Stencil<double>&, int,
-                                  int64_t, cudaStream_t);
+template ew_status step3d<float>(const GridGeom&, const float*, float*, float*, float*, float, const Stencil<float>&,
+                                 int, int64_t, cudaStream_t);
+template ew_status step3d<double>(const GridGeom&, const double*, double*, double*, double*, double,
+                                  const Stencil<double>&, int, int64_t, cudaStream_t);
 
 }  // namespace ew

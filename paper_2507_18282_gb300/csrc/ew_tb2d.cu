@@ -4,19 +4,20 @@
 // (eq. explicitScheme) and adds c_{n+1} W^{n+1} + ... + c_{n+b} W^{n+b} to the
 // filter sum (eq. filterQuadrature) without leaving shared memory.
 //
-// Tiling.  A CTA owns a TX x TY tile.  It stages W^{n-1} and W^n over the tile
+// Tiling.  A CTA owns a TX x TY tile.  It stages D^n = W^n - W^{n-1} (the
+// summed form of the recurrence, see ew_stencil.cu) and W^n over the tile
 // plus a halo of H = R B points (R = stencil radius: 1 for order 2, 2 for
 // order 4) in two shared-memory buffers, and updates the fixed "compute
 // region" (the staged region minus an R-wide rim) B times.  Each step the
 // valid part of the region shrinks by R, so after b steps the owned tile is
 // exact; halo points are recomputed by several CTAs but only owned points are
-// accumulated and stored.  W^{n+b-1}, W^{n+b} go to a second pair of global
+// accumulated and stored.  D^{n+b}, W^{n+b} go to a second pair of global
 // buffers because neighbouring CTAs still read the first pair.
 //
 // Threads.  A warp covers 32 consecutive columns of the compute region and
 // each thread a column segment of KY rows, held as a sliding register window
 // along y, so a point costs five shared-memory loads (centre column entry,
-// x +- 1, x +- 2), the W^{n-1} load and one store per step, and the step needs
+// x +- 1, x +- 2) and one store per step (D^n stays in registers), and the step needs
 // one barrier.
 //
 // Boundary conditions without branches.  Points of the staged region outside
@@ -49,7 +50,21 @@ struct Tb2dVariant {
     size_t smem;
     void* fn;  // kernel pointer
     int minb, fence;
+    int kind = 0;  // 0: shared-memory form (k_step_tb2d), 1: register-blocked persistent form (k_step_rb2d)
+    int rb = -1;   // index into rb2d_variants(R) for kind 1
 };
+
+// FP32 lists also carry the register-blocked forms; the autotuner picks among all
+static std::vector<Tb2dVariant> with_rb2d(std::vector<Tb2dVariant> v, int R) {
+    const auto& rb = rb2d_variants(R);
+    for (size_t i = 0; i < rb.size(); ++i) {
+        Tb2dVariant x{1, rb[i].nty, rb[i].ky, rb[i].B, rb[i].TX, rb[i].TY, rb[i].threads, rb[i].smem, rb[i].fn, 1, 0};
+        x.kind = 1;
+        x.rb = (int)i;
+        v.push_back(x);
+    }
+    return v;
+}
 
 #define EW_TB2D_VARIANT(T, R, NWX, NTY, KY, B, MINB)                                                  \
     Tb2dVariant {                                                                                     \
@@ -64,23 +79,25 @@ static const std::vector<Tb2dVariant>& tb2d_variants();
 // Index 0 of each list is the default used when the caller fixes the depth.
 template <>
 const std::vector<Tb2dVariant>& tb2d_variants<float, 2>() {
-    static const std::vector<Tb2dVariant> v = {
+    static const std::vector<Tb2dVariant> v = with_rb2d({
         EW_TB2D_VARIANT(float, 2, 2, 8, 8, 4, 2),  EW_TB2D_VARIANT(float, 2, 2, 8, 8, 2, 2),
         EW_TB2D_VARIANT(float, 2, 2, 8, 8, 3, 2),  EW_TB2D_VARIANT(float, 2, 2, 16, 8, 4, 1),
         EW_TB2D_VARIANT(float, 2, 2, 16, 8, 6, 1), EW_TB2D_VARIANT(float, 2, 2, 4, 16, 4, 2),
         EW_TB2D_VARIANT(float, 2, 4, 4, 8, 4, 2),  EW_TB2D_VARIANT(float, 2, 2, 8, 12, 4, 1),
         EW_TB2D_VARIANT(float, 2, 2, 16, 8, 8, 1), EW_TB2D_VARIANT(float, 2, 1, 16, 8, 4, 2),
-    };
+        // depths whose tile count fills whole waves of 152 SMs on common grids
+        EW_TB2D_VARIANT(float, 2, 2, 16, 8, 7, 1), EW_TB2D_VARIANT(float, 2, 2, 16, 8, 5, 1),
+    }, 2);
     return v;
 }
 template <>
 const std::vector<Tb2dVariant>& tb2d_variants<float, 1>() {
-    static const std::vector<Tb2dVariant> v = {
+    static const std::vector<Tb2dVariant> v = with_rb2d({
         EW_TB2D_VARIANT(float, 1, 2, 8, 8, 4, 2),  EW_TB2D_VARIANT(float, 1, 2, 8, 8, 8, 2),
         EW_TB2D_VARIANT(float, 1, 2, 8, 8, 2, 2),  EW_TB2D_VARIANT(float, 1, 2, 16, 8, 8, 1),
         EW_TB2D_VARIANT(float, 1, 2, 16, 8, 12, 1), EW_TB2D_VARIANT(float, 1, 2, 4, 16, 8, 2),
         EW_TB2D_VARIANT(float, 1, 4, 4, 8, 8, 2),
-    };
+    }, 1);
     return v;
 }
 template <>
@@ -115,6 +132,12 @@ template <typename T>
 static ew_status launch_variant(const Tb2dVariant& var, const GridGeom& g, const T* Ain, const T* Bin, T* Aout,
                                 T* Bout, T* acc, const T* cw, int b, const Stencil<T>& s, int nvec,
                                 int64_t fstride, cudaStream_t st) {
+    if (var.kind == 1) {
+        if constexpr (sizeof(T) == 4)
+            return rb2d_launch(rb2d_variants(g.order == 2 ? 1 : 2)[(size_t)var.rb], g, Ain, Bin, Aout, Bout, acc, cw, b,
+                               s, nvec, fstride, st);
+        return set_error(EW_EUNSUPPORTED, "register-blocked step is FP32 only");
+    }
     {
         // raise the dynamic shared-memory limit once per kernel and device
         static std::map<std::pair<void*, int>, bool> done;
@@ -148,6 +171,19 @@ static std::mutex g_tune_mu;
 template <typename T>
 static ew_status autotune(const GridGeom& g, T* const* F, T* acc, const T* cw, const Stencil<T>& s, int nvec,
                           int64_t fstride, cudaStream_t st, int* out, bool lookup_only) {
+    const auto& vars = variants_for<T>(g.order);
+    // the register-blocked forms stage rows with 16-byte bulk copies
+    const bool rb_ok = sizeof(T) == 4 && fstride % 4 == 0 &&
+                       (((uintptr_t)F[0] | (uintptr_t)F[1] | (uintptr_t)F[2] | (uintptr_t)F[3]) & 15) == 0;
+    // EW_TB2D_VARIANT=i fixes the variant (index into this precision's and
+    // order's list) instead of timing them: a tuning and testing override
+    if (const char* fv = getenv("EW_TB2D_VARIANT")) {
+        const int i = atoi(fv);
+        if (i < 0 || i >= (int)vars.size() || (vars[(size_t)i].kind == 1 && !rb_ok))
+            return set_error(EW_EINVAL, "EW_TB2D_VARIANT: no such variant for this grid");
+        *out = i;
+        return EW_OK;
+    }
     int dev = 0;
     EW_CUDA_TRY(cudaGetDevice(&dev));
     TuneKey key{g.n[0], g.n[1], g.order, (int)sizeof(T), nvec, dev};
@@ -163,7 +199,6 @@ static ew_status autotune(const GridGeom& g, T* const* F, T* acc, const T* cw, c
             return EW_OK;
         }
     }
-    const auto& vars = variants_for<T>(g.order);
     bool prof = g_profile_on;
     g_profile_on = false;  // tuning launches are not counted
     cudaEvent_t e0, e1;
@@ -174,6 +209,7 @@ static ew_status autotune(const GridGeom& g, T* const* F, T* acc, const T* cw, c
     ew_status status = EW_OK;
     for (size_t i = 0; i < vars.size() && status == EW_OK; ++i) {
         const auto& var = vars[i];
+        if (var.kind == 1 && !rb_ok) continue;
         int b = var.B;
         // one warm launch, then three timed ones
         for (int rep = 0; rep < 4 && status == EW_OK; ++rep) {
@@ -187,9 +223,10 @@ static ew_status autotune(const GridGeom& g, T* const* F, T* acc, const T* cw, c
         double rate = (double)b * 3.0 / std::max(ms, 1e-6f);  // time steps per ms
         if (getenv("EW_TUNE_LOG"))
             fprintf(stderr, "[ew tune] %lldx%lld order %d %s: variant %zu (warps %dx%d, rows %d, depth %d, "
-                            "minb %d, fence %d, tile %dx%d): %.4f ms/step\n",
+                            "minb %d, fence %d, tile %dx%d)%s: %.4f ms/step\n",
                     (long long)g.n[0], (long long)g.n[1], g.order, sizeof(T) == 4 ? "fp32" : "fp64", i, var.nwx,
-                    var.nty, var.ky, var.B, var.minb, var.fence, var.TX, var.TY, 1.0 / rate);
+                    var.nty, var.ky, var.B, var.minb, var.fence, var.TX, var.TY, var.kind ? " register-blocked" : "",
+                    1.0 / rate);
         if (rate > best_rate) {
             best_rate = rate;
             best = (int)i;

@@ -104,14 +104,14 @@ __device__ __forceinline__ void tb2d_tile(int nx, int ny, const T* __restrict__ 
     constexpr int RX = S::RX, RY = S::RY, PX = S::PX, OFF = S::OFF, H = S::H, TX = S::TX, TY = S::TY,
                   NT = S::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sP = reinterpret_cast<T*>(smem_raw);  // W^{n-1} at staging, then the level being written
+    T* sP = reinterpret_cast<T*>(smem_raw);  // D^n at staging, then the level being written
     T* sC = sP + PX * RY;                    // W^n
 
     const int x0 = tile_x * TX - H;  // global coordinate of staged column 0
     const int y0 = tile_y * TY - H;
     const int tid = threadIdx.x;
 
-    // ---- stage W^{n-1}, W^n: asynchronous copies inside the box, the odd
+    // ---- stage D^n, W^n: asynchronous copies inside the box, the odd
     //      extension outside it ---------------------------------------------
     const bool inside = x0 >= 0 && y0 >= 0 && x0 + RX <= nx && y0 + RY <= ny;
     for (int q = tid; q < RX * RY; q += NT) {
@@ -160,16 +160,15 @@ __device__ __forceinline__ void tb2d_tile(int nx, int ny, const T* __restrict__ 
     cp_async_wait_all();
     __syncthreads();
 
-    // W^{n-1} of the thread's own points lives in registers from here on
-    T2 pp[KY];
+    // D^n = W^n - W^{n-1} of the thread's own points lives in registers from here on
+    T2 dd[KY];
 #pragma unroll
-    for (int k = 0; k < KY; ++k) pp[k] = *reinterpret_cast<const T2*>(sP + (sy0 + k) * PX + cx);
+    for (int k = 0; k < KY; ++k) dd[k] = *reinterpret_cast<const T2*>(sP + (sy0 + k) * PX + cx);
 
     const T2 C0{st.c0, st.c0}, C1X{st.c1[0], st.c1[0]}, C1Y{st.c1[1], st.c1[1]};
     const T2 C2X{st.c2[0], st.c2[0]}, C2Y{st.c2[1], st.c2[1]};
-    const T2 TWO{T(2), T(2)}, MONE{T(-1), T(-1)};
     T* cur = sC;
-    T* nxt = sP;  // its old content (W^{n-1}) is only ever read by the owning thread
+    T* nxt = sP;  // its old content (D^n) is only ever read by the owning thread
     for (int s = 0; s < b; ++s) {
         const T* col = cur + cx;
         // the order-2 stencil never reads rows sy0-2 and sy0+KY+1 (outside its staged region)
@@ -197,9 +196,10 @@ __device__ __forceinline__ void tb2d_tile(int nx, int ny, const T* __restrict__ 
                 lap = p_fma(C2X, p_add(L, Q), lap);
                 lap = p_fma(C2Y, p_add(w0, w4), lap);
             }
-            const T2 nv = p_fma(TWO, w2, p_fma(MONE, pp[k], lap));  // 2 W^n + (dt^2 L W^n - W^{n-1})
+            const T2 d = p_add(dd[k], lap);  // D^{n+1} = D^n + dt^2 L W^n
+            const T2 nv = p_add(w2, d);      // W^{n+1} = W^n + D^{n+1}
             *reinterpret_cast<T2*>(nxt + row) = nv;
-            pp[k] = w2;
+            dd[k] = d;
             accp[k] = p_fma(CS, nv, accp[k]);  // only owned entries are stored
             w0 = w1;
             w1 = w2;
@@ -211,7 +211,7 @@ __device__ __forceinline__ void tb2d_tile(int nx, int ny, const T* __restrict__ 
         cur = nxt;
         nxt = t;
     }
-    // cur = W^{n+b} (shared), pp = W^{n+b-1} (registers)
+    // cur = W^{n+b} (shared), dd = D^{n+b} (registers)
     int64_t base = (int64_t)gy0 * nx + gx;
     asm volatile("" : "+l"(base));
 #pragma unroll
@@ -221,12 +221,12 @@ __device__ __forceinline__ void tb2d_tile(int nx, int ny, const T* __restrict__ 
             const int64_t g = base + (int64_t)k * nx;
             if (own_a) {
                 Bout[g] = c2.x;
-                Aout[g] = pp[k].x;
+                Aout[g] = dd[k].x;
                 acc[g] = accp[k].x;
             }
             if (own_b) {
                 Bout[g + 1] = c2.y;
-                Aout[g + 1] = pp[k].y;
+                Aout[g + 1] = dd[k].y;
                 acc[g + 1] = accp[k].y;
             }
         }

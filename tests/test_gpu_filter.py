@@ -90,6 +90,31 @@ def test_tiling_variants_bit_identical(ew):
     assert np.array_equal(a, b) and np.array_equal(a, c)
 
 
+@pytest.mark.parametrize("order", [2, 4])
+def test_every_tiling_variant_bit_identical(ew, order, monkeypatch):
+    """Every 2D FP32 variant -- tile shape, temporal depth, and kernel form
+    (shared-memory tiles or the register-blocked persistent kernel with bulk
+    row copies) -- performs the same operations per point, so forcing each in
+    turn gives the same result bit for bit.  700 x 900 with 3 vectors spans
+    more tiles than SMs (persistent CTAs walk several tiles) with ragged tiles
+    on two sides."""
+    n, L = (700, 900), (1.0, 1.3)
+    ref, count = None, 0
+    for i in range(64):
+        monkeypatch.setenv("EW_TB2D_VARIANT", str(i))
+        try:
+            _, out, _ = _run(ew, n, L, order, "fp32", 45.0, nvec=3, seed=21)
+        except ew.EWError as e:  # past the end of the list
+            assert "EW_TB2D_VARIANT" in str(e)
+            break
+        assert np.all(np.isfinite(out))
+        if ref is None:
+            ref = out
+        assert np.array_equal(out, ref), "variant %d differs" % i
+        count += 1
+    assert count >= 8
+
+
 def test_fp64_blocked_equals_simple(ew):
     """Temporal blocking changes only rounding order: depth 4 vs depth 1."""
     v, a, _ = _run(ew, (300, 140), (1.0, 0.5), 4, "fp64", 40.0, Np=2, tb=4)
@@ -173,6 +198,25 @@ def test_full_size_random_parity_rectangle(ew):
     # sampled points one by one
     idx = np.array([0, 2046, 2047, 1234567, n[0] * n[1] - 1])
     assert np.max(np.abs(out[idx] - ref[idx])) < 4 * info["Nt"] * EPS32
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_stencil_coefficients_exactly_consistent(ew, order, prec):
+    """The stored stencil coefficients sum to exactly zero, so L_h applied to
+    the constant 1 is exactly 0 away from the boundary.  Coefficients rounded
+    one by one would leave a mass term of about eps |c0|: in FP32 on fine grids
+    a frequency error of up to 1e-2 for the low modes."""
+    n, L = (2047, 301), (1.0, 0.147)
+    g = ew.ew_grid_create(2, n, L, order=order, prec=prec)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    x = torch.ones(n[0] * n[1], dtype=dt, device="cuda")
+    y = torch.empty_like(x)
+    ew.ew_apply_L(g, x, y)
+    torch.cuda.synchronize()
+    Y = y.cpu().numpy().reshape(n[1], n[0])
+    assert np.all(Y[2:-2, 2:-2] == 0.0)
+    g.close()
 
 
 def test_apply_L_and_rayleigh(ew):
