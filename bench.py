@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--temporal-block", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--workload", choices=["rect2d", "cube3d", "batched", "implicit3d", "eigs2d"], default="rect2d",
+    ap.add_argument("--workload", choices=["rect2d", "cube3d", "batched", "implicit3d", "mg3d", "eigs2d"],
+                    default="rect2d",
                     help="rect2d is the headline line; the others print their own line")
     ap.add_argument("--num-periods", type=int, default=64, help="N_p of the eigs2d workload")
     return ap.parse_args()
@@ -413,10 +414,10 @@ def run_extra(args):
         cells = g.size * info["Nt"] * args.steps
         launches = max(prof["fused_launches"], 1)
         mean = prof["fused_ms"] / launches
-        bytes_launch = 24 * prof["fused_points"] / launches  # one step per launch: W^n, D^n, acc in; W^{n+1}, D^{n+1}, acc out
+        bytes_launch = 24 * prof["fused_points"] / launches  # per launch: W^n, D^n, acc in; W^{n+b}, D^{n+b}, acc out
         line = dict(workload="cube3d_511_order2_fp32_explicit", metric=METRIC, unit=UNIT,
                     value=cells / (ms / 1e3) / 1e9, ms_per_step=ms / args.steps, time_steps_per_step=info["Nt"],
-                    roofline=dict(bound="hbm", kernel="k_step3d<float,1>", bytes_per_launch=bytes_launch,
+                    roofline=dict(bound="hbm", kernel="k_step_tb3d<float,4>", bytes_per_launch=bytes_launch,
                                   achieved=bytes_launch / (mean / 1e3) / 1e9, peak=pk["hbm_gbs"], unit="GB/s",
                                   frac=bytes_launch / (mean / 1e3) / 1e9 / pk["hbm_gbs"], peak_source=pk_kind))
     elif w == "batched":
@@ -463,6 +464,27 @@ def run_extra(args):
                              gcell_steps_per_s=g.size * info["Nt"] / (ms / max(1, args.steps // 4) / 1e3) / 1e9)
         line = dict(workload="implicit3d_255_order4_fp32_mg_v22", unit="ms", train=rep, train_seconds=train_s,
                     plain=res["plain"], learned=res["learned"])
+    elif w == "mg3d":
+        # one V(2,2) cycle of M = I - (dt^2/2) L_h on 255^3 order 4 FP32 (the implicit
+        # step of the 10-steps-per-period scheme at omega = 80): plain Jacobi smoothing
+        # and the learned smoother on the finest level (seeded weights: speed only)
+        n, L = (255, 255, 255), (1.0, 1.0, 1.0)
+        g = ew.ew_grid_create(3, n, L, order=4, prec="fp32")
+        probe = ew.filter_params(80.0, num_periods=1, steps_per_period=10, scheme="implicit", adjust_omega=True,
+                                 mg=ew.mg_params())
+        info, _ = ew.ew_filter_setup(g, probe)
+        a = 0.5 * info["dt"] ** 2
+        wts = torch.tensor(ew_inputs.learned_init(36, 0.05), dtype=torch.float32, device="cuda")
+        rhs = torch.tensor(ew_inputs.uniform_pm1(ew_inputs.BASE_SEED + 5, g.size), dtype=torch.float32, device="cuda")
+        x = torch.zeros_like(rhs)
+        res = {}
+        for name, learned in [("plain", 0), ("learned", 1)]:
+            one = ew.mg_params(pre=2, post=2, max_cycles=1, learned_levels=learned, weights=wts if learned else None)
+            t = _timed(lambda: ew.ew_implicit_step_mg(g, a, rhs, x, one), args.steps, args.warmup, flush)
+            res[name] = dict(ms_per_vcycle=t / args.steps)
+        # fine-level sweep traffic: a Jacobi sweep reads x, b and writes x (12 B per point)
+        line = dict(workload="mg3d_255_order4_fp32_vcycle22", unit="ms", plain=res["plain"], learned=res["learned"],
+                    points=g.size, fine_sweep_bytes=12 * g.size)
     elif w == "eigs2d":
         # time to the 8 eigenpairs nearest omega = 150 on the 2047 x 3071 order-4 rectangle:
         # FP32 wave-solves + FP64 refinement against FP64 wave-solves throughout

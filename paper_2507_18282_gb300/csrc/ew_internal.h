@@ -115,6 +115,11 @@ ew_status launch_apply_L(const GridGeom& g, const T* u, T* Lu, int nvec, double 
 
 // one explicit wave-solve for nvec vectors; fields = 4 * N * nvec elements
 // of scratch; cdev = N_t + 1 weights (device, type T).
+// temporally blocked 3D second-order steps (ew_tb3d.cu)
+template <typename T>
+ew_status tb3d_advance(const GridGeom& g, const FilterPlan& plan, const T* cdev, T* const* F, int* prv, int* cur,
+                       int64_t L, T* acc, int nvec, int64_t fstride, int tb, cudaStream_t st);
+
 // register-blocked persistent form of the 2D FP32 blocked step (ew_rb2d.cu)
 struct Rb2dDesc {
     void* fn;

@@ -65,6 +65,14 @@ static int grid_blocks(int64_t N, int threads) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
+// one thread per point: x from the block's threads, y and z from the grid (no
+// integer division in the kernels)
+static int pt_threads(int64_t nx) { return nx >= 128 ? 128 : (int)(((nx + 31) / 32) * 32); }
+static dim3 pt_grid(int64_t nx, int64_t ny, int64_t nz) {
+    const int t = pt_threads(nx);
+    return dim3((unsigned)((nx + t - 1) / t), (unsigned)ny, (unsigned)nz);
+}
+
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
@@ -72,23 +80,21 @@ static int grid_blocks(int64_t N, int threads) {
 template <typename T, int DIM, int ORDER>
 __global__ void k_mg_resid(int64_t nx, int64_t ny, int64_t nz, const T* __restrict__ x, const T* __restrict__ b,
                            T* __restrict__ r, Stencil<T> sa) {
-    const int64_t N = nx * ny * nz;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = q % nx, t = q / nx, j = t % ny, k = t / ny;
-        r[q] = (b[q] - x[q]) + lap_global<T, DIM, ORDER>(x, sa, q, i, j, k, nx, ny, nz);
-    }
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    const int64_t j = blockIdx.y, k = blockIdx.z, q = (k * ny + j) * nx + i;
+    r[q] = (b[q] - x[q]) + lap_global<T, DIM, ORDER>(x, sa, q, i, j, k, nx, ny, nz);
 }
 
 // x_out = x_in + wd (b - M x_in), wd = w / D
 template <typename T, int DIM, int ORDER>
 __global__ void k_mg_jacobi(int64_t nx, int64_t ny, int64_t nz, const T* __restrict__ x, const T* __restrict__ b,
                             T* __restrict__ xo, Stencil<T> sa, T wd) {
-    const int64_t N = nx * ny * nz;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = q % nx, t = q / nx, j = t % ny, k = t / ny;
-        T r = (b[q] - x[q]) + lap_global<T, DIM, ORDER>(x, sa, q, i, j, k, nx, ny, nz);
-        xo[q] = x[q] + wd * r;
-    }
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    const int64_t j = blockIdx.y, k = blockIdx.z, q = (k * ny + j) * nx + i;
+    T r = (b[q] - x[q]) + lap_global<T, DIM, ORDER>(x, sa, q, i, j, k, nx, ny, nz);
+    xo[q] = x[q] + wd * r;
 }
 
 template <typename T>
@@ -102,10 +108,11 @@ __device__ __forceinline__ T get0(const T* __restrict__ v, int64_t i, int64_t j,
 template <typename T, int DIM>
 __global__ void k_mg_restrict(int64_t fx, int64_t fy, int64_t fz, int64_t cx, int64_t cy, int64_t cz,
                               const T* __restrict__ r, T* __restrict__ bc, T* __restrict__ xc) {
-    const int64_t N = cx * cy * cz;
     const T w[3] = {T(0.25), T(0.5), T(0.25)};
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t I = q % cx, t = q / cx, J = t % cy, K = t / cy;
+    {
+        const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        if (I >= cx) return;
+        const int64_t J = blockIdx.y, K = blockIdx.z, q = (K * cy + J) * cx + I;
         int64_t fi = 2 * I + 1, fj = 2 * J + 1, fk = DIM == 3 ? 2 * K + 1 : 0;
         T s = T(0);
         for (int oz = (DIM == 3 ? -1 : 0); oz <= (DIM == 3 ? 1 : 0); ++oz)
@@ -123,9 +130,10 @@ __global__ void k_mg_restrict(int64_t fx, int64_t fy, int64_t fz, int64_t cx, in
 template <typename T, int DIM>
 __global__ void k_mg_prolong(int64_t fx, int64_t fy, int64_t fz, int64_t cx, int64_t cy, int64_t cz,
                              const T* __restrict__ ec, T* __restrict__ xf) {
-    const int64_t N = fx * fy * fz;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = q % fx, t = q / fx, j = t % fy, k = t / fy;
+    {
+        const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        if (i >= fx) return;
+        const int64_t j = blockIdx.y, k = blockIdx.z, q = (k * fy + j) * fx + i;
         int64_t ci[2], cj[2], ck[2];
         T wi[2], wj[2], wk[2];
         int ni, nj, nk;
@@ -251,6 +259,8 @@ struct MGSolver {
         st = s;
         wJ = params->jacobi_weight > 0 ? params->jacobi_weight : 0.8;
         nlev = mg_levels(g->geom, lv, 16);
+        if (g->geom.n[1] > 65535 || g->geom.n[2] > 65535)
+            return set_error(EW_EUNSUPPORTED, "multigrid: axes longer than 65535 points");
         if (lv[nlev - 1].N > kCoarseMax)
             return set_error(EW_EUNSUPPORTED, "multigrid needs axes that halve down to at most 2048 coarse points "
                                               "(n = 2^k - 1 per axis, for example)");
@@ -281,11 +291,12 @@ struct MGSolver {
 #define EW_MG_DISPATCH(KERN, GEOM, ...)                                                                  \
     do {                                                                                                 \
         const GridGeom& g_ = (GEOM);                                                                     \
-        dim3 grid_(grid_blocks(g_.N, 256));                                                              \
-        if (g_.dim == 2 && g_.order == 2) KERN<T, 2, 2><<<grid_, 256, 0, st>>>(g_.n[0], g_.n[1], 1, __VA_ARGS__); \
-        else if (g_.dim == 2) KERN<T, 2, 4><<<grid_, 256, 0, st>>>(g_.n[0], g_.n[1], 1, __VA_ARGS__);             \
-        else if (g_.order == 2) KERN<T, 3, 2><<<grid_, 256, 0, st>>>(g_.n[0], g_.n[1], g_.n[2], __VA_ARGS__);     \
-        else KERN<T, 3, 4><<<grid_, 256, 0, st>>>(g_.n[0], g_.n[1], g_.n[2], __VA_ARGS__);                        \
+        const int nz_ = g_.dim == 3 ? (int)g_.n[2] : 1;                                                 \
+        dim3 grid_ = pt_grid(g_.n[0], g_.n[1], nz_), blk_(pt_threads(g_.n[0]));                          \
+        if (g_.dim == 2 && g_.order == 2) KERN<T, 2, 2><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], 1, __VA_ARGS__); \
+        else if (g_.dim == 2) KERN<T, 2, 4><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], 1, __VA_ARGS__);             \
+        else if (g_.order == 2) KERN<T, 3, 2><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], g_.n[2], __VA_ARGS__);     \
+        else KERN<T, 3, 4><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], g_.n[2], __VA_ARGS__);                        \
         count_launch();                                                                                  \
     } while (0)
 
@@ -329,20 +340,21 @@ struct MGSolver {
         Stencil<T> sa = make_stencil<T>(lv[L], a);
         EW_MG_DISPATCH(k_mg_resid, lv[L], X[L], B[L], R[L], sa);
         const GridGeom &f = lv[L], &c = lv[L + 1];
+        const int fz = f.dim == 3 ? (int)f.n[2] : 1, cz = f.dim == 3 ? (int)c.n[2] : 1;
         if (f.dim == 2)
-            k_mg_restrict<T, 2><<<grid_blocks(c.N, 256), 256, 0, st>>>(f.n[0], f.n[1], f.n[2], c.n[0], c.n[1], c.n[2],
-                                                                      R[L], B[L + 1], X[L + 1]);
+            k_mg_restrict<T, 2><<<pt_grid(c.n[0], c.n[1], cz), pt_threads(c.n[0]), 0, st>>>(
+                f.n[0], f.n[1], fz, c.n[0], c.n[1], cz, R[L], B[L + 1], X[L + 1]);
         else
-            k_mg_restrict<T, 3><<<grid_blocks(c.N, 256), 256, 0, st>>>(f.n[0], f.n[1], f.n[2], c.n[0], c.n[1], c.n[2],
-                                                                      R[L], B[L + 1], X[L + 1]);
+            k_mg_restrict<T, 3><<<pt_grid(c.n[0], c.n[1], cz), pt_threads(c.n[0]), 0, st>>>(
+                f.n[0], f.n[1], fz, c.n[0], c.n[1], cz, R[L], B[L + 1], X[L + 1]);
         count_launch();
         EW_TRY(vcycle(L + 1));
         if (f.dim == 2)
-            k_mg_prolong<T, 2><<<grid_blocks(f.N, 256), 256, 0, st>>>(f.n[0], f.n[1], f.n[2], c.n[0], c.n[1], c.n[2],
-                                                                     X[L + 1], X[L]);
+            k_mg_prolong<T, 2><<<pt_grid(f.n[0], f.n[1], fz), pt_threads(f.n[0]), 0, st>>>(
+                f.n[0], f.n[1], fz, c.n[0], c.n[1], cz, X[L + 1], X[L]);
         else
-            k_mg_prolong<T, 3><<<grid_blocks(f.N, 256), 256, 0, st>>>(f.n[0], f.n[1], f.n[2], c.n[0], c.n[1], c.n[2],
-                                                                     X[L + 1], X[L]);
+            k_mg_prolong<T, 3><<<pt_grid(f.n[0], f.n[1], fz), pt_threads(f.n[0]), 0, st>>>(
+                f.n[0], f.n[1], fz, c.n[0], c.n[1], cz, X[L + 1], X[L]);
         count_launch();
         EW_TRY(smooth(L, p->post));
         EW_CUDA_TRY(cudaGetLastError());
@@ -440,11 +452,11 @@ static ew_status step_mg_t(ew_grid* g, double a, const T* rhs, T* x, const ew_mg
         T* r = mg.R[0];
         {
             const GridGeom& gg = g->geom;
-            dim3 grid_(grid_blocks(gg.N, 256));
-            if (gg.dim == 2 && gg.order == 2) k_mg_resid<T, 2, 2><<<grid_, 256, 0, st>>>(gg.n[0], gg.n[1], 1, mg.X[0], mg.B[0], r, sa);
-            else if (gg.dim == 2) k_mg_resid<T, 2, 4><<<grid_, 256, 0, st>>>(gg.n[0], gg.n[1], 1, mg.X[0], mg.B[0], r, sa);
-            else if (gg.order == 2) k_mg_resid<T, 3, 2><<<grid_, 256, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
-            else k_mg_resid<T, 3, 4><<<grid_, 256, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
+            dim3 grid_ = pt_grid(gg.n[0], gg.n[1], gg.dim == 3 ? gg.n[2] : 1), blk_(pt_threads(gg.n[0]));
+            if (gg.dim == 2 && gg.order == 2) k_mg_resid<T, 2, 2><<<grid_, blk_, 0, st>>>(gg.n[0], gg.n[1], 1, mg.X[0], mg.B[0], r, sa);
+            else if (gg.dim == 2) k_mg_resid<T, 2, 4><<<grid_, blk_, 0, st>>>(gg.n[0], gg.n[1], 1, mg.X[0], mg.B[0], r, sa);
+            else if (gg.order == 2) k_mg_resid<T, 3, 2><<<grid_, blk_, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
+            else k_mg_resid<T, 3, 4><<<grid_, blk_, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
             count_launch();
         }
         EW_TRY(launch_dots<T>(r, r, N, 1, dpart, dres, st));
@@ -503,11 +515,11 @@ ew_status mg_collect_residuals(ew_grid* g, double a, const ew_mg_params* mp, int
         for (int c = 0; c < 3 && k < nsamples && s == EW_OK; ++c) {
             float* r = out + (size_t)k * N;
             const GridGeom& gg = g->geom;
-            dim3 grid_(grid_blocks(gg.N, 256));
+            dim3 grid_ = pt_grid(gg.n[0], gg.n[1], gg.n[2]), blk_(pt_threads(gg.n[0]));
             if (gg.order == 2)
-                k_mg_resid<float, 3, 2><<<grid_, 256, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
+                k_mg_resid<float, 3, 2><<<grid_, blk_, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
             else
-                k_mg_resid<float, 3, 4><<<grid_, 256, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
+                k_mg_resid<float, 3, 4><<<grid_, blk_, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
             count_launch();
             ++k;
             s = mg.vcycle(0);

@@ -194,14 +194,188 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
     w[e] -= lr * mh / (sqrtf(vh) + eps);
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core forward (FP32 fields): both layers on BF16 mma.sync.m16n8k16
+// with FP32 accumulation.
+//
+//   layer 1  H[q][c]  = sum_k A[q][k] B1[k][c]   A = im2col of r (k = tap,
+//            27 padded to 32), B1[k][c] = W1[c][k]; 16 hidden points per MMA row
+//            block, N = 8 channels
+//   layer 2  Z[q][o]  = sum_c H[q][c] B2[c][o]  B2[c][o] = W2[c][o] (K = 8
+//            channels padded to 16, N = 27 taps padded to 32): the accumulator
+//            fragment of layer 1, rounded to BF16, is exactly the A fragment of
+//            layer 2 (row q, k = c), so H never leaves registers
+//   output   N(r)(x) = sum_o Z[x + o][o]   (27-term gather from shared memory)
+//
+// Hidden points outside the box are zero (the second convolution's zero
+// padding).  Tile: 8 x 8 x 4 outputs, 10 x 10 x 6 hidden points, 12 x 12 x 8
+// residual points, 8 warps.
+// ---------------------------------------------------------------------------
+constexpr int kTX = 8, kTY = 8, kTZ = 4;                    // output tile
+constexpr int kHX = kTX + 2, kHY = kTY + 2, kHZ = kTZ + 2;  // hidden region
+constexpr int kRX = kTX + 4, kRY = kTY + 4, kRZ = kTZ + 4;  // staged residual
+constexpr int kHN = kHX * kHY * kHZ;                        // 600 hidden points
+constexpr int kHG = (kHN + 15) / 16;                        // 38 row blocks of 16
+constexpr int kZS = kHG * 16 + 4;                           // Z row stride (612: conflict-free stores)
+constexpr int kTcThreads = 256;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <bool ADD>
+__global__ void __launch_bounds__(kTcThreads)
+    k_smoother_fwd_tc(int nx, int ny, int nz, const float* __restrict__ w, const float* __restrict__ r,
+                      float* __restrict__ out) {
+    extern __shared__ __align__(16) float smem_tc[];
+    float* sR = smem_tc;                   // kRX * kRY * kRZ
+    float* sZ = smem_tc + kRX * kRY * kRZ;  // 27 * kZS
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, tig = lane & 3;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z * kTZ;
+    // staged residual (BF16-rounded, zero outside the box), origin (x0-2, y0-2, z0-2)
+    for (int q = tid; q < kRX * kRY * kRZ; q += kTcThreads) {
+        int lx = q % kRX, t = q / kRX, ly = t % kRY, lz = t / kRY;
+        sR[q] = ld_r(r, x0 - 2 + lx, y0 - 2 + ly, z0 - 2 + lz, nx, ny, nz);
+    }
+    // B fragments (fixed per thread).  Layer 1, k-step s: b0 = B1[16s + 2tig (+1)][g],
+    // b1 = B1[16s + 2tig + 8 (+1)][g] with B1[k][c] = W1[c][k] (0 for k >= 27).
+    auto w1 = [&](int k, int c) { return k < 27 ? w[c * 27 + k] : 0.f; };
+    uint32_t b1f[2][2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        b1f[s][0] = pack_bf16(w1(16 * s + 2 * tig, g), w1(16 * s + 2 * tig + 1, g));
+        b1f[s][1] = pack_bf16(w1(16 * s + 2 * tig + 8, g), w1(16 * s + 2 * tig + 9, g));
+    }
+    // layer 2, n-tile j: b0 = B2[2tig (+1)][8j + g] = W2[2tig (+1)][8j + g], b1 = 0 (k >= 8)
+    uint32_t b2f[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int o = 8 * j + g;
+        b2f[j] = o < 27 ? pack_bf16(w[kW + (2 * tig) * 27 + o], w[kW + (2 * tig + 1) * 27 + o]) : 0u;
+    }
+    // this thread's im2col taps: k-step s holds taps 16s + {2tig, 2tig+1, 2tig+8, 2tig+9}
+    int toff[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int k = 16 * (e >> 2) + 2 * tig + (e & 1) + ((e >> 1) & 1) * 8;
+        const int kk = k < 27 ? k : 0;  // padded taps read a valid point, times a zero weight
+        toff[e] = ((kk / 9) * kRY + (kk / 3) % 3) * kRX + kk % 3;
+    }
+    __syncthreads();
+    for (int G = warp; G < kHG; G += kTcThreads / 32) {
+        // rows g and g + 8 of the block: hidden points q0, q1
+        const int q0 = 16 * G + g, q1 = q0 + 8;
+        auto hpos = [&](int q, int& base, bool& in) {
+            const int hx = q % kHX, t = q / kHX, hy = t % kHY, hz = t / kHY;
+            base = (hz * kRY + hy) * kRX + hx;  // residual index of tap (0,0,0) = offset (-1,-1,-1)
+            const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
+            in = q < kHN && gx >= 0 && gy >= 0 && gz >= 0 && gx < nx && gy < ny && gz < nz;
+            if (q >= kHN) base = 0;
+        };
+        int bq0, bq1;
+        bool in0, in1;
+        hpos(q0, bq0, in0);
+        hpos(q1, bq1, in1);
+        float h[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            uint32_t a[4];
+            a[0] = pack_bf16(sR[bq0 + toff[4 * s + 0]], sR[bq0 + toff[4 * s + 1]]);
+            a[1] = pack_bf16(sR[bq1 + toff[4 * s + 0]], sR[bq1 + toff[4 * s + 1]]);
+            a[2] = pack_bf16(sR[bq0 + toff[4 * s + 2]], sR[bq0 + toff[4 * s + 3]]);
+            a[3] = pack_bf16(sR[bq1 + toff[4 * s + 2]], sR[bq1 + toff[4 * s + 3]]);
+            mma_bf16(h, a, b1f[s][0], b1f[s][1]);
+        }
+        // h: (row g, channels 2tig, 2tig+1) and (row g+8, same): zero outside the box,
+        // round to BF16 -> the A fragment of layer 2 (k = channel; k >= 8 zero)
+        uint32_t a2[4];
+        a2[0] = in0 ? pack_bf16(h[0], h[1]) : 0u;
+        a2[1] = in1 ? pack_bf16(h[2], h[3]) : 0u;
+        a2[2] = 0u;
+        a2[3] = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float z[4] = {0.f, 0.f, 0.f, 0.f};
+            mma_bf16(z, a2, b2f[j], 0u);
+            const int o = 8 * j + 2 * tig;
+            if (o < 27) {
+                sZ[o * kZS + q0] = z[0];
+                sZ[o * kZS + q1] = z[2];
+            }
+            if (o + 1 < 27) {
+                sZ[(o + 1) * kZS + q0] = z[1];
+                sZ[(o + 1) * kZS + q1] = z[3];
+            }
+        }
+    }
+    __syncthreads();
+    // output x = (lx, ly, lz): sum over taps o of Z[x + o][o]
+    {
+        const int lx = tid % kTX, t = tid / kTX, ly = t % kTY, lz = t / kTY;
+        const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+        if (gx < nx && gy < ny && gz < nz) {
+            float sacc = 0.f;
+            int o = 0;
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx, ++o)
+                        sacc += sZ[o * kZS + ((lz + dz) * kHY + (ly + dy)) * kHX + (lx + dx)];
+            const int64_t gi = ((int64_t)gz * ny + gy) * nx + gx;
+            if (ADD)
+                out[gi] += sacc;
+            else
+                out[gi] = sacc;
+        }
+    }
+}
+
+constexpr size_t kTcSmem = sizeof(float) * ((size_t)kRX * kRY * kRZ + 27 * (size_t)kZS);
+
+template <bool ADD>
+static ew_status launch_fwd_tc(const GridGeom& g, const float* w, const float* r, float* out, cudaStream_t st);
+
+static dim3 tc_tiles(const GridGeom& g) {
+    return dim3((unsigned)((g.n[0] + kTX - 1) / kTX), (unsigned)((g.n[1] + kTY - 1) / kTY),
+                (unsigned)((g.n[2] + kTZ - 1) / kTZ));
+}
+
+template <bool ADD>
+static ew_status launch_fwd_tc(const GridGeom& g, const float* w, const float* r, float* out, cudaStream_t st) {
+    static bool attr = false;  // raised once per process (same value on every device)
+    if (!attr) {
+        EW_CUDA_TRY(cudaFuncSetAttribute(k_smoother_fwd_tc<ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTcSmem));
+        attr = true;
+    }
+    k_smoother_fwd_tc<ADD><<<tc_tiles(g), kTcThreads, kTcSmem, st>>>((int)g.n[0], (int)g.n[1], (int)g.n[2], w, r, out);
+    EW_CUDA_TRY(cudaGetLastError());
+    return EW_OK;
+}
+
 static dim3 tiles(const GridGeom& g) {
     return dim3((unsigned)((g.n[0] + kTile - 1) / kTile), (unsigned)((g.n[1] + kTile - 1) / kTile),
                 (unsigned)((g.n[2] + kTile - 1) / kTile));
 }
 
+// x += N(r): tensor cores for FP32 fields, the CUDA-core kernel for FP64 ones
 template <typename T>
 ew_status smoother_apply(const GridGeom& g, const float* weights, const T* r, T* x, cudaStream_t st) {
-    k_smoother_fwd<T, true><<<tiles(g), kThreads, 0, st>>>((int)g.n[0], (int)g.n[1], (int)g.n[2], weights, r, x);
+    if constexpr (sizeof(T) == 4)
+        EW_TRY(launch_fwd_tc<true>(g, weights, r, x, st));
+    else
+        k_smoother_fwd<T, true><<<tiles(g), kThreads, 0, st>>>((int)g.n[0], (int)g.n[1], (int)g.n[2], weights, r, x);
     EW_CUDA_TRY(cudaGetLastError());
     count_launch();
     return EW_OK;
@@ -211,7 +385,10 @@ template ew_status smoother_apply<double>(const GridGeom&, const float*, const d
 
 template <typename T>
 static ew_status smoother_forward_t(const GridGeom& g, const float* w, const T* r, T* y, cudaStream_t st) {
-    k_smoother_fwd<T, false><<<tiles(g), kThreads, 0, st>>>((int)g.n[0], (int)g.n[1], (int)g.n[2], w, r, y);
+    if constexpr (sizeof(T) == 4)
+        EW_TRY(launch_fwd_tc<false>(g, w, r, y, st));
+    else
+        k_smoother_fwd<T, false><<<tiles(g), kThreads, 0, st>>>((int)g.n[0], (int)g.n[1], (int)g.n[2], w, r, y);
     EW_CUDA_TRY(cudaGetLastError());
     count_launch();
     return EW_OK;

@@ -101,14 +101,12 @@ template <typename T, int DIM, int ORDER>
 __global__ void k_apply_L(int64_t nx, int64_t ny, int64_t nz, const T* __restrict__ u,
                           T* __restrict__ Lu, Stencil<T> s) {
     const int64_t N = nx * ny * nz;
-    const int64_t v = blockIdx.y;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    const int64_t v = blockIdx.z / nz, k = blockIdx.z - v * nz, j = blockIdx.y, q = (k * ny + j) * nx + i;
     u += v * N;
     Lu += v * N;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = q % nx, t = q / nx, j = t % ny, k = t / ny;
-        Lu[q] = lap_global<T, DIM, ORDER>(u, s, q, i, j, k, nx, ny, nz);
-    }
+    Lu[q] = lap_global<T, DIM, ORDER>(u, s, q, i, j, k, nx, ny, nz);
 }
 
 // a3: D^1 = (dt^2/2) L V, W^1 = V + D^1, V_out = c0 W^0 + c1 W^1.  `s`
@@ -118,21 +116,19 @@ __global__ void k_first_step(int64_t nx, int64_t ny, int64_t nz, const T* __rest
                              T* __restrict__ D1, T* __restrict__ W1, T* __restrict__ vout,
                              Stencil<T> s, T c0, T c1, int64_t fstride) {
     const int64_t N = nx * ny * nz;
-    const int64_t v = blockIdx.y;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    const int64_t v = blockIdx.z / nz, k = blockIdx.z - v * nz, j = blockIdx.y, q = (k * ny + j) * nx + i;
     vin += v * N;
     vout += v * N;
     D1 += v * fstride;
     W1 += v * fstride;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = q % nx, t = q / nx, j = t % ny, k = t / ny;
-        T x = vin[q];
-        T d = lap_global<T, DIM, ORDER>(vin, s, q, i, j, k, nx, ny, nz);
-        T w1 = x + d;
-        D1[q] = d;
-        W1[q] = w1;
-        vout[q] = c0 * x + c1 * w1;
-    }
+    T x = vin[q];
+    T d = lap_global<T, DIM, ORDER>(vin, s, q, i, j, k, nx, ny, nz);
+    T w1 = x + d;
+    D1[q] = d;
+    W1[q] = w1;
+    vout[q] = c0 * x + c1 * w1;
 }
 
 // one step: D <- D + dt^2 L W (in place), Wout <- W + D, acc += c Wout
@@ -141,20 +137,18 @@ __global__ void k_step_simple(int64_t nx, int64_t ny, int64_t nz, const T* __res
                               T* __restrict__ D, T* __restrict__ Wout, T* __restrict__ acc, Stencil<T> s, T c,
                               int64_t fstride) {
     const int64_t N = nx * ny * nz;
-    const int64_t v = blockIdx.y;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    const int64_t v = blockIdx.z / nz, k = blockIdx.z - v * nz, j = blockIdx.y, q = (k * ny + j) * nx + i;
     W += v * fstride;
     D += v * fstride;
     Wout += v * fstride;
     acc += v * N;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = q % nx, t = q / nx, j = t % ny, k = t / ny;
-        T d = D[q] + lap_global<T, DIM, ORDER>(W, s, q, i, j, k, nx, ny, nz);
-        T wn = W[q] + d;
-        D[q] = d;
-        Wout[q] = wn;
-        acc[q] += c * wn;
-    }
+    T d = D[q] + lap_global<T, DIM, ORDER>(W, s, q, i, j, k, nx, ny, nz);
+    T wn = W[q] + d;
+    D[q] = d;
+    Wout[q] = wn;
+    acc[q] += c * wn;
 }
 
 // ---------------------------------------------------------------------------
@@ -260,26 +254,37 @@ __global__ void __launch_bounds__(1024)
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static int grid_blocks(int64_t N, int threads) {
-    int64_t b = (N + threads - 1) / threads;
-    if (b > 152 * 16) b = 152 * 16;
-    if (b < 1) b = 1;
-    return (int)b;
+// one thread per point: x from the block's threads, y from grid.y, z and the
+// vector from grid.z (no integer division by the grid shape in the kernels)
+static int pt_threads(int64_t nx) { return nx >= 128 ? 128 : (int)(((nx + 31) / 32) * 32); }
+static dim3 pt_grid(const GridGeom& g, int nvec) {
+    const int t = pt_threads(g.n[0]);
+    const int64_t nz = g.dim == 3 ? g.n[2] : 1;
+    return dim3((unsigned)((g.n[0] + t - 1) / t), (unsigned)g.n[1], (unsigned)(nz * nvec));
 }
+
+static ew_status pt_check(const GridGeom& g, int nvec) {
+    const int64_t nz = g.dim == 3 ? g.n[2] : 1;
+    if (g.n[1] > 65535 || nz * nvec > 65535)
+        return set_error(EW_EUNSUPPORTED, "grid too long in y, or z x vectors too many (at most 65535)");
+    return EW_OK;
+}
+
 
 template <typename T>
 ew_status launch_apply_L(const GridGeom& g, const T* u, T* Lu, int nvec, double scale,
                          cudaStream_t st) {
     Stencil<T> s = make_stencil<T>(g, scale);
-    dim3 grid(grid_blocks(g.N, 256), nvec);
+    EW_TRY(pt_check(g, nvec));
+    dim3 grid = pt_grid(g, nvec), blk(pt_threads(g.n[0]));
     if (g.dim == 2 && g.order == 2)
-        k_apply_L<T, 2, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, u, Lu, s);
+        k_apply_L<T, 2, 2><<<grid, blk, 0, st>>>(g.n[0], g.n[1], 1, u, Lu, s);
     else if (g.dim == 2)
-        k_apply_L<T, 2, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, u, Lu, s);
+        k_apply_L<T, 2, 4><<<grid, blk, 0, st>>>(g.n[0], g.n[1], 1, u, Lu, s);
     else if (g.order == 2)
-        k_apply_L<T, 3, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], u, Lu, s);
+        k_apply_L<T, 3, 2><<<grid, blk, 0, st>>>(g.n[0], g.n[1], g.n[2], u, Lu, s);
     else
-        k_apply_L<T, 3, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], u, Lu, s);
+        k_apply_L<T, 3, 4><<<grid, blk, 0, st>>>(g.n[0], g.n[1], g.n[2], u, Lu, s);
     EW_CUDA_TRY(cudaGetLastError());
     count_launch();
     return EW_OK;
@@ -302,16 +307,17 @@ template <typename T>
 ew_status first_step(const GridGeom& g, const T* vin, T* D1, T* W1, T* vout,
                             const FilterPlan& plan, int nvec, int64_t fstride, cudaStream_t st) {
     Stencil<T> s = make_stencil<T>(g, 0.5 * plan.dt * plan.dt);
-    dim3 grid(grid_blocks(g.N, 256), nvec);
+    EW_TRY(pt_check(g, nvec));
+    dim3 grid = pt_grid(g, nvec), blk(pt_threads(g.n[0]));
     T c0 = T(plan.cn(0)), c1 = T(plan.cn(1));
     if (g.dim == 2 && g.order == 2)
-        k_first_step<T, 2, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, vin, D1, W1, vout, s, c0, c1, fstride);
+        k_first_step<T, 2, 2><<<grid, blk, 0, st>>>(g.n[0], g.n[1], 1, vin, D1, W1, vout, s, c0, c1, fstride);
     else if (g.dim == 2)
-        k_first_step<T, 2, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, vin, D1, W1, vout, s, c0, c1, fstride);
+        k_first_step<T, 2, 4><<<grid, blk, 0, st>>>(g.n[0], g.n[1], 1, vin, D1, W1, vout, s, c0, c1, fstride);
     else if (g.order == 2)
-        k_first_step<T, 3, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, D1, W1, vout, s, c0, c1, fstride);
+        k_first_step<T, 3, 2><<<grid, blk, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, D1, W1, vout, s, c0, c1, fstride);
     else
-        k_first_step<T, 3, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, D1, W1, vout, s, c0, c1, fstride);
+        k_first_step<T, 3, 4><<<grid, blk, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, D1, W1, vout, s, c0, c1, fstride);
     EW_CUDA_TRY(cudaGetLastError());
     count_launch();
     return EW_OK;
@@ -320,16 +326,17 @@ ew_status first_step(const GridGeom& g, const T* vin, T* D1, T* W1, T* vout,
 template <typename T>
 static ew_status step_simple(const GridGeom& g, const T* W, T* D, T* Wout, T* acc, T c, const Stencil<T>& s,
                              int nvec, int64_t fstride, cudaStream_t st) {
-    dim3 grid(grid_blocks(g.N, 256), nvec);
+    EW_TRY(pt_check(g, nvec));
+    dim3 grid = pt_grid(g, nvec), blk(pt_threads(g.n[0]));
     cudaEvent_t ev = fused_begin(st);
     if (g.dim == 2 && g.order == 2)
-        k_step_simple<T, 2, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, W, D, Wout, acc, s, c, fstride);
+        k_step_simple<T, 2, 2><<<grid, blk, 0, st>>>(g.n[0], g.n[1], 1, W, D, Wout, acc, s, c, fstride);
     else if (g.dim == 2)
-        k_step_simple<T, 2, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], 1, W, D, Wout, acc, s, c, fstride);
+        k_step_simple<T, 2, 4><<<grid, blk, 0, st>>>(g.n[0], g.n[1], 1, W, D, Wout, acc, s, c, fstride);
     else if (g.order == 2)
-        k_step_simple<T, 3, 2><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], W, D, Wout, acc, s, c, fstride);
+        k_step_simple<T, 3, 2><<<grid, blk, 0, st>>>(g.n[0], g.n[1], g.n[2], W, D, Wout, acc, s, c, fstride);
     else
-        k_step_simple<T, 3, 4><<<grid, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], W, D, Wout, acc, s, c, fstride);
+        k_step_simple<T, 3, 4><<<grid, blk, 0, st>>>(g.n[0], g.n[1], g.n[2], W, D, Wout, acc, s, c, fstride);
     EW_CUDA_TRY(cudaGetLastError());
     fused_end(ev, st, g.N * nvec, g.N * nvec);
     return EW_OK;
@@ -381,6 +388,10 @@ ew_status explicit_wave_solve(const GridGeom& g, const FilterPlan& plan, const T
     if (blocked) {
         int prv = 0, cur = 1;
         return tb2d_advance<T>(g, plan, cdev, F, &prv, &cur, 1, vout, nvec, fstride, temporal_block, st);
+    }
+    if (g.dim == 3 && g.order == 2 && temporal_block != 1) {
+        int prv = 0, cur = 1;
+        return tb3d_advance<T>(g, plan, cdev, F, &prv, &cur, 1, vout, nvec, fstride, temporal_block, st);
     }
     Stencil<T> s = make_stencil<T>(g, plan.dt * plan.dt);
     int cur = 1, nxt = 2;

@@ -1,0 +1,225 @@
+// ew_tb3d.cu -- temporally blocked fused leapfrog + filter steps on 3D grids,
+// second-order stencil (eqs. explicitScheme, filterQuadrature), in the summed
+// form of the recurrence (see ew_stencil.cu):
+//
+//   D^{k} = D^{k-1} + dt^2 L_h W^{k-1},  W^{k} = W^{k-1} + D^{k},  acc += c_k W^{k}
+//
+// 2.5D blocking.  A CTA owns a TXo x TYo column of the box and streams it
+// along z.  Its 32 x 32 threads cover the tile plus a rim of H = B points in x
+// and y (one thread per (x, y)); one launch advances b <= B time levels.
+// Level k works one plane behind level k-1: at step z of the march, level 0
+// loads plane z of W^n and D^n, and level k (1..b) computes plane z - k from
+// level k-1's planes z-k-1 .. z-k+1.  Each thread keeps, per level, the
+// z-neighbours of its own column in a three-entry register queue, the D value
+// it hands to the next level, and the filter sums of the last B planes; only
+// the x/y neighbours go through shared memory, one double-buffered plane per
+// level, and one barrier per plane serves all levels.  Level b writes
+// D^{n+b}, W^{n+b} and the finished filter sum of plane z - b for the owned
+// points.  Wrong x/y neighbours at the region's edge spread one point per
+// level and stay inside the rim.
+//
+// Points outside the box (x, y or z) are loaded with the odd extension of the
+// field (0 on the boundary planes, -u(mirror) beyond); the update keeps it
+// exact, as in the 2D kernel, so planes beyond the box are simply computed.
+// Global traffic per point and launch: W^n, D^n, acc in, W^{n+b}, D^{n+b}, acc
+// out (24 B in FP32), i.e. 24/b B per cell-step.
+#include <algorithm>
+
+#include "ew_internal.h"
+
+namespace ew {
+
+constexpr int kT3 = 32;  // compute region edge (threads per axis)
+
+// odd extension of an axis of length n (period 2(n+1)): interior index and
+// sign, or -1 on a boundary line
+__device__ __forceinline__ int odd_ext3(int p, int n, int& sign) {
+    const int P = 2 * (n + 1);
+    int q = (p + 1) % P;
+    if (q < 0) q += P;
+    q -= 1;
+    if (q == -1 || q == n) return -1;
+    if (q < n) {
+        sign = 1;
+        return q;
+    }
+    sign = -1;
+    return 2 * n - q;
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(kT3* kT3, 1)
+    k_step_tb3d(int nx, int ny, int nz, const T* __restrict__ Din, const T* __restrict__ Win, T* __restrict__ Dout,
+                T* __restrict__ Wout, T* __restrict__ acc, const T* __restrict__ cw, int b, Stencil<T> st,
+                int64_t fstride) {
+    constexpr int H = B, TO = kT3 - 2 * H;  // rim, owned tile edge
+    extern __shared__ __align__(16) unsigned char smem_tb3d[];
+    // sP[k][buf]: level k's output plane (k = 0: the loaded W^n), double-buffered
+    T(*sP)[2][kT3 * kT3] = reinterpret_cast<T(*)[2][kT3 * kT3]>(smem_tb3d);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int gx = blockIdx.x * TO - H + tx, gy = blockIdx.y * TO - H + ty;
+    const int64_t v = blockIdx.z;
+    const int64_t N = (int64_t)nx * ny * nz, plane = (int64_t)nx * ny;
+    Din += v * fstride;
+    Win += v * fstride;
+    Dout += v * fstride;
+    Wout += v * fstride;
+    acc += v * N;
+    // x/y odd extension of this column: source column and sign (0: boundary line)
+    int sx = 1, sy = 1;
+    const int ix = odd_ext3(gx, nx, sx), iy = odd_ext3(gy, ny, sy);
+    const int sxy = (ix < 0 || iy < 0) ? 0 : sx * sy;
+    const int64_t col = sxy ? (int64_t)iy * nx + ix : 0;
+    const bool own = tx >= H && tx < H + TO && ty >= H && ty < H + TO && gx < nx && gy < ny;
+    const int64_t ocol = (int64_t)gy * nx + gx;
+    // neighbours inside the region (clamped at its edge: those values are wrong but stay in the rim)
+    const int ixm = max(tx - 1, 0), ixp = min(tx + 1, kT3 - 1), iym = max(ty - 1, 0), iyp = min(ty + 1, kT3 - 1);
+    const int me = ty * kT3 + tx;
+    const int nxm = ty * kT3 + ixm, nxp = ty * kT3 + ixp, nym = iym * kT3 + tx, nyp = iyp * kT3 + tx;
+
+    auto ld = [&](const T* __restrict__ f, int z) -> T {
+        if (!sxy) return T(0);
+        int szz = 1, iz = z;
+        if (z < 0 || z >= nz) iz = odd_ext3(z, nz, szz);
+        if (iz < 0) return T(0);
+        const T x = f[(int64_t)iz * plane + col];
+        return (sxy * szz < 0) ? -x : x;
+    };
+    // plane z's inputs are loaded kPF steps ahead (register queue), so the
+    // loads of later planes are in flight while earlier planes are computed
+    constexpr int kPF = 4;
+    T pw[kPF], pd[kPF], pa[kPF];
+    auto issue = [&](int z, int slot) {
+        const bool live = z < nz + B;
+        pw[slot] = live ? ld(Win, z) : T(0);
+        pd[slot] = live ? ld(Din, z) : T(0);
+        pa[slot] = (own && z >= 0 && z < nz) ? acc[(int64_t)z * plane + ocol] : T(0);
+    };
+#pragma unroll
+    for (int q = 0; q < kPF; ++q) issue(-B + q, q);
+
+    T Wq[B + 1][3];  // Wq[k]: W of level k-1 at planes p_k - 1, p_k, p_k + 1 (k = 1..B)
+    T Dq[B + 1];     // Dq[k]: D of level k-1 at plane p_k
+    T accq[B];       // accq[j]: filter sum of plane z - 1 - j
+#pragma unroll
+    for (int k = 0; k <= B; ++k) {
+        Wq[k][0] = Wq[k][1] = Wq[k][2] = T(0);
+        Dq[k] = T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < B; ++j) accq[j] = T(0);
+    const T c0 = st.c0, c1x = st.c1[0], c1y = st.c1[1], c1z = st.c1[2];
+
+    for (int z = -B; z < nz + B; ++z) {
+        const int buf = z & 1, obuf = buf ^ 1;
+        // ---- level 0: plane z of W^n, D^n and its filter sum (loaded kPF steps ago) -----
+        const T w0 = pw[0], d0 = pd[0], a0 = pa[0];
+#pragma unroll
+        for (int q = 0; q + 1 < kPF; ++q) {
+            pw[q] = pw[q + 1];
+            pd[q] = pd[q + 1];
+            pa[q] = pa[q + 1];
+        }
+        issue(z + kPF, kPF - 1);
+        sP[0][buf][me] = w0;
+        T dnext = d0;   // D handed from level k-1 to level k (this iteration's plane p_{k-1})
+        T wnext = w0;   // W of level k-1 at plane p_{k-1} = p_k + 1
+        // ---- levels 1..b ---------------------------------------------------------------
+#pragma unroll
+        for (int k = 1; k <= B; ++k) {
+            if (k > b) break;
+            // z-queue of level k-1 around plane p_k = z - k
+            Wq[k][0] = Wq[k][1];
+            Wq[k][1] = Wq[k][2];
+            Wq[k][2] = wnext;
+            const T* sq = sP[k - 1][obuf];  // level k-1's plane p_k, written one step ago
+            const T u = Wq[k][1];
+            T lap = c0 * u;
+            lap += c1x * (sq[nxm] + sq[nxp]);
+            lap += c1y * (sq[nym] + sq[nyp]);
+            lap += c1z * (Wq[k][0] + Wq[k][2]);
+            const T d = Dq[k] + lap;
+            const T wn = u + d;
+            Dq[k] = dnext;  // level k-1's D of plane p_k + 1, used by level k next step
+            accq[k - 1] += cw[k - 1] * wn;
+            if (k < b) {
+                sP[k][buf][me] = wn;
+                dnext = d;
+                wnext = wn;
+            } else {
+                const int p = z - k;
+                if (own && p >= 0 && p < nz) {
+                    const int64_t gi = (int64_t)p * plane + ocol;
+                    Wout[gi] = wn;
+                    Dout[gi] = d;
+                }
+            }
+        }
+        // ---- plane z - b is complete: store its filter sum, shift the queue -----------
+        {
+            const int p = z - b;
+            if (own && p >= 0 && p < nz) acc[(int64_t)p * plane + ocol] = accq[b - 1];
+#pragma unroll
+            for (int j = B - 1; j > 0; --j) accq[j] = accq[j - 1];
+            accq[0] = a0;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int B>
+static ew_status launch_tb3d(const GridGeom& g, const T* Din, const T* Win, T* Dout, T* Wout, T* acc, const T* cw,
+                             int b, const Stencil<T>& s, int nvec, int64_t fstride, cudaStream_t st) {
+    constexpr int TO = kT3 - 2 * B;
+    constexpr size_t smem = sizeof(T) * (size_t)B * 2 * kT3 * kT3;
+    static bool attr = false;  // per instantiation (same value on every device)
+    if (!attr) {
+        EW_CUDA_TRY(cudaFuncSetAttribute(k_step_tb3d<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    dim3 grid((unsigned)((g.n[0] + TO - 1) / TO), (unsigned)((g.n[1] + TO - 1) / TO), (unsigned)nvec);
+    cudaEvent_t ev = fused_begin(st);
+    k_step_tb3d<T, B><<<grid, dim3(kT3, kT3), smem, st>>>((int)g.n[0], (int)g.n[1], (int)g.n[2], Din, Win, Dout, Wout,
+                                                        acc, cw, b, s, fstride);
+    EW_CUDA_TRY(cudaGetLastError());
+    fused_end(ev, st, g.N * nvec, g.N * nvec * b);
+    return EW_OK;
+}
+
+// Advance from level L (W = F[cur], D = F[prv]) to level Nt in launches of up
+// to B levels (B = 4, or `tb` when 1 < tb < 4).  Second-order 3D grids only.
+template <typename T>
+ew_status tb3d_advance(const GridGeom& g, const FilterPlan& plan, const T* cdev, T* const* F, int* prv, int* cur,
+                       int64_t L, T* acc, int nvec, int64_t fstride, int tb, cudaStream_t st) {
+    if (g.dim != 3 || g.order != 2) return set_error(EW_EUNSUPPORTED, "3D temporal blocking is second order only");
+    if (nvec > 65535) return set_error(EW_EUNSUPPORTED, "too many vectors in one call");
+    Stencil<T> s = make_stencil<T>(g, plan.dt * plan.dt);
+    const int B = (tb > 1 && tb < 4) ? tb : 4;
+    int p = *prv, c = *cur, a = -1, d = -1;
+    for (int q = 0; q < 4; ++q)
+        if (q != p && q != c) (a < 0 ? a : d) = q;
+    while (L < plan.Nt) {
+        const int b = (int)std::min<int64_t>(B, plan.Nt - L);
+        const T* cw = cdev + L + 1;
+        ew_status s2;
+        if (B == 4)
+            s2 = launch_tb3d<T, 4>(g, F[p], F[c], F[a], F[d], acc, cw, b, s, nvec, fstride, st);
+        else if (B == 3)
+            s2 = launch_tb3d<T, 3>(g, F[p], F[c], F[a], F[d], acc, cw, b, s, nvec, fstride, st);
+        else
+            s2 = launch_tb3d<T, 2>(g, F[p], F[c], F[a], F[d], acc, cw, b, s, nvec, fstride, st);
+        EW_TRY(s2);
+        L += b;
+        std::swap(p, a);
+        std::swap(c, d);
+    }
+    *prv = p;
+    *cur = c;
+    return EW_OK;
+}
+template ew_status tb3d_advance<float>(const GridGeom&, const FilterPlan&, const float*, float* const*, int*, int*,
+                                       int64_t, float*, int, int64_t, int, cudaStream_t);
+template ew_status tb3d_advance<double>(const GridGeom&, const FilterPlan&, const double*, double* const*, int*, int*,
+                                        int64_t, double*, int, int64_t, int, cudaStream_t);
+
+}  // namespace ew

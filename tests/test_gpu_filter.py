@@ -122,6 +122,19 @@ def test_fp64_blocked_equals_simple(ew):
     assert np.max(np.abs(a - b)) < 1e-13 * np.max(np.abs(b))
 
 
+@pytest.mark.parametrize("tb", [0, 2, 3])
+def test_fp64_3d_blocked_equals_simple(ew, tb):
+    """3D second-order temporal blocking (2.5D, levels pipelined along z)
+    changes only rounding order: depths 4 (default), 2 and 3 against one step
+    per launch, two vectors, ragged tiles in x and y, N_t not a multiple of
+    the depth."""
+    n, L = (61, 50, 23), (1.0, 0.8, 0.4)
+    v, a, info = _run(ew, n, L, 2, "fp64", 30.0, Np=2, tb=tb, nvec=2)
+    _, b, _ = _run(ew, n, L, 2, "fp64", 30.0, Np=2, tb=1, nvec=2)
+    assert info["Nt"] % 4 != 0 or info["Nt"] % 3 != 0
+    assert np.max(np.abs(a - b)) < 1e-13 * np.max(np.abs(b))
+
+
 def test_multi_vector_block(ew):
     """nvec vectors in one call equal separate calls, bit for bit."""
     n, L = (150, 40), (1.0, 0.3)
