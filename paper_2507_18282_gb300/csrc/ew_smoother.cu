@@ -196,28 +196,33 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
 
 // ---------------------------------------------------------------------------
 // Tensor-core forward (FP32 fields): both layers on BF16 mma.sync.m16n8k16
-// with FP32 accumulation.
+// with FP32 accumulation, streamed along z.
 //
 //   layer 1  H[q][c]  = sum_k A[q][k] B1[k][c]   A = im2col of r (k = tap,
-//            27 padded to 32), B1[k][c] = W1[c][k]; 16 hidden points per MMA row
-//            block, N = 8 channels
+//            27 padded to 32), B1[k][c] = W1[c][k]; 16 hidden points of one
+//            plane per MMA row block, N = 8 channels
 //   layer 2  Z[q][o]  = sum_c H[q][c] B2[c][o]  B2[c][o] = W2[c][o] (K = 8
 //            channels padded to 16, N = 27 taps padded to 32): the accumulator
 //            fragment of layer 1, rounded to BF16, is exactly the A fragment of
 //            layer 2 (row q, k = c), so H never leaves registers
-//   output   N(r)(x) = sum_o Z[x + o][o]   (27-term gather from shared memory)
+//   output   N(r)(x) = sum_o Z[x + o][o]
 //
-// Hidden points outside the box are zero (the second convolution's zero
-// padding).  Tile: 8 x 8 x 4 outputs, 10 x 10 x 6 hidden points, 12 x 12 x 8
-// residual points, 8 warps.
+// A CTA owns a 16 x 16 column of outputs and kZC planes of it.  Step s
+// computes hidden plane hz = z0 - 1 + s (18 x 18 points) from a three-plane
+// ring of residual planes, stores its Z (27 taps) in shared memory, and each
+// thread adds the taps of that plane to the three output planes it touches
+// (hz + 1, hz, hz - 1 for dz = -1, 0, +1), kept in registers; output plane
+// hz - 1 is then complete.  Hidden points outside the box are zero (the
+// second convolution's zero padding).
 // ---------------------------------------------------------------------------
-constexpr int kTX = 8, kTY = 8, kTZ = 4;                    // output tile
-constexpr int kHX = kTX + 2, kHY = kTY + 2, kHZ = kTZ + 2;  // hidden region
-constexpr int kRX = kTX + 4, kRY = kTY + 4, kRZ = kTZ + 4;  // staged residual
-constexpr int kHN = kHX * kHY * kHZ;                        // 600 hidden points
-constexpr int kHG = (kHN + 15) / 16;                        // 38 row blocks of 16
-constexpr int kZS = kHG * 16 + 4;                           // Z row stride (612: conflict-free stores)
-constexpr int kTcThreads = 256;
+constexpr int kOX = 16, kOY = 16, kZC = 32;          // output column and planes per CTA
+constexpr int kHX = kOX + 2, kHY = kOY + 2;          // hidden plane (halo 1)
+constexpr int kRX = kOX + 4, kRY = kOY + 4;          // residual plane (halo 2)
+constexpr int kHP = kHX * kHY;                       // 324 hidden points per plane
+constexpr int kHG = (kHP + 15) / 16;                 // 21 row blocks of 16
+constexpr int kZS = kHG * 16 + 4;                    // Z row stride (340: conflict-free stores)
+constexpr int kRP = kRX * kRY;                       // 400 residual points per plane
+constexpr int kTcThreads = kOX * kOY;                // 256: one output column each
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -236,16 +241,26 @@ __global__ void __launch_bounds__(kTcThreads)
     k_smoother_fwd_tc(int nx, int ny, int nz, const float* __restrict__ w, const float* __restrict__ r,
                       float* __restrict__ out) {
     extern __shared__ __align__(16) float smem_tc[];
-    float* sR = smem_tc;                   // kRX * kRY * kRZ
-    float* sZ = smem_tc + kRX * kRY * kRZ;  // 27 * kZS
+    float* sR = smem_tc;               // [3][kRP]: residual planes, ring indexed by plane mod 3
+    float* sZ = smem_tc + 3 * kRP;     // [27][kZS]: Z of the current hidden plane
+    int* sHB = reinterpret_cast<int*>(sZ + 27 * kZS);  // [kHG * 16]: residual offset of each hidden point, -1 outside
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, tig = lane & 3;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z * kTZ;
-    // staged residual (BF16-rounded, zero outside the box), origin (x0-2, y0-2, z0-2)
-    for (int q = tid; q < kRX * kRY * kRZ; q += kTcThreads) {
-        int lx = q % kRX, t = q / kRX, ly = t % kRY, lz = t / kRY;
-        sR[q] = ld_r(r, x0 - 2 + lx, y0 - 2 + ly, z0 - 2 + lz, nx, ny, nz);
+    const int x0 = blockIdx.x * kOX, y0 = blockIdx.y * kOY, z0 = blockIdx.z * kZC;
+    const int z1 = min(nz, z0 + kZC);
+    // hidden points of a plane: offset of tap (-1,-1) in a residual plane, -1 if outside the box in x/y
+    for (int q = tid; q < kHG * 16; q += kTcThreads) {
+        const int hx = q % kHX, hy = q / kHX;
+        const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+        sHB[q] = (q < kHP && gx >= 0 && gy >= 0 && gx < nx && gy < ny) ? hy * kRX + hx : -1;
     }
+    auto load_plane = [&](int zr) {  // residual plane zr (BF16-rounded, zero outside) into its ring slot
+        float* dst = sR + ((zr + 3) % 3) * kRP;
+        for (int q = tid; q < kRP; q += kTcThreads) {
+            const int lx = q % kRX, ly = q / kRX;
+            dst[q] = ld_r(r, x0 - 2 + lx, y0 - 2 + ly, zr, nx, ny, nz);
+        }
+    };
     // B fragments (fixed per thread).  Layer 1, k-step s: b0 = B1[16s + 2tig (+1)][g],
     // b1 = B1[16s + 2tig + 8 (+1)][g] with B1[k][c] = W1[c][k] (0 for k >= 27).
     auto w1 = [&](int k, int c) { return k < 27 ? w[c * 27 + k] : 0.f; };
@@ -262,94 +277,110 @@ __global__ void __launch_bounds__(kTcThreads)
         const int o = 8 * j + g;
         b2f[j] = o < 27 ? pack_bf16(w[kW + (2 * tig) * 27 + o], w[kW + (2 * tig + 1) * 27 + o]) : 0u;
     }
-    // this thread's im2col taps: k-step s holds taps 16s + {2tig, 2tig+1, 2tig+8, 2tig+9}
-    int toff[8];
+    // this thread's im2col taps: k-step s holds taps 16s + {2tig, 2tig+1, 2tig+8, 2tig+9};
+    // tap k = (dz+1) 9 + (dy+1) 3 + (dx+1): residual plane dz (relative), offset dy * kRX + dx
+    int tdz[8], toff[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const int k = 16 * (e >> 2) + 2 * tig + (e & 1) + ((e >> 1) & 1) * 8;
-        const int kk = k < 27 ? k : 0;  // padded taps read a valid point, times a zero weight
-        toff[e] = ((kk / 9) * kRY + (kk / 3) % 3) * kRX + kk % 3;
+        const int kk = k < 27 ? k : 13;  // padded taps read a valid point, times a zero weight
+        tdz[e] = kk / 9;
+        toff[e] = ((kk / 3) % 3) * kRX + kk % 3;
     }
-    __syncthreads();
-    for (int G = warp; G < kHG; G += kTcThreads / 32) {
-        // rows g and g + 8 of the block: hidden points q0, q1
-        const int q0 = 16 * G + g, q1 = q0 + 8;
-        auto hpos = [&](int q, int& base, bool& in) {
-            const int hx = q % kHX, t = q / kHX, hy = t % kHY, hz = t / kHY;
-            base = (hz * kRY + hy) * kRX + hx;  // residual index of tap (0,0,0) = offset (-1,-1,-1)
-            const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
-            in = q < kHN && gx >= 0 && gy >= 0 && gz >= 0 && gx < nx && gy < ny && gz < nz;
-            if (q >= kHN) base = 0;
-        };
-        int bq0, bq1;
-        bool in0, in1;
-        hpos(q0, bq0, in0);
-        hpos(q1, bq1, in1);
-        float h[4] = {0.f, 0.f, 0.f, 0.f};
+    load_plane(z0 - 2);
+    load_plane(z0 - 1);
+    const int ox = tid % kOX, oy = tid / kOX;  // this thread's output column
+    const int gx = x0 + ox, gy = y0 + oy;
+    const bool own = gx < nx && gy < ny;
+    float oa = 0.f, ob = 0.f, oc = 0.f;        // output planes hz - 1, hz, hz + 1
+    for (int hz = z0 - 1; hz <= z1; ++hz) {
+        load_plane(hz + 1);
+        __syncthreads();  // residual planes hz-1..hz+1 in place; the previous Z has been read
+        const bool zin = hz >= 0 && hz < nz;
+        if (zin) {
+            // ring slots of residual planes hz - 1, hz, hz + 1 -> each tap's offset in sR
+            const int s0 = ((hz + 2) % 3) * kRP, s1 = ((hz + 3) % 3) * kRP, s2 = ((hz + 4) % 3) * kRP;
+            int tap[8];
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            uint32_t a[4];
-            a[0] = pack_bf16(sR[bq0 + toff[4 * s + 0]], sR[bq0 + toff[4 * s + 1]]);
-            a[1] = pack_bf16(sR[bq1 + toff[4 * s + 0]], sR[bq1 + toff[4 * s + 1]]);
-            a[2] = pack_bf16(sR[bq0 + toff[4 * s + 2]], sR[bq0 + toff[4 * s + 3]]);
-            a[3] = pack_bf16(sR[bq1 + toff[4 * s + 2]], sR[bq1 + toff[4 * s + 3]]);
-            mma_bf16(h, a, b1f[s][0], b1f[s][1]);
-        }
-        // h: (row g, channels 2tig, 2tig+1) and (row g+8, same): zero outside the box,
-        // round to BF16 -> the A fragment of layer 2 (k = channel; k >= 8 zero)
-        uint32_t a2[4];
-        a2[0] = in0 ? pack_bf16(h[0], h[1]) : 0u;
-        a2[1] = in1 ? pack_bf16(h[2], h[3]) : 0u;
-        a2[2] = 0u;
-        a2[3] = 0u;
+            for (int e = 0; e < 8; ++e) tap[e] = (tdz[e] == 0 ? s0 : tdz[e] == 1 ? s1 : s2) + toff[e];
+            for (int G = warp; G < kHG; G += kTcThreads / 32) {
+                const int q0 = 16 * G + g, q1 = q0 + 8;
+                const int hb0 = sHB[q0], hb1 = sHB[q1];
+                const int bb0 = hb0 < 0 ? 0 : hb0, bb1 = hb1 < 0 ? 0 : hb1;
+                float h[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float z[4] = {0.f, 0.f, 0.f, 0.f};
-            mma_bf16(z, a2, b2f[j], 0u);
-            const int o = 8 * j + 2 * tig;
-            if (o < 27) {
-                sZ[o * kZS + q0] = z[0];
-                sZ[o * kZS + q1] = z[2];
-            }
-            if (o + 1 < 27) {
-                sZ[(o + 1) * kZS + q0] = z[1];
-                sZ[(o + 1) * kZS + q1] = z[3];
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    uint32_t a[4];
+                    const int e = 4 * s2;
+                    a[0] = pack_bf16(sR[bb0 + tap[e]], sR[bb0 + tap[e + 1]]);
+                    a[1] = pack_bf16(sR[bb1 + tap[e]], sR[bb1 + tap[e + 1]]);
+                    a[2] = pack_bf16(sR[bb0 + tap[e + 2]], sR[bb0 + tap[e + 3]]);
+                    a[3] = pack_bf16(sR[bb1 + tap[e + 2]], sR[bb1 + tap[e + 3]]);
+                    mma_bf16(h, a, b1f[s2][0], b1f[s2][1]);
+                }
+                // h: (row g, channels 2tig, 2tig+1), (row g+8, same): zero outside the box,
+                // round to BF16 -> the A fragment of layer 2 (k = channel; k >= 8 zero)
+                uint32_t a2[4];
+                a2[0] = hb0 >= 0 ? pack_bf16(h[0], h[1]) : 0u;
+                a2[1] = hb1 >= 0 ? pack_bf16(h[2], h[3]) : 0u;
+                a2[2] = 0u;
+                a2[3] = 0u;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float zf[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma_bf16(zf, a2, b2f[j], 0u);
+                    const int o = 8 * j + 2 * tig;
+                    if (o < 27) {
+                        sZ[o * kZS + q0] = zf[0];
+                        sZ[o * kZS + q1] = zf[2];
+                    }
+                    if (o + 1 < 27) {
+                        sZ[(o + 1) * kZS + q0] = zf[1];
+                        sZ[(o + 1) * kZS + q1] = zf[3];
+                    }
+                }
             }
         }
-    }
-    __syncthreads();
-    // output x = (lx, ly, lz): sum over taps o of Z[x + o][o]
-    {
-        const int lx = tid % kTX, t = tid / kTX, ly = t % kTY, lz = t / kTY;
-        const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-        if (gx < nx && gy < ny && gz < nz) {
-            float sacc = 0.f;
-            int o = 0;
+        __syncthreads();  // Z of plane hz complete
+        if (zin) {
+            // taps of plane hz: dz = +1 feeds output plane hz - 1, dz = 0 plane hz, dz = -1 plane hz + 1
+            float t[3] = {0.f, 0.f, 0.f};
 #pragma unroll
             for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
                 for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-                    for (int dx = 0; dx < 3; ++dx, ++o)
-                        sacc += sZ[o * kZS + ((lz + dz) * kHY + (ly + dy)) * kHX + (lx + dx)];
-            const int64_t gi = ((int64_t)gz * ny + gy) * nx + gx;
-            if (ADD)
-                out[gi] += sacc;
-            else
-                out[gi] = sacc;
+                    for (int dx = 0; dx < 3; ++dx)
+                        t[dz] += sZ[(dz * 9 + dy * 3 + dx) * kZS + (oy + dy) * kHX + (ox + dx)];
+            oa += t[2];
+            ob += t[1];
+            oc += t[0];
         }
+        // output plane hz - 1 is complete
+        const int zo = hz - 1;
+        if (own && zo >= z0 && zo < z1) {
+            const int64_t gi = ((int64_t)zo * ny + gy) * nx + gx;
+            if (ADD)
+                out[gi] += oa;
+            else
+                out[gi] = oa;
+        }
+        oa = ob;
+        ob = oc;
+        oc = 0.f;
     }
 }
 
-constexpr size_t kTcSmem = sizeof(float) * ((size_t)kRX * kRY * kRZ + 27 * (size_t)kZS);
+static dim3 tc_tiles(const GridGeom& g) {
+    return dim3((unsigned)((g.n[0] + kOX - 1) / kOX), (unsigned)((g.n[1] + kOY - 1) / kOY),
+                (unsigned)((g.n[2] + kZC - 1) / kZC));
+}
+
+constexpr size_t kTcSmem = sizeof(float) * (3 * (size_t)kRP + 27 * (size_t)kZS) + sizeof(int) * kHG * 16;
 
 template <bool ADD>
 static ew_status launch_fwd_tc(const GridGeom& g, const float* w, const float* r, float* out, cudaStream_t st);
 
-static dim3 tc_tiles(const GridGeom& g) {
-    return dim3((unsigned)((g.n[0] + kTX - 1) / kTX), (unsigned)((g.n[1] + kTY - 1) / kTY),
-                (unsigned)((g.n[2] + kTZ - 1) / kTZ));
-}
 
 template <bool ADD>
 static ew_status launch_fwd_tc(const GridGeom& g, const float* w, const float* r, float* out, cudaStream_t st) {

@@ -47,7 +47,8 @@ __device__ __forceinline__ int odd_ext3(int p, int n, int& sign) {
     return 2 * n - q;
 }
 
-template <typename T, int B>
+// FULL: b == B (every launch but the last of a wave-solve)
+template <typename T, int B, bool FULL>
 __global__ void __launch_bounds__(kT3* kT3, 1)
     k_step_tb3d(int nx, int ny, int nz, const T* __restrict__ Din, const T* __restrict__ Win, T* __restrict__ Dout,
                 T* __restrict__ Wout, T* __restrict__ acc, const T* __restrict__ cw, int b, Stencil<T> st,
@@ -85,85 +86,90 @@ __global__ void __launch_bounds__(kT3* kT3, 1)
         const T x = f[(int64_t)iz * plane + col];
         return (sxy * szz < 0) ? -x : x;
     };
-    // plane z's inputs are loaded kPF steps ahead (register queue), so the
-    // loads of later planes are in flight while earlier planes are computed
+    // plane z's inputs are loaded kPF steps ahead into slot z mod kPF; the march
+    // is unrolled by kPF so every slot is a fixed register (a register queue
+    // that shifted would consume each load one step after issuing it)
     constexpr int kPF = 4;
     T pw[kPF], pd[kPF], pa[kPF];
-    auto issue = [&](int z, int slot) {
+    auto issue = [&](int z, T& w, T& d, T& a) {
         const bool live = z < nz + B;
-        pw[slot] = live ? ld(Win, z) : T(0);
-        pd[slot] = live ? ld(Din, z) : T(0);
-        pa[slot] = (own && z >= 0 && z < nz) ? acc[(int64_t)z * plane + ocol] : T(0);
+        w = live ? ld(Win, z) : T(0);
+        d = live ? ld(Din, z) : T(0);
+        a = (own && z >= 0 && z < nz) ? acc[(int64_t)z * plane + ocol] : T(0);
     };
 #pragma unroll
-    for (int q = 0; q < kPF; ++q) issue(-B + q, q);
+    for (int q = 0; q < kPF; ++q) issue(-B + q, pw[q], pd[q], pa[q]);
 
     T Wq[B + 1][3];  // Wq[k]: W of level k-1 at planes p_k - 1, p_k, p_k + 1 (k = 1..B)
     T Dq[B + 1];     // Dq[k]: D of level k-1 at plane p_k
     T accq[B];       // accq[j]: filter sum of plane z - 1 - j
+    T cwr[B];        // filter weights of the b levels
 #pragma unroll
     for (int k = 0; k <= B; ++k) {
         Wq[k][0] = Wq[k][1] = Wq[k][2] = T(0);
         Dq[k] = T(0);
     }
 #pragma unroll
-    for (int j = 0; j < B; ++j) accq[j] = T(0);
+    for (int j = 0; j < B; ++j) {
+        accq[j] = T(0);
+        cwr[j] = (FULL || j < b) ? cw[j] : T(0);
+    }
     const T c0 = st.c0, c1x = st.c1[0], c1y = st.c1[1], c1z = st.c1[2];
+    const int nb = FULL ? B : b;
 
-    for (int z = -B; z < nz + B; ++z) {
-        const int buf = z & 1, obuf = buf ^ 1;
-        // ---- level 0: plane z of W^n, D^n and its filter sum (loaded kPF steps ago) -----
-        const T w0 = pw[0], d0 = pd[0], a0 = pa[0];
+    for (int zb = -B; zb < nz + B; zb += kPF) {
 #pragma unroll
-        for (int q = 0; q + 1 < kPF; ++q) {
-            pw[q] = pw[q + 1];
-            pd[q] = pd[q + 1];
-            pa[q] = pa[q + 1];
-        }
-        issue(z + kPF, kPF - 1);
-        sP[0][buf][me] = w0;
-        T dnext = d0;   // D handed from level k-1 to level k (this iteration's plane p_{k-1})
-        T wnext = w0;   // W of level k-1 at plane p_{k-1} = p_k + 1
-        // ---- levels 1..b ---------------------------------------------------------------
+        for (int j = 0; j < kPF; ++j) {
+            const int z = zb + j;
+            if (z >= nz + B) break;
+            const int buf = z & 1, obuf = buf ^ 1;
+            // ---- level 0: plane z of W^n, D^n and its filter sum (loaded kPF steps ago) -
+            const T w0 = pw[j], d0 = pd[j], a0 = pa[j];
+            issue(z + kPF, pw[j], pd[j], pa[j]);
+            sP[0][buf][me] = w0;
+            T dnext = d0;  // D handed from level k-1 to level k (this step's plane p_{k-1})
+            T wnext = w0;  // W of level k-1 at plane p_{k-1} = p_k + 1
+            // ---- levels 1..b -----------------------------------------------------------
 #pragma unroll
-        for (int k = 1; k <= B; ++k) {
-            if (k > b) break;
-            // z-queue of level k-1 around plane p_k = z - k
-            Wq[k][0] = Wq[k][1];
-            Wq[k][1] = Wq[k][2];
-            Wq[k][2] = wnext;
-            const T* sq = sP[k - 1][obuf];  // level k-1's plane p_k, written one step ago
-            const T u = Wq[k][1];
-            T lap = c0 * u;
-            lap += c1x * (sq[nxm] + sq[nxp]);
-            lap += c1y * (sq[nym] + sq[nyp]);
-            lap += c1z * (Wq[k][0] + Wq[k][2]);
-            const T d = Dq[k] + lap;
-            const T wn = u + d;
-            Dq[k] = dnext;  // level k-1's D of plane p_k + 1, used by level k next step
-            accq[k - 1] += cw[k - 1] * wn;
-            if (k < b) {
-                sP[k][buf][me] = wn;
-                dnext = d;
-                wnext = wn;
-            } else {
-                const int p = z - k;
-                if (own && p >= 0 && p < nz) {
-                    const int64_t gi = (int64_t)p * plane + ocol;
-                    Wout[gi] = wn;
-                    Dout[gi] = d;
+            for (int k = 1; k <= B; ++k) {
+                if (!FULL && k > nb) break;
+                // z-queue of level k-1 around plane p_k = z - k
+                Wq[k][0] = Wq[k][1];
+                Wq[k][1] = Wq[k][2];
+                Wq[k][2] = wnext;
+                const T* sq = sP[k - 1][obuf];  // level k-1's plane p_k, written one step ago
+                const T u = Wq[k][1];
+                T lap = c0 * u;
+                lap += c1x * (sq[nxm] + sq[nxp]);
+                lap += c1y * (sq[nym] + sq[nyp]);
+                lap += c1z * (Wq[k][0] + Wq[k][2]);
+                const T d = Dq[k] + lap;
+                const T wn = u + d;
+                Dq[k] = dnext;  // level k-1's D of plane p_k + 1, used by level k next step
+                accq[k - 1] += cwr[k - 1] * wn;
+                if (k < nb) {
+                    sP[k][buf][me] = wn;
+                    dnext = d;
+                    wnext = wn;
+                } else {
+                    const int p = z - k;
+                    if (own && p >= 0 && p < nz) {
+                        const int64_t gi = (int64_t)p * plane + ocol;
+                        Wout[gi] = wn;
+                        Dout[gi] = d;
+                    }
                 }
             }
-        }
-        // ---- plane z - b is complete: store its filter sum, shift the queue -----------
-        {
-            const int p = z - b;
-            if (own && p >= 0 && p < nz) acc[(int64_t)p * plane + ocol] = accq[b - 1];
+            // ---- plane z - b is complete: store its filter sum, shift the queue ---------
+            {
+                const int p = z - nb;
+                if (own && p >= 0 && p < nz) acc[(int64_t)p * plane + ocol] = accq[nb - 1];
 #pragma unroll
-            for (int j = B - 1; j > 0; --j) accq[j] = accq[j - 1];
-            accq[0] = a0;
+                for (int q = B - 1; q > 0; --q) accq[q] = accq[q - 1];
+                accq[0] = a0;
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -174,12 +180,16 @@ static ew_status launch_tb3d(const GridGeom& g, const T* Din, const T* Win, T* D
     constexpr size_t smem = sizeof(T) * (size_t)B * 2 * kT3 * kT3;
     static bool attr = false;  // per instantiation (same value on every device)
     if (!attr) {
-        EW_CUDA_TRY(cudaFuncSetAttribute(k_step_tb3d<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        EW_CUDA_TRY(cudaFuncSetAttribute(k_step_tb3d<T, B, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        EW_CUDA_TRY(cudaFuncSetAttribute(k_step_tb3d<T, B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
         attr = true;
     }
     dim3 grid((unsigned)((g.n[0] + TO - 1) / TO), (unsigned)((g.n[1] + TO - 1) / TO), (unsigned)nvec);
     cudaEvent_t ev = fused_begin(st);
-    k_step_tb3d<T, B><<<grid, dim3(kT3, kT3), smem, st>>>((int)g.n[0], (int)g.n[1], (int)g.n[2], Din, Win, Dout, Wout,
+    auto kern = b == B ? k_step_tb3d<T, B, true> : k_step_tb3d<T, B, false>;
+    kern<<<grid, dim3(kT3, kT3), smem, st>>>((int)g.n[0], (int)g.n[1], (int)g.n[2], Din, Win, Dout, Wout,
                                                         acc, cw, b, s, fstride);
     EW_CUDA_TRY(cudaGetLastError());
     fused_end(ev, st, g.N * nvec, g.N * nvec * b);
