@@ -289,12 +289,36 @@ __global__ void __launch_bounds__(kTcThreads)
     }
     load_plane(z0 - 2);
     load_plane(z0 - 1);
+    // the next residual plane is loaded into registers one step ahead (raw; the
+    // BF16 rounding is applied when it is stored, a step later)
+    float pr[2];
+    auto prefetch = [&](int zr) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int q = tid + u * kTcThreads;
+            const int lx = q % kRX, ly = q / kRX;
+            const int xx = x0 - 2 + lx, yy = y0 - 2 + ly;
+            pr[u] = 0.f;
+            if (q < kRP && xx >= 0 && yy >= 0 && zr >= 0 && xx < nx && yy < ny && zr < nz)
+                pr[u] = r[((int64_t)zr * ny + yy) * nx + xx];
+        }
+    };
+    auto commit = [&](int zr) {
+        float* dst = sR + ((zr + 3) % 3) * kRP;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int q = tid + u * kTcThreads;
+            if (q < kRP) dst[q] = bf16r(pr[u]);
+        }
+    };
+    prefetch(z0);
     const int ox = tid % kOX, oy = tid / kOX;  // this thread's output column
     const int gx = x0 + ox, gy = y0 + oy;
     const bool own = gx < nx && gy < ny;
     float oa = 0.f, ob = 0.f, oc = 0.f;        // output planes hz - 1, hz, hz + 1
     for (int hz = z0 - 1; hz <= z1; ++hz) {
-        load_plane(hz + 1);
+        commit(hz + 1);
+        prefetch(hz + 2);
         __syncthreads();  // residual planes hz-1..hz+1 in place; the previous Z has been read
         const bool zin = hz >= 0 && hz < nz;
         if (zin) {

@@ -78,27 +78,29 @@ __global__ void __launch_bounds__(kT3* kT3, 1)
     const int me = ty * kT3 + tx;
     const int nxm = ty * kT3 + ixm, nxp = ty * kT3 + ixp, nym = iym * kT3 + tx, nyp = iyp * kT3 + tx;
 
-    auto ld = [&](const T* __restrict__ f, int z) -> T {
-        if (!sxy) return T(0);
+    // plane z's inputs are loaded kPF steps ahead into slot z mod kPF, raw, with
+    // the odd-extension sign kept beside them (applying it at load time would
+    // make the warp wait for the load right away); the march is unrolled by kPF
+    // so every slot is a fixed register
+    constexpr int kPF = 4;
+    T pw[kPF], pd[kPF], pa[kPF], sg[kPF];
+    auto issue = [&](int z, T& w, T& d, T& a, T& sgn) {
         int szz = 1, iz = z;
         if (z < 0 || z >= nz) iz = odd_ext3(z, nz, szz);
-        if (iz < 0) return T(0);
-        const T x = f[(int64_t)iz * plane + col];
-        return (sxy * szz < 0) ? -x : x;
-    };
-    // plane z's inputs are loaded kPF steps ahead into slot z mod kPF; the march
-    // is unrolled by kPF so every slot is a fixed register (a register queue
-    // that shifted would consume each load one step after issuing it)
-    constexpr int kPF = 4;
-    T pw[kPF], pd[kPF], pa[kPF];
-    auto issue = [&](int z, T& w, T& d, T& a) {
-        const bool live = z < nz + B;
-        w = live ? ld(Win, z) : T(0);
-        d = live ? ld(Din, z) : T(0);
-        a = (own && z >= 0 && z < nz) ? acc[(int64_t)z * plane + ocol] : T(0);
+        const bool live = sxy != 0 && iz >= 0 && z < nz + B;
+        const int64_t gi = (int64_t)(live ? iz : 0) * plane + col;
+        w = T(0);
+        d = T(0);
+        a = T(0);
+        if (live) {
+            w = Win[gi];
+            d = Din[gi];
+        }
+        if (own && z >= 0 && z < nz) a = acc[(int64_t)z * plane + ocol];
+        sgn = live ? T(sxy * szz) : T(0);
     };
 #pragma unroll
-    for (int q = 0; q < kPF; ++q) issue(-B + q, pw[q], pd[q], pa[q]);
+    for (int q = 0; q < kPF; ++q) issue(-B + q, pw[q], pd[q], pa[q], sg[q]);
 
     T Wq[B + 1][3];  // Wq[k]: W of level k-1 at planes p_k - 1, p_k, p_k + 1 (k = 1..B)
     T Dq[B + 1];     // Dq[k]: D of level k-1 at plane p_k
@@ -124,8 +126,8 @@ __global__ void __launch_bounds__(kT3* kT3, 1)
             if (z >= nz + B) break;
             const int buf = z & 1, obuf = buf ^ 1;
             // ---- level 0: plane z of W^n, D^n and its filter sum (loaded kPF steps ago) -
-            const T w0 = pw[j], d0 = pd[j], a0 = pa[j];
-            issue(z + kPF, pw[j], pd[j], pa[j]);
+            const T w0 = sg[j] * pw[j], d0 = sg[j] * pd[j], a0 = pa[j];
+            issue(z + kPF, pw[j], pd[j], pa[j], sg[j]);
             sP[0][buf][me] = w0;
             T dnext = d0;  // D handed from level k-1 to level k (this step's plane p_{k-1})
             T wnext = w0;  // W of level k-1 at plane p_{k-1} = p_k + 1
