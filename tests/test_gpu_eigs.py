@@ -131,3 +131,32 @@ def test_invalid_eigs_params(ew):
             ew.ew_arnoldi_eigs(g, p, e)
         assert ex.value.status == 1
     g.close()
+
+
+def _batched_box_plan(b):
+    """N_p for a box of the batched workload: about 12 eigenvalues within
+    omega / N_p of omega (density A omega / (2 pi) near omega)."""
+    area = b["length"][0] * b["length"][1]
+    return max(4, math.ceil(area * b["omega"] ** 2 / (12 * math.pi)))
+
+
+def test_batched_boxes_per_problem_eigenvalues(ew):
+    """Batched workload (64 uneven boxes, order 2, anisotropic h): the 4
+    eigenpairs nearest each box's omega from FP32 wave-solves with FP64
+    refinement, each eigenvalue against the closed form of its own box.  Run on
+    the six boxes whose eigen-solve is cheapest (the whole set costs minutes of
+    GPU time; every box shares the same code path)."""
+    boxes = ew_inputs.batched_boxes(ew_inputs.BASE_SEED + 3)
+
+    def cost(b):
+        hx, hy = (b["length"][a] / (b["n"][a] + 1) for a in range(2))
+        spp = math.ceil((2 * math.pi / b["omega"]) / (0.8 * 2 / math.sqrt(4 / hx ** 2 + 4 / hy ** 2)))
+        return b["n"][0] * b["n"][1] * spp * _batched_box_plan(b)
+
+    for b in sorted(boxes, key=cost)[:6]:
+        n, L, omega, Np = tuple(b["n"]), tuple(b["length"]), b["omega"], _batched_box_plan(b)
+        lam, rep, info, _ = _solve(ew, n, L, 2, "fp32", omega, Np, 4, 2, 16, refine=1, seed=5)
+        og = O.Grid(n, L, 2)
+        want, _, _ = _wanted(og, O.filter_params(omega, Np, info["steps_per_period"]), 4)
+        np.testing.assert_allclose(np.sort(lam), np.sort(want), rtol=1e-9)
+        assert np.all(rep["eig_res"] <= 1e-8), (n, omega, rep["eig_res"])
