@@ -74,8 +74,9 @@ template <typename T, int R>
 static const std::vector<BVariant>& bvariants();
 template <>
 const std::vector<BVariant>& bvariants<float, 1>() {
-    static const std::vector<BVariant> v = {EW_BVAR(float, 1, 2, 8, 8, 4, 2), EW_BVAR(float, 1, 2, 8, 8, 8, 2),
-                                            EW_BVAR(float, 1, 2, 16, 8, 8, 1), EW_BVAR(float, 1, 2, 4, 16, 8, 2)};
+    static const std::vector<BVariant> v = {EW_BVAR(float, 1, 2, 8, 8, 4, 2),   EW_BVAR(float, 1, 2, 8, 8, 8, 2),
+                                            EW_BVAR(float, 1, 2, 16, 8, 8, 1),  EW_BVAR(float, 1, 2, 4, 16, 8, 2),
+                                            EW_BVAR(float, 1, 2, 16, 8, 12, 1), EW_BVAR(float, 1, 2, 16, 8, 16, 1)};
     return v;
 }
 template <>

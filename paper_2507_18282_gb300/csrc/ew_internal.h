@@ -117,6 +117,9 @@ ew_status launch_apply_L(const GridGeom& g, const T* u, T* Lu, int nvec, double 
 // of scratch; cdev = N_t + 1 weights (device, type T).
 // temporally blocked 3D second-order steps (ew_tb3d.cu)
 template <typename T>
+ew_status tb3d_tune(const GridGeom& g, const FilterPlan& plan, const T* cdev, T* const* F, T* acc, int nvec,
+                    int64_t fstride, cudaStream_t st);
+template <typename T>
 ew_status tb3d_advance(const GridGeom& g, const FilterPlan& plan, const T* cdev, T* const* F, int* prv, int* cur,
                        int64_t L, T* acc, int nvec, int64_t fstride, int tb, cudaStream_t st);
 

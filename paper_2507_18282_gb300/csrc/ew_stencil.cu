@@ -383,6 +383,8 @@ ew_status explicit_wave_solve(const GridGeom& g, const FilterPlan& plan, const T
     const bool blocked = g.dim == 2 && temporal_block != 1;
     // the tuner writes the spare fields and the filter sum, so it runs before the first step
     if (blocked && temporal_block == 0) EW_TRY(tb2d_tune<T>(g, plan, cdev, F, vout, nvec, fstride, st));
+    if (g.dim == 3 && g.order == 2 && temporal_block == 0)
+        EW_TRY(tb3d_tune<T>(g, plan, cdev, F, vout, nvec, fstride, st));
     // F[0] = D^n, F[1] = W^n; the unblocked steps write W^{n+1} to F[2] and swap
     EW_TRY(first_step<T>(g, vin, F[0], F[1], vout, plan, nvec, fstride, st));
     if (blocked) {

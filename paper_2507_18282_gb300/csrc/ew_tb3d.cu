@@ -23,7 +23,13 @@
 // exact, as in the 2D kernel, so planes beyond the box are simply computed.
 // Global traffic per point and launch: W^n, D^n, acc in, W^{n+b}, D^{n+b}, acc
 // out (24 B in FP32), i.e. 24/b B per cell-step.
+#include <stdio.h>
+#include <stdlib.h>
+
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "ew_internal.h"
 
@@ -198,29 +204,96 @@ static ew_status launch_tb3d(const GridGeom& g, const T* Din, const T* Win, T* D
     return EW_OK;
 }
 
+template <typename T>
+static ew_status launch_depth(int B, const GridGeom& g, const T* Din, const T* Win, T* Dout, T* Wout, T* acc,
+                              const T* cw, int b, const Stencil<T>& s, int nvec, int64_t fstride, cudaStream_t st) {
+    if (B == 4) return launch_tb3d<T, 4>(g, Din, Win, Dout, Wout, acc, cw, b, s, nvec, fstride, st);
+    if (B == 3) return launch_tb3d<T, 3>(g, Din, Win, Dout, Wout, acc, cw, b, s, nvec, fstride, st);
+    return launch_tb3d<T, 2>(g, Din, Win, Dout, Wout, acc, cw, b, s, nvec, fstride, st);
+}
+
+// depth autotuner: times depths 2..4 on the caller's buffers (before the real
+// wave-solve overwrites them) and caches the fastest per grid shape
+using Tb3dKey = std::tuple<int64_t, int64_t, int64_t, int, int, int>;  // nx, ny, nz, elem, nvec, device
+static std::map<Tb3dKey, int> g_tb3d_cache;
+static std::mutex g_tb3d_mu;
+
+template <typename T>
+ew_status tb3d_tune(const GridGeom& g, const FilterPlan& plan, const T* cdev, T* const* F, T* acc, int nvec,
+                    int64_t fstride, cudaStream_t st) {
+    if (g.dim != 3 || g.order != 2) return EW_OK;
+    int dev = 0;
+    EW_CUDA_TRY(cudaGetDevice(&dev));
+    Tb3dKey key{g.n[0], g.n[1], g.n[2], (int)sizeof(T), nvec, dev};
+    {
+        std::lock_guard<std::mutex> lk(g_tb3d_mu);
+        if (g_tb3d_cache.count(key)) return EW_OK;
+    }
+    Stencil<T> s = make_stencil<T>(g, plan.dt * plan.dt);
+    bool prof = g_profile_on;
+    g_profile_on = false;  // tuning launches are not counted
+    cudaEvent_t e0, e1;
+    EW_CUDA_TRY(cudaEventCreate(&e0));
+    EW_CUDA_TRY(cudaEventCreate(&e1));
+    int best = 4;
+    double best_rate = -1.0;
+    ew_status status = EW_OK;
+    for (int B = 2; B <= 4 && status == EW_OK; ++B) {
+        for (int rep = 0; rep < 3 && status == EW_OK; ++rep) {  // one warm launch, two timed
+            if (rep == 1) cudaEventRecord(e0, st);
+            status = launch_depth<T>(B, g, F[0], F[1], F[2], F[3], acc, cdev, B, s, nvec, fstride, st);
+        }
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double rate = 2.0 * B / std::max(ms, 1e-6f);  // time steps per ms
+        if (getenv("EW_TUNE_LOG"))
+            fprintf(stderr, "[ew tune] %lldx%lldx%lld 3D order 2 %s: depth %d: %.4f ms/step\n", (long long)g.n[0],
+                    (long long)g.n[1], (long long)g.n[2], sizeof(T) == 4 ? "fp32" : "fp64", B, 1.0 / rate);
+        if (rate > best_rate) {
+            best_rate = rate;
+            best = B;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g_profile_on = prof;
+    EW_TRY(status);
+    std::lock_guard<std::mutex> lk(g_tb3d_mu);
+    g_tb3d_cache[key] = best;
+    return EW_OK;
+}
+template ew_status tb3d_tune<float>(const GridGeom&, const FilterPlan&, const float*, float* const*, float*, int,
+                                    int64_t, cudaStream_t);
+template ew_status tb3d_tune<double>(const GridGeom&, const FilterPlan&, const double*, double* const*, double*, int,
+                                     int64_t, cudaStream_t);
+
 // Advance from level L (W = F[cur], D = F[prv]) to level Nt in launches of up
-// to B levels (B = 4, or `tb` when 1 < tb < 4).  Second-order 3D grids only.
+// to B levels (the tuned depth, 4 before tuning, or `tb` when 1 < tb <= 4).
+// Second-order 3D grids only.
 template <typename T>
 ew_status tb3d_advance(const GridGeom& g, const FilterPlan& plan, const T* cdev, T* const* F, int* prv, int* cur,
                        int64_t L, T* acc, int nvec, int64_t fstride, int tb, cudaStream_t st) {
     if (g.dim != 3 || g.order != 2) return set_error(EW_EUNSUPPORTED, "3D temporal blocking is second order only");
     if (nvec > 65535) return set_error(EW_EUNSUPPORTED, "too many vectors in one call");
     Stencil<T> s = make_stencil<T>(g, plan.dt * plan.dt);
-    const int B = (tb > 1 && tb < 4) ? tb : 4;
+    int B = 4;
+    if (tb > 1) {
+        B = std::min(tb, 4);
+    } else {
+        int dev = 0;
+        EW_CUDA_TRY(cudaGetDevice(&dev));
+        std::lock_guard<std::mutex> lk(g_tb3d_mu);
+        auto it = g_tb3d_cache.find(Tb3dKey{g.n[0], g.n[1], g.n[2], (int)sizeof(T), nvec, dev});
+        if (it != g_tb3d_cache.end()) B = it->second;
+    }
     int p = *prv, c = *cur, a = -1, d = -1;
     for (int q = 0; q < 4; ++q)
         if (q != p && q != c) (a < 0 ? a : d) = q;
     while (L < plan.Nt) {
         const int b = (int)std::min<int64_t>(B, plan.Nt - L);
-        const T* cw = cdev + L + 1;
-        ew_status s2;
-        if (B == 4)
-            s2 = launch_tb3d<T, 4>(g, F[p], F[c], F[a], F[d], acc, cw, b, s, nvec, fstride, st);
-        else if (B == 3)
-            s2 = launch_tb3d<T, 3>(g, F[p], F[c], F[a], F[d], acc, cw, b, s, nvec, fstride, st);
-        else
-            s2 = launch_tb3d<T, 2>(g, F[p], F[c], F[a], F[d], acc, cw, b, s, nvec, fstride, st);
-        EW_TRY(s2);
+        EW_TRY(launch_depth<T>(B, g, F[p], F[c], F[a], F[d], acc, cdev + L + 1, b, s, nvec, fstride, st));
         L += b;
         std::swap(p, a);
         std::swap(c, d);
