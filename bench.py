@@ -417,7 +417,7 @@ def run_extra(args):
         bytes_launch = 24 * prof["fused_points"] / launches  # per launch: W^n, D^n, acc in; W^{n+b}, D^{n+b}, acc out
         line = dict(workload="cube3d_511_order2_fp32_explicit", metric=METRIC, unit=UNIT,
                     value=cells / (ms / 1e3) / 1e9, ms_per_step=ms / args.steps, time_steps_per_step=info["Nt"],
-                    roofline=dict(bound="hbm", kernel="k_step_tb3d<float,4>", bytes_per_launch=bytes_launch,
+                    roofline=dict(bound="hbm", kernel="k_step_tb3d<float, tuned depth>", bytes_per_launch=bytes_launch,
                                   achieved=bytes_launch / (mean / 1e3) / 1e9, peak=pk["hbm_gbs"], unit="GB/s",
                                   frac=bytes_launch / (mean / 1e3) / 1e9 / pk["hbm_gbs"], peak_source=pk_kind))
     elif w == "batched":
