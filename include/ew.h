@@ -28,7 +28,10 @@
  *    (simple Rayleigh quotient, eq. simpleRayleighQuotient).
  *  - Errors: every call returns an ew_status; on failure ew_last_error()
  *    returns a message for the calling thread.  No exception crosses the ABI.
- *    Device-side waits are bounded and report EW_ETIMEOUT.
+ *    Device-side waits are bounded and report EW_ETIMEOUT.  A wave-solve
+ *    returns before its kernels run, so a wait that gave up there is reported
+ *    by the next call that synchronises (the autotuner, ew_rayleigh and the
+ *    solvers built on it); the outputs of that wave-solve are then invalid.
  */
 #ifndef EW_H_
 #define EW_H_

@@ -387,6 +387,7 @@ static ew_status rayleigh_t(ew_grid* g, const T* phi, int nvec, double* lam_host
     double* h = (double*)hp;
     EW_CUDA_TRY(cudaMemcpyAsync(h, dnum, sizeof(double) * 2 * nvec, cudaMemcpyDeviceToHost, st));
     EW_CUDA_TRY(cudaStreamSynchronize(st));
+    EW_TRY(rb2d_check_timeout());  // a register-blocked wave-solve before this point gave up a wait
     std::vector<double> lam2(nvec);
     for (int j = 0; j < nvec; ++j) {
         double den = h[nvec + j];

@@ -281,7 +281,7 @@ template <int R, int NTY, int KY, int B>
 __global__ void __launch_bounds__(32 * NTY, 1)
     k_step_rb2d(int nx, int ny, const float* __restrict__ Ain, const float* __restrict__ Bin, float* __restrict__ Aout,
                 float* __restrict__ Bout, float* __restrict__ acc, const float* __restrict__ cw, int b, Stencil<float> st,
-                int64_t fstride, int tiles_x, int tiles_per_vec, int ntiles) {
+                int64_t fstride, int tiles_x, int tiles_per_vec, int ntiles, unsigned stall_tx) {
     using S = Rb2dShape<R, NTY, KY, B>;
     constexpr int CW = S::CW, CH = S::CH, NT = S::NT, PITCH = S::PITCH, H = S::H, TX = S::TX, TY = S::TY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -302,6 +302,9 @@ __global__ void __launch_bounds__(32 * NTY, 1)
         rb_tile(t, tiles_x, tiles_per_vec, TX, TY, H, v, x0, y0);
         rb_issue<CH, CW, PITCH, NT>(Ain, Bin, nx, ny, N, v, fstride, x0, y0, stage, bar, tid);
     }
+    // stall_tx > 0 (a test of the bounded wait): expect bytes that never arrive, so
+    // the first wait runs out and the CTA reports it and returns
+    if (tid == 0 && stall_tx) mbar_expect_tx(bar, stall_tx);
     __syncthreads();
     if (tid == 0) mbar_arrive(bar);
 
@@ -433,9 +436,11 @@ ew_status rb2d_launch(const Rb2dDesc& d, const GridGeom& g, const float* Ain, co
     if (nt64 > INT32_MAX) return set_error(EW_EUNSUPPORTED, "register-blocked step: too many tiles");
     int ntiles = (int)nt64;
     int grid = std::min(ntiles, nsm);
+    // EW_TEST_RB2D_STALL: test hook that makes every CTA's first staging wait run out
+    unsigned stall_tx = getenv("EW_TEST_RB2D_STALL") ? 16u : 0u;
     void* args[] = {(void*)&nx,   (void*)&ny, (void*)&Ain, (void*)&Bin,     (void*)&Aout,          (void*)&Bout,
                     (void*)&acc,  (void*)&cw, (void*)&b,   (void*)&s,       (void*)&fstride,       (void*)&tiles_x,
-                    (void*)&tiles_per_vec, (void*)&ntiles};
+                    (void*)&tiles_per_vec, (void*)&ntiles, (void*)&stall_tx};
     cudaEvent_t ev = fused_begin(st);
     EW_CUDA_TRY(cudaLaunchKernel(d.fn, dim3(grid), dim3(d.threads), args, d.smem, st));
     fused_end(ev, st, g.N * nvec, g.N * nvec * b);

@@ -218,6 +218,7 @@ static ew_status autotune(const GridGeom& g, T* const* F, T* acc, const T* cw, c
         }
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
+        if (status == EW_OK && var.kind == 1) status = rb2d_check_timeout();
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         double rate = (double)b * 3.0 / std::max(ms, 1e-6f);  // time steps per ms

@@ -299,3 +299,41 @@ def test_invalid_calls(ew):
     with pytest.raises(TypeError):
         ew.ew_filter_apply(g, p, x[:1200].double(), x[1200:].double())
     g.close()
+
+
+def test_register_blocked_staging_wait_gives_up_cleanly(ew, monkeypatch):
+    """Failure handling without a fault: the register-blocked kernel's waits on
+    its bulk copies are bounded (about 2 s).  A test hook makes every CTA expect
+    16 bytes that never arrive, so its first wait runs out; the kernel records
+    that and returns, the next synchronising call reports EW_ETIMEOUT, and the
+    device stays usable: the same wave-solve without the hook then matches the
+    shared-memory kernel bit for bit."""
+    n, L = (300, 140), (1.0, 0.5)
+    count = 0
+    for i in range(64):  # the register-blocked forms are the last entries of the variant list
+        monkeypatch.setenv("EW_TB2D_VARIANT", str(i))
+        try:
+            _run(ew, n, L, 4, "fp32", 20.0, spp=8)
+        except ew.EWError:
+            break
+        count += 1
+    last = count - 1
+    g = ew.ew_grid_create(2, n, L, order=4, prec="fp32")
+    p = ew.filter_params(40.0, num_periods=1, steps_per_period=8)
+    vin = torch.tensor(ew_inputs.uniform_pm1(77, g.size), dtype=torch.float32, device="cuda")
+    out = torch.empty_like(vin)
+    monkeypatch.setenv("EW_TB2D_VARIANT", str(last))
+    monkeypatch.setenv("EW_TEST_RB2D_STALL", "1")
+    ew.ew_filter_apply(g, p, vin, out)  # returns before the kernels run
+    with pytest.raises(ew.EWError) as e:
+        ew.ew_rayleigh(g, out, nvec=1)
+    assert e.value.status == 6  # EW_ETIMEOUT
+    monkeypatch.delenv("EW_TEST_RB2D_STALL")
+    ew.ew_filter_apply(g, p, vin, out)
+    monkeypatch.setenv("EW_TB2D_VARIANT", "0")
+    ref = torch.empty_like(vin)
+    ew.ew_filter_apply(g, p, vin, ref)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    ew.ew_rayleigh(g, out, nvec=1)  # no stale report left behind
+    g.close()
