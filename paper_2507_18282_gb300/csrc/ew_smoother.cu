@@ -222,6 +222,9 @@ constexpr int kHP = kHX * kHY;                       // 324 hidden points per pl
 constexpr int kHG = (kHP + 15) / 16;                 // 21 row blocks of 16
 constexpr int kZS = kHG * 16 + 4;                    // Z row stride (340: conflict-free stores)
 constexpr int kRP = kRX * kRY;                       // 400 residual points per plane
+constexpr int kRS = (kRP + 31) / 32 * 32;            // plane slot stride (416: bank-aligned slots)
+__device__ constexpr int kTapOrder[32] = {10, 24, 25, 14, 23, 7,  13, 2,  -1, 0, 16, 12, 15, -1, 9,  4,
+                                          21, 6,  -1, 18, 22, 8, 19, -1, 17, 1, 3,  -1, 26, 5,  20, 11};
 constexpr int kTcThreads = kOX * kOY;                // 256: one output column each
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -237,12 +240,12 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 }
 
 template <bool ADD>
-__global__ void __launch_bounds__(kTcThreads)
+__global__ void __launch_bounds__(kTcThreads, 4)
     k_smoother_fwd_tc(int nx, int ny, int nz, const float* __restrict__ w, const float* __restrict__ r,
                       float* __restrict__ out) {
     extern __shared__ __align__(16) float smem_tc[];
-    float* sR = smem_tc;               // [3][kRP]: residual planes, ring indexed by plane mod 3
-    float* sZ = smem_tc + 3 * kRP;     // [27][kZS]: Z of the current hidden plane
+    float* sR = smem_tc;               // [3][kRS]: residual planes, ring indexed by plane mod 3
+    float* sZ = smem_tc + 3 * kRS;     // [27][kZS]: Z of the current hidden plane
     int* sHB = reinterpret_cast<int*>(sZ + 27 * kZS);  // [kHG * 16]: residual offset of each hidden point, -1 outside
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, tig = lane & 3;
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(kTcThreads)
         sHB[q] = (q < kHP && gx >= 0 && gy >= 0 && gx < nx && gy < ny) ? hy * kRX + hx : -1;
     }
     auto load_plane = [&](int zr) {  // residual plane zr (BF16-rounded, zero outside) into its ring slot
-        float* dst = sR + ((zr + 3) % 3) * kRP;
+        float* dst = sR + ((zr + 3) % 3) * kRS;
         for (int q = tid; q < kRP; q += kTcThreads) {
             const int lx = q % kRX, ly = q / kRX;
             dst[q] = ld_r(r, x0 - 2 + lx, y0 - 2 + ly, zr, nx, ny, nz);
@@ -263,12 +266,20 @@ __global__ void __launch_bounds__(kTcThreads)
     };
     // B fragments (fixed per thread).  Layer 1, k-step s: b0 = B1[16s + 2tig (+1)][g],
     // b1 = B1[16s + 2tig + 8 (+1)][g] with B1[k][c] = W1[c][k] (0 for k >= 27).
-    auto w1 = [&](int k, int c) { return k < 27 ? w[c * 27 + k] : 0.f; };
+    // K order of layer 1.  Slot e (0..7) of lane group tig holds tap kTapOrder[4e + tig]
+    // (k = 16 (e >> 2) + 2 tig + (e & 1) + 8 ((e >> 1) & 1) in the MMA); any order works as
+    // long as A and B use the same one.  This one keeps the four lanes of one load on
+    // different shared-memory banks as far as the 27 offsets allow (searched offline for
+    // the row pitch kRX = 20 and 32-float-aligned plane slots); -1 marks a padding slot,
+    // which reads the address of another lane of its load (a broadcast) times a zero weight.
+    const int tapo[8] = {kTapOrder[tig], kTapOrder[4 + tig], kTapOrder[8 + tig], kTapOrder[12 + tig],
+                         kTapOrder[16 + tig], kTapOrder[20 + tig], kTapOrder[24 + tig], kTapOrder[28 + tig]};
+    auto w1 = [&](int tap, int c) { return tap >= 0 ? w[c * 27 + tap] : 0.f; };
     uint32_t b1f[2][2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        b1f[s][0] = pack_bf16(w1(16 * s + 2 * tig, g), w1(16 * s + 2 * tig + 1, g));
-        b1f[s][1] = pack_bf16(w1(16 * s + 2 * tig + 8, g), w1(16 * s + 2 * tig + 9, g));
+        b1f[s][0] = pack_bf16(w1(tapo[4 * s], g), w1(tapo[4 * s + 1], g));
+        b1f[s][1] = pack_bf16(w1(tapo[4 * s + 2], g), w1(tapo[4 * s + 3], g));
     }
     // layer 2, n-tile j: b0 = B2[2tig (+1)][8j + g] = W2[2tig (+1)][8j + g], b1 = 0 (k >= 8)
     uint32_t b2f[4];
@@ -277,15 +288,17 @@ __global__ void __launch_bounds__(kTcThreads)
         const int o = 8 * j + g;
         b2f[j] = o < 27 ? pack_bf16(w[kW + (2 * tig) * 27 + o], w[kW + (2 * tig + 1) * 27 + o]) : 0u;
     }
-    // this thread's im2col taps: k-step s holds taps 16s + {2tig, 2tig+1, 2tig+8, 2tig+9};
-    // tap k = (dz+1) 9 + (dy+1) 3 + (dx+1): residual plane dz (relative), offset dy * kRX + dx
+    // this thread's im2col taps; tap t = (dz+1) 9 + (dy+1) 3 + (dx+1): residual plane dz
+    // (relative), offset dy * kRX + dx
     int tdz[8], toff[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        const int k = 16 * (e >> 2) + 2 * tig + (e & 1) + ((e >> 1) & 1) * 8;
-        const int kk = k < 27 ? k : 13;  // padded taps read a valid point, times a zero weight
-        tdz[e] = kk / 9;
-        toff[e] = ((kk / 3) % 3) * kRX + kk % 3;
+        int t = tapo[e];
+        if (t < 0)  // padding: the address of the first real tap of this load
+            for (int u = 3; u >= 0; --u)
+                if (kTapOrder[4 * e + u] >= 0) t = kTapOrder[4 * e + u];
+        tdz[e] = t / 9;
+        toff[e] = ((t / 3) % 3) * kRX + t % 3;
     }
     load_plane(z0 - 2);
     load_plane(z0 - 1);
@@ -304,7 +317,7 @@ __global__ void __launch_bounds__(kTcThreads)
         }
     };
     auto commit = [&](int zr) {
-        float* dst = sR + ((zr + 3) % 3) * kRP;
+        float* dst = sR + ((zr + 3) % 3) * kRS;
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const int q = tid + u * kTcThreads;
@@ -323,7 +336,7 @@ __global__ void __launch_bounds__(kTcThreads)
         const bool zin = hz >= 0 && hz < nz;
         if (zin) {
             // ring slots of residual planes hz - 1, hz, hz + 1 -> each tap's offset in sR
-            const int s0 = ((hz + 2) % 3) * kRP, s1 = ((hz + 3) % 3) * kRP, s2 = ((hz + 4) % 3) * kRP;
+            const int s0 = ((hz + 2) % 3) * kRS, s1 = ((hz + 3) % 3) * kRS, s2 = ((hz + 4) % 3) * kRS;
             int tap[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) tap[e] = (tdz[e] == 0 ? s0 : tdz[e] == 1 ? s1 : s2) + toff[e];
@@ -400,7 +413,7 @@ static dim3 tc_tiles(const GridGeom& g) {
                 (unsigned)((g.n[2] + kZC - 1) / kZC));
 }
 
-constexpr size_t kTcSmem = sizeof(float) * (3 * (size_t)kRP + 27 * (size_t)kZS) + sizeof(int) * kHG * 16;
+constexpr size_t kTcSmem = sizeof(float) * (3 * (size_t)kRS + 27 * (size_t)kZS) + sizeof(int) * kHG * 16;
 
 template <bool ADD>
 static ew_status launch_fwd_tc(const GridGeom& g, const float* w, const float* r, float* out, cudaStream_t st);
