@@ -313,13 +313,13 @@ def test_register_blocked_staging_wait_gives_up_cleanly(ew, monkeypatch):
     for i in range(64):  # the register-blocked forms are the last entries of the variant list
         monkeypatch.setenv("EW_TB2D_VARIANT", str(i))
         try:
-            _run(ew, n, L, 4, "fp32", 20.0, spp=8)
+            _run(ew, n, L, 4, "fp32", 400.0)
         except ew.EWError:
             break
         count += 1
     last = count - 1
     g = ew.ew_grid_create(2, n, L, order=4, prec="fp32")
-    p = ew.filter_params(40.0, num_periods=1, steps_per_period=8)
+    p = ew.filter_params(400.0, num_periods=1)  # about 10 steps: two launches, each wait runs out once
     vin = torch.tensor(ew_inputs.uniform_pm1(77, g.size), dtype=torch.float32, device="cuda")
     out = torch.empty_like(vin)
     monkeypatch.setenv("EW_TB2D_VARIANT", str(last))
