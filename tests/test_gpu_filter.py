@@ -337,3 +337,28 @@ def test_register_blocked_staging_wait_gives_up_cleanly(ew, monkeypatch):
     assert torch.equal(out, ref)
     ew.ew_rayleigh(g, out, nvec=1)  # no stale report left behind
     g.close()
+
+
+@pytest.mark.parametrize("k", [(2, 3, 4), (19, 17, 21)])
+def test_cube_511_mode_amplification(ew, k):
+    """Full-size 3D workload (511^3, order 2, FP32, CFL 0.8, omega = 60, one
+    period) through the launch configuration the bench times (temporally
+    blocked 2.5D kernel at its tuned depth): a sine mode is an eigenvector of S,
+    so S phi_k = beta~_d(lambda_k) phi_k (eq. correctedBeta with the time
+    correction of eq. discreteExplicitLambdaTilde).  A low mode and one near
+    the peak; FP32 error bound 4 N_t eps relative."""
+    n, L, omega = (511, 511, 511), (1.0, 1.0, 1.0), 60.0
+    og = O.Grid(n, L, 2)
+    phi = O.sine_mode(og, k)
+    lam = math.sqrt(O.lambda2_closed_form(og, [k])[0])
+    g = ew.ew_grid_create(3, n, L, order=2, prec="fp32")
+    p = ew.filter_params(omega)
+    info, _ = ew.ew_filter_setup(g, p)
+    vin = torch.tensor(phi, dtype=torch.float32, device="cuda")
+    vout = torch.empty_like(vin)
+    ew.ew_filter_apply(g, p, vin, vout)
+    torch.cuda.synchronize()
+    beta = O.beta_tilde(lam, O.filter_params(omega, 1, info["steps_per_period"]))[0]
+    err = np.linalg.norm(vout.cpu().double().numpy() - beta * phi) / np.linalg.norm(phi)
+    assert err < 4 * info["Nt"] * EPS32, (err, beta)
+    g.close()
