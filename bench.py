@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--workload", choices=["rect2d", "cube3d", "batched", "implicit3d", "mg3d", "eigs2d"],
                     default="rect2d",
                     help="rect2d is the headline line; the others print their own line")
-    ap.add_argument("--num-periods", type=int, default=64, help="N_p of the eigs2d workload")
+    ap.add_argument("--num-periods", type=int, default=0,
+                    help="N_p of the eigs2d workload (0: the library's choice, ew_choose_num_periods)")
     return ap.parse_args()
 
 
@@ -490,9 +491,15 @@ def run_extra(args):
         # FP32 wave-solves + FP64 refinement against FP64 wave-solves throughout
         n, L = (2047, 3071), (1.0, 1.5)
         runs = {}
+        num_periods, cr_est = args.num_periods, None
+        if num_periods <= 0:  # the convergence estimate of simultaneous iteration over the box's spectrum
+            g = ew.ew_grid_create(2, n, L, order=4, prec="fp32")
+            num_periods, cr = ew.ew_choose_num_periods(g, ew.filter_params(150.0), 8, 32, max_periods=1024)
+            cr_est = float(cr[num_periods.bit_length() - 1])
+            g.close()
         for name, prec, refine, tol in [("fp32_fp64_refine", "fp32", 1, 0.0), ("plain_fp64", "fp64", 0, 1e-10)]:
             g = ew.ew_grid_create(2, n, L, order=4, prec=prec)
-            p = ew.filter_params(150.0, num_periods=args.num_periods)
+            p = ew.filter_params(150.0, num_periods=num_periods)
             e = ew.eigs_params(8, krylov_dim=32, block=4, tol=tol, seed=7, refine_fp64=refine,
                                max_wave_solves=600)
             torch.cuda.synchronize()
@@ -508,7 +515,7 @@ def run_extra(args):
                               max_rel_err=max(err))
             g.close()
         line = dict(workload="eigs_rect2d_2047x3071_order4_8_nearest_omega150", unit="s",
-                    num_periods=args.num_periods, metric="s to 8 eigenpairs at 1e-8 resid vs plain", runs=runs,
+                    num_periods=num_periods, cr_estimate=cr_est, metric="s to 8 eigenpairs at 1e-8 resid vs plain", runs=runs,
                     speedup=runs["plain_fp64"]["seconds"] / runs["fp32_fp64_refine"]["seconds"])
     else:
         raise SystemExit("unknown workload %s" % w)

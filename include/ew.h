@@ -140,6 +140,21 @@ typedef struct {
 ew_status ew_filter_setup(const ew_grid* grid, const ew_filter_params* params,
                           ew_filter_info* info_host, double* weights_host, int64_t weights_cap);
 
+/* Number of filter periods N_p for an eigen-solve of n_wanted pairs with a
+ * Krylov dimension krylov_dim (Section "Estimating the EigenWave convergence
+ * rate based on simultaneous iteration", eq. subSpaceIterationCR: CR =
+ * beta_{N_a+1} / beta_{N_r}, N_r = n_wanted, N_a = krylov_dim, beta_j the
+ * filter values beta_d of the grid's discrete eigenvalues in decreasing
+ * order).  For N_p = 1, 2, 4, ..., max_periods, with the other fields of
+ * params as given (omega, scheme, CFL or steps per period, adjust_omega), the
+ * estimated cost N_p / (-ln CR) is evaluated from the exact discrete spectrum
+ * of the box (tensor sine modes) and the cheapest N_p is written to
+ * *num_periods.  cr_host (may be NULL; capacity floor(log2(max_periods)) + 1)
+ * receives CR for each candidate.  Host work only (no GPU, no stream).
+ * EW_EUNSUPPORTED if no candidate gives CR < 1. */
+ew_status ew_choose_num_periods(const ew_grid* grid, const ew_filter_params* params, int n_wanted,
+                                int krylov_dim, int max_periods, int* num_periods, double* cr_host);
+
 /* v_out = S v_in for each of `nvec` vectors: one wave-solve (Algorithm matVec
  * with the explicit or implicit scheme and the trapezoidal filter).  v_in and
  * v_out are device blocks of nvec vectors in the grid precision; they must not

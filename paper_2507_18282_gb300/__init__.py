@@ -20,7 +20,8 @@ from ._lib import (EW_EXPLICIT, EW_FP32, EW_FP64, EW_IMPLICIT, EWError, check, l
                    ew_filter_info, ew_filter_params, ew_mg_params)
 
 __all__ = ["Grid", "EWError", "ew_grid_create", "ew_grid_destroy", "filter_params", "mg_params",
-           "ew_filter_setup", "ew_filter_apply", "ew_apply_L", "ew_rayleigh", "ew_power_iteration",
+           "ew_filter_setup", "ew_choose_num_periods", "ew_filter_apply", "ew_apply_L", "ew_rayleigh",
+           "ew_power_iteration",
            "ew_last_error", "LIB_PATH"]
 
 LIB_PATH = _lib.LIB_PATH
@@ -111,6 +112,17 @@ def ew_filter_setup(grid: Grid, params):
                               w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), w.size))
     return dict(omega=info.omega_used, Tf=info.final_time, dt=info.dt, alpha_d=info.alpha_d,
                 Nt=info.num_steps, steps_per_period=info.steps_per_period), w
+
+
+def ew_choose_num_periods(grid: Grid, params, n_wanted, krylov_dim, max_periods=1024):
+    """(N_p, CR estimate per candidate N_p = 1, 2, 4, ... as a float64 numpy array)."""
+    ncand = int(max_periods).bit_length()
+    cr = np.zeros(ncand)
+    npc = ctypes.c_int(0)
+    check(lib.ew_choose_num_periods(grid.handle, ctypes.byref(params), int(n_wanted), int(krylov_dim),
+                                    int(max_periods), ctypes.byref(npc),
+                                    cr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return npc.value, cr
 
 
 def ew_filter_apply(grid: Grid, params, v_in, v_out, nvec=None, stream=None):

@@ -403,7 +403,7 @@ struct KSRun {
 // beta_d of the discrete filter at a spatial eigenvalue lambda: eq. betad with
 // the time-corrected frequency of eq. discreteExplicitLambdaTilde (explicit)
 // or eq. discreteCorr (implicit).  Modes beyond the leapfrog limit get -1.
-static double filter_beta(const FilterPlan& plan, ew_scheme scheme, double lam) {
+double filter_beta(const FilterPlan& plan, ew_scheme scheme, double lam) {
     const double dt = plan.dt;
     double x;
     if (scheme == EW_EXPLICIT) {
