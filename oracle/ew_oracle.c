@@ -7,13 +7,17 @@
  *
  * Everything here is written for a reader checking it against the paper
  * (Appelo, Banks, Henshaw, Le, Schwendeman, "EigenWave", arXiv 2507.18282):
- *   - grid functions live on a Cartesian box with homogeneous Dirichlet
- *     conditions (eq. eigBVPdiscrete), vectors hold the active (interior)
- *     points only, x fastest (Algorithm "matVec", Note 1);
+ *   - grid functions live on a Cartesian box (eq. eigBVPdiscrete) whose
+ *     faces carry homogeneous Dirichlet conditions or, as the paper does for
+ *     a symmetry plane, Neumann conditions; vectors hold the active points
+ *     only, x fastest (Algorithm "matVec", Note 1): the interior points, plus
+ *     the wall points of a Neumann face;
  *   - L_h is the 2nd-order (5/7-point) or 4th-order (9/13-point wide cross)
- *     centred Laplacian.  The 4th-order boundary closure (the paper leaves the
- *     compatibility conditions out) is the odd reflection u_{-j} = -u_{j}
- *     about the boundary point, which is u = 0 and u_xx = 0 on the wall;
+ *     centred Laplacian.  The boundary closure (the paper leaves the
+ *     compatibility conditions out) is a reflection about the wall point:
+ *     Dirichlet, u = 0 on the wall and the odd reflection u_{-j} = -u_{j}
+ *     beyond it (u = 0 and u_xx = 0 on the wall); Neumann, the even
+ *     reflection u_{-j} = u_{j} (the centred normal derivative vanishes);
  *   - the explicit scheme is eq. explicitScheme with the first step
  *     eq. explicitStep1, the implicit one eq. implicitScheme with
  *     M = I - (dt^2/2) L_h (eq. impMatrix) and first step eq. implicitStep1;
@@ -32,24 +36,29 @@
 
 typedef struct {
     int dim;        /* 2 or 3 */
-    long n[3];      /* interior points per axis (n[2] = 1 in 2D) */
+    long n[3];      /* active points per axis (n[2] = 1 in 2D) */
     double h[3];    /* grid spacing per axis */
     int order;      /* 2 or 4 */
+    int neu[6];     /* face f = 2 axis + side (0 low, 1 high): 1 Neumann, 0 Dirichlet */
     long p[3];      /* padded extents */
     long npad;      /* padded size */
     long nact;      /* active size */
 } og_grid;
 
-static int og_init(og_grid* g, int dim, const long* n, const double* h, int order) {
+/* bc: six face flags (1 = Neumann) or NULL for all Dirichlet */
+static int og_init(og_grid* g, int dim, const long* n, const double* h, int order, const int* bc) {
     if (dim != 2 && dim != 3) return -1;
     if (order != 2 && order != 4) return -1;
     g->dim = dim;
     g->order = order;
     g->npad = 1;
     g->nact = 1;
+    for (int f = 0; f < 6; ++f) g->neu[f] = (bc && f < 2 * dim) ? (bc[f] != 0) : 0;
     for (int a = 0; a < 3; ++a) {
         if (a < dim) {
             if (n[a] < 1) return -1;
+            /* a Neumann ghost mirrors the point two in from the wall */
+            if ((g->neu[2 * a] || g->neu[2 * a + 1]) && n[a] < 3) return -1;
             g->n[a] = n[a];
             g->h[a] = h[a];
             g->p[a] = n[a] + 2 * OG_G;
@@ -64,8 +73,10 @@ static int og_init(og_grid* g, int dim, const long* n, const double* h, int orde
     return 0;
 }
 
-/* padded index of interior point (i, j, k), 0-based interior coordinates;
- * i = -1 and i = n are boundary points, i = -2 and i = n+1 ghosts. */
+/* padded index of active point (i, j, k), 0-based active coordinates; i = -1,
+ * -2 and i = n, n+1 are the two layers beyond the active points on each side
+ * (for a Dirichlet face: the wall point and a ghost; for a Neumann face,
+ * whose wall point is active point 0 or n-1: two ghosts). */
 static long og_at(const og_grid* g, long i, long j, long k) {
     long gi = i + OG_G;
     long gj = j + OG_G;
@@ -84,32 +95,43 @@ static void og_scatter(const og_grid* g, const double* v, double* U) {
             for (long i = 0; i < g->n[0]; ++i) U[og_at(g, i, j, k)] = v[m++];
 }
 
-/* Dirichlet: boundary points are zero, ghosts are the odd reflection of the
- * first interior points (only the 4th-order stencil reads them). */
+/* the two layers beyond one face of a line of points: U(x) for x = base +
+ * t stride, t = -2 .. n+1, active for 0 <= t < n.
+ *   Dirichlet low:  U(-1) = 0,      U(-2) = -U(0)     (odd about the wall t = -1)
+ *   Neumann low:    U(-1) = U(1),   U(-2) = U(2)      (even about the wall t = 0)
+ *   Dirichlet high: U(n) = 0,       U(n+1) = -U(n-1)  (odd about the wall t = n)
+ *   Neumann high:   U(n) = U(n-2),  U(n+1) = U(n-3)   (even about the wall t = n-1) */
+static void og_fill_line(double* U, long base, long stride, long n, int neu_lo, int neu_hi) {
+#define AT(t) U[base + (t) * stride]
+    if (neu_lo) {
+        AT(-1) = AT(1);
+        AT(-2) = AT(2);
+    } else {
+        AT(-1) = 0.0;
+        AT(-2) = -AT(0);
+    }
+    if (neu_hi) {
+        AT(n) = AT(n - 2);
+        AT(n + 1) = AT(n - 3);
+    } else {
+        AT(n) = 0.0;
+        AT(n + 1) = -AT(n - 1);
+    }
+#undef AT
+}
+
+/* fill the inactive layers of every line of active points, axis by axis (the
+ * cross-shaped stencils never read the corner blocks). */
 static void og_fill_bc(const og_grid* g, double* U) {
     long n0 = g->n[0], n1 = g->n[1], n2 = g->n[2];
+    long sy = g->p[0], sz = g->p[0] * g->p[1];
     for (long k = 0; k < n2; ++k)
-        for (long j = 0; j < n1; ++j) {
-            U[og_at(g, -1, j, k)] = 0.0;
-            U[og_at(g, n0, j, k)] = 0.0;
-            U[og_at(g, -2, j, k)] = -U[og_at(g, 0, j, k)];
-            U[og_at(g, n0 + 1, j, k)] = -U[og_at(g, n0 - 1, j, k)];
-        }
+        for (long j = 0; j < n1; ++j) og_fill_line(U, og_at(g, 0, j, k), 1, n0, g->neu[0], g->neu[1]);
     for (long k = 0; k < n2; ++k)
-        for (long i = 0; i < n0; ++i) {
-            U[og_at(g, i, -1, k)] = 0.0;
-            U[og_at(g, i, n1, k)] = 0.0;
-            U[og_at(g, i, -2, k)] = -U[og_at(g, i, 0, k)];
-            U[og_at(g, i, n1 + 1, k)] = -U[og_at(g, i, n1 - 1, k)];
-        }
+        for (long i = 0; i < n0; ++i) og_fill_line(U, og_at(g, i, 0, k), sy, n1, g->neu[2], g->neu[3]);
     if (g->dim == 3)
         for (long j = 0; j < n1; ++j)
-            for (long i = 0; i < n0; ++i) {
-                U[og_at(g, i, j, -1)] = 0.0;
-                U[og_at(g, i, j, n2)] = 0.0;
-                U[og_at(g, i, j, -2)] = -U[og_at(g, i, j, 0)];
-                U[og_at(g, i, j, n2 + 1)] = -U[og_at(g, i, j, n2 - 1)];
-            }
+            for (long i = 0; i < n0; ++i) og_fill_line(U, og_at(g, i, j, 0), sz, n2, g->neu[4], g->neu[5]);
 }
 
 /* L_h at one interior point of a padded grid function whose inactive points
@@ -136,10 +158,10 @@ static double og_lap_point(const og_grid* g, const double* U, long i, long j, lo
     return sum;
 }
 
-/* Lu = L_h u on active vectors. */
-int og_apply_L(int dim, const long* n, const double* h, int order, const double* u, double* Lu) {
+/* Lu = L_h u on active vectors; bc: six face flags (1 = Neumann) or NULL. */
+int og_apply_L(int dim, const long* n, const double* h, int order, const int* bc, const double* u, double* Lu) {
     og_grid g;
-    if (og_init(&g, dim, n, h, order)) return -1;
+    if (og_init(&g, dim, n, h, order, bc)) return -1;
     double* U = (double*)malloc(sizeof(double) * (size_t)g.npad);
     if (!U) return -2;
     og_scatter(&g, u, U);
@@ -158,10 +180,10 @@ int og_apply_L(int dim, const long* n, const double* h, int order, const double*
  *   W^{n+1} = 2 W^n - W^{n-1} + dt^2 L_h W^n,  n = 1..Nt-1   (eq. explicitScheme)
  *   out = sum_{n=0}^{Nt} c_n W^n                             (eq. filterQuadrature)
  * Arrays hold active points; c has Nt+1 entries. */
-int og_filter_explicit(int dim, const long* n, const double* h, int order, long Nt, double dt,
+int og_filter_explicit(int dim, const long* n, const double* h, int order, const int* bc, long Nt, double dt,
                        const double* c, const double* v, double* out) {
     og_grid g;
-    if (og_init(&g, dim, n, h, order) || Nt < 1) return -1;
+    if (og_init(&g, dim, n, h, order, bc) || Nt < 1) return -1;
     size_t bytes = sizeof(double) * (size_t)g.npad;
     double* Wm = (double*)malloc(bytes); /* W^{n-1} */
     double* W0 = (double*)malloc(bytes); /* W^n     */
@@ -218,10 +240,10 @@ int og_filter_explicit(int dim, const long* n, const double* h, int order, long 
 int og_apply_M(int dim, const long* n, const double* h, int order, double a, const double* x,
                double* y) {
     og_grid g;
-    if (og_init(&g, dim, n, h, order)) return -1;
+    if (og_init(&g, dim, n, h, order, NULL)) return -1;
     double* L = (double*)malloc(sizeof(double) * (size_t)g.nact);
     if (!L) return -2;
-    og_apply_L(dim, n, h, order, x, L);
+    og_apply_L(dim, n, h, order, NULL, x, L);
     for (long m = 0; m < g.nact; ++m) y[m] = x[m] - a * L[m];
     free(L);
     return 0;
@@ -239,7 +261,7 @@ static double og_dot(long N, const double* x, const double* y) {
 int og_cg_solve_M(int dim, const long* n, const double* h, int order, double a, const double* b,
                   double* x, double tol, int maxit) {
     og_grid g;
-    if (og_init(&g, dim, n, h, order)) return -1;
+    if (og_init(&g, dim, n, h, order, NULL)) return -1;
     long N = g.nact;
     double* r = (double*)malloc(sizeof(double) * (size_t)N);
     double* p = (double*)malloc(sizeof(double) * (size_t)N);
@@ -292,7 +314,7 @@ done:
 int og_filter_implicit(int dim, const long* n, const double* h, int order, long Nt, double dt,
                        const double* c, const double* v, double* out, double tol) {
     og_grid g;
-    if (og_init(&g, dim, n, h, order) || Nt < 1) return -1;
+    if (og_init(&g, dim, n, h, order, NULL) || Nt < 1) return -1;
     long N = g.nact;
     size_t bytes = sizeof(double) * (size_t)N;
     double a = 0.5 * dt * dt;

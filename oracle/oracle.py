@@ -54,9 +54,10 @@ def _load():
             dp = ctypes.POINTER(ctypes.c_double)
             lp = ctypes.POINTER(ctypes.c_long)
             i, l, d = ctypes.c_int, ctypes.c_long, ctypes.c_double
-            lib.og_apply_L.argtypes = [i, lp, dp, i, dp, dp]
+            ip = ctypes.POINTER(ctypes.c_int)
+            lib.og_apply_L.argtypes = [i, lp, dp, i, ip, dp, dp]
             lib.og_apply_M.argtypes = [i, lp, dp, i, d, dp, dp]
-            lib.og_filter_explicit.argtypes = [i, lp, dp, i, l, d, dp, dp, dp]
+            lib.og_filter_explicit.argtypes = [i, lp, dp, i, ip, l, d, dp, dp, dp]
             lib.og_filter_implicit.argtypes = [i, lp, dp, i, l, d, dp, dp, dp, d]
             lib.og_cg_solve_M.argtypes = [i, lp, dp, i, d, dp, dp, d, i]
             lib.og_mg_solve.argtypes = [i, lp, dp, i, d, dp, dp, i, i, d, i, dp, i, dp]
@@ -71,27 +72,40 @@ def _dp(a):
 
 
 class Grid:
-    """Cartesian box with homogeneous Dirichlet conditions (eq. eigBVPdiscrete).
+    """Cartesian box (eq. eigBVPdiscrete) with homogeneous Dirichlet faces or
+    Neumann faces (the paper's symmetry-plane condition).
 
-    ``n`` = active (interior) points per axis, ``length`` = box side lengths,
-    h_i = length_i / (n_i + 1).  Vectors hold active points, x fastest
-    (Algorithm matVec; Note 1 of the Arnoldi section)."""
+    ``n`` = interior points per axis, ``length`` = box side lengths,
+    h_i = length_i / (n_i + 1); ``bc`` = None (all Dirichlet) or 2 dim face
+    kinds "D" / "N" in the order -x, +x, -y, +y[, -z, +z].  A Neumann face's
+    wall points are active, so axis i has ``nact[i]`` = n_i + (its Neumann
+    faces) active points.  Vectors hold active points, x fastest (Algorithm
+    matVec; Note 1 of the Arnoldi section)."""
 
-    def __init__(self, n, length, order):
+    def __init__(self, n, length, order, bc=None):
         self.dim = len(n)
         assert self.dim in (2, 3) and order in (2, 4)
         self.n = tuple(int(v) for v in n)
         self.length = tuple(float(v) for v in length)
         self.order = int(order)
+        self.bc = tuple("D" for _ in range(2 * self.dim)) if bc is None else tuple(bc)
+        assert len(self.bc) == 2 * self.dim and all(f in ("D", "N") for f in self.bc)
         self.h = tuple(L / (m + 1) for L, m in zip(self.length, self.n))
-        self.size = int(np.prod(self.n))
-        self._n3 = (ctypes.c_long * 3)(*(list(self.n) + [1] * (3 - self.dim)))
+        self.nact = tuple(m + (self.bc[2 * a] == "N") + (self.bc[2 * a + 1] == "N")
+                          for a, m in enumerate(self.n))
+        self.size = int(np.prod(self.nact))
+        self.neumann = "N" in self.bc
+        self._n3 = (ctypes.c_long * 3)(*(list(self.nact) + [1] * (3 - self.dim)))
         self._h3 = (ctypes.c_double * 3)(*(list(self.h) + [1.0] * (3 - self.dim)))
+        self._bc6 = (ctypes.c_int * 6)(*([int(f == "N") for f in self.bc] + [0] * (6 - 2 * self.dim)))
 
     @property
     def shape(self):
         """numpy shape of a grid function with x fastest."""
-        return tuple(reversed(self.n))
+        return tuple(reversed(self.nact))
+
+    def dirichlet_only(self):
+        assert not self.neumann, "this oracle routine takes Dirichlet boxes only"
 
 
 # ----------------------------------------------------------------------------
@@ -102,13 +116,14 @@ def apply_L(g: Grid, u):
     """L_h u, the order-p centred Laplacian with Dirichlet closure (eq. eigBVPdiscrete)."""
     u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
     out = np.empty_like(u)
-    rc = _load().og_apply_L(g.dim, g._n3, g._h3, g.order, _dp(u), _dp(out))
+    rc = _load().og_apply_L(g.dim, g._n3, g._h3, g.order, g._bc6, _dp(u), _dp(out))
     assert rc == 0
     return out
 
 
 def apply_M(g: Grid, a, x):
     """M x = (I - a L_h) x with a = dt^2/2 (eq. impMatrix)."""
+    g.dirichlet_only()
     x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
     out = np.empty_like(x)
     rc = _load().og_apply_M(g.dim, g._n3, g._h3, g.order, float(a), _dp(x), _dp(out))
@@ -118,6 +133,7 @@ def apply_M(g: Grid, a, x):
 
 def cg_solve_M(g: Grid, a, b, tol=1e-14, maxit=100000):
     """Solve M x = b by conjugate gradients (M symmetric positive definite, eq. impMatrix)."""
+    g.dirichlet_only()
     b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
     x = np.empty_like(b)
     it = _load().og_cg_solve_M(g.dim, g._n3, g._h3, g.order, float(a), _dp(b), _dp(x),
@@ -185,7 +201,7 @@ def filter_explicit(g: Grid, prm, v):
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
     c = np.ascontiguousarray(prm["c"], dtype=np.float64)
     out = np.empty_like(v)
-    rc = _load().og_filter_explicit(g.dim, g._n3, g._h3, g.order, int(prm["Nt"]),
+    rc = _load().og_filter_explicit(g.dim, g._n3, g._h3, g.order, g._bc6, int(prm["Nt"]),
                                     float(prm["dt"]), _dp(c), _dp(v), _dp(out))
     assert rc == 0
     return out
@@ -194,6 +210,7 @@ def filter_explicit(g: Grid, prm, v):
 def filter_implicit(g: Grid, prm, v, tol=1e-14):
     """S v with the implicit trapezoidal scheme, every M-solve done by CG to
     ``tol`` (eqs. implicitScheme, impMatrix, implicitStep1, filterQuadrature)."""
+    g.dirichlet_only()
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
     c = np.ascontiguousarray(prm["c"], dtype=np.float64)
     out = np.empty_like(v)
@@ -213,6 +230,7 @@ def filter_apply(g: Grid, prm, v, scheme="explicit"):
 
 def mode_indices(g: Grid):
     """All multi-indices k (1-based per axis) in vector order of the DST."""
+    g.dirichlet_only()
     axes = [np.arange(1, m + 1) for m in g.n]
     mesh = np.meshgrid(*axes, indexing="ij")
     return np.stack([m.reshape(-1) for m in mesh], axis=1)
@@ -234,6 +252,7 @@ def lambda2_closed_form(g: Grid, k):
 
 def sine_mode(g: Grid, k):
     """Tensor sine mode phi_k(x_i) = prod_a sin(k_a pi (i_a + 1) / (n_a + 1)), as an active vector."""
+    g.dirichlet_only()
     vecs = [np.sin(k[a] * math.pi * np.arange(1, g.n[a] + 1) / (g.n[a] + 1)) for a in range(g.dim)]
     out = vecs[0]
     for a in range(1, g.dim):
@@ -277,6 +296,7 @@ def beta_continuous(lam, omega, Tf):
 
 def dst(g: Grid, v):
     """Orthonormal DST-I over every axis: coefficients of v in the normalised sine modes."""
+    g.dirichlet_only()
     import scipy.fft
     return scipy.fft.dstn(np.asarray(v, dtype=np.float64).reshape(g.shape), type=1,
                           norm="ortho").reshape(-1)
@@ -290,6 +310,7 @@ def idst(g: Grid, vhat):
 
 def spectrum(g: Grid):
     """lambda_h^2 of every sine mode, in DST coefficient order (x fastest)."""
+    g.dirichlet_only()
     axes = [np.arange(1, m + 1) for m in reversed(g.n)]
     mesh = np.meshgrid(*axes, indexing="ij")   # slowest axis first
     k = np.stack([m.reshape(-1) for m in reversed(mesh)], axis=1)  # columns kx, ky, (kz)
@@ -299,14 +320,100 @@ def spectrum(g: Grid):
 def filter_closed_form(g: Grid, prm, v, power=1, scheme="explicit"):
     """S^power v on a box, computed in the sine basis: S is diagonal there with
     entries beta~_d(lambda_k) (Theorem 'Eigenvalues of the EigenWave operator',
-    discrete form eq. discreteBeta)."""
+    discrete form eq. discreteBeta).  Boxes with Neumann faces use the
+    tensor sine / cosine modes of ``axis_modes``."""
+    if g.neumann:
+        return modes_closed_form(g, v, lambda lam2: beta_tilde(np.sqrt(lam2), prm, scheme) ** power)
     lam2, _ = spectrum(g)
     b = beta_tilde(np.sqrt(lam2), prm, scheme)
     return idst(g, (b ** power) * dst(g, v))
 
 
+def axis_modes(g: Grid, a):
+    """Exact eigenvectors of L_h along axis a (Section 'discrete analysis':
+    the closure is a reflection about the wall point, so the modes of the
+    infinite grid that obey it are eigenvectors of the box), as the columns of
+    a matrix over the axis's active points, with their angles theta.  With
+    M = n_a + 1 and the vertex index j (walls at j = 0 and j = M):
+      D-D  sin(theta j), theta = k pi / M,         k = 1 .. M-1, j = 1 .. M-1
+      N-N  cos(theta j), theta = k pi / M,         k = 0 .. M,   j = 0 .. M
+      N-D  cos(theta j), theta = (k - 1/2) pi / M, k = 1 .. M,   j = 0 .. M-1
+      D-N  sin(theta j), theta = (k - 1/2) pi / M, k = 1 .. M,   j = 1 .. M
+    (odd about a Dirichlet wall, even about a Neumann wall)."""
+    lo, hi = g.bc[2 * a], g.bc[2 * a + 1]
+    M = g.n[a] + 1
+    if lo == "D" and hi == "D":
+        th, j, f = np.arange(1, M) * math.pi / M, np.arange(1, M), np.sin
+    elif lo == "N" and hi == "N":
+        th, j, f = np.arange(0, M + 1) * math.pi / M, np.arange(0, M + 1), np.cos
+    elif lo == "N":
+        th, j, f = (np.arange(1, M + 1) - 0.5) * math.pi / M, np.arange(0, M), np.cos
+    else:
+        th, j, f = (np.arange(1, M + 1) - 0.5) * math.pi / M, np.arange(1, M + 1), np.sin
+    return th, f(np.outer(j, th))
+
+
+def axis_symbol(g: Grid, a, theta):
+    """1D eigenvalue of -L_h along axis a for angle theta, s = sin^2(theta / 2):
+    order 2: 4 s / h^2; order 4: 4 (s + s^2 / 3) / h^2 (the symbol of
+    (-1, 16, -30, 16, -1) / 12)."""
+    s = np.sin(0.5 * np.asarray(theta)) ** 2
+    return (4.0 * s if g.order == 2 else 4.0 * (s + s * s / 3.0)) / (g.h[a] ** 2)
+
+
+def spectrum_modes(g: Grid):
+    """lambda_h^2 of every tensor mode of ``axis_modes`` (any faces), in mode
+    order with the x index fastest."""
+    lam2 = np.zeros(1)
+    for a in range(g.dim):
+        th, _ = axis_modes(g, a)
+        lam2 = np.add.outer(axis_symbol(g, a, th), lam2)   # new axis slowest
+    return lam2.reshape(-1)
+
+
+def modes_closed_form(g: Grid, v, fn):
+    """Apply the function fn(lambda^2) of L_h to v exactly: expand v in the
+    tensor modes of ``axis_modes`` (a solve per axis), scale each coefficient,
+    sum the modes back."""
+    mats = [axis_modes(g, a)[1] for a in range(g.dim)]
+    x = np.asarray(v, dtype=np.float64).reshape(g.shape)   # (z,) y, x
+    for a in range(g.dim):
+        ax = g.dim - 1 - a
+        x = np.moveaxis(np.tensordot(np.linalg.inv(mats[a]), x, axes=([1], [ax])), 0, ax)
+    x = x.reshape(-1) * fn(spectrum_modes(g))
+    x = x.reshape(g.shape)
+    for a in range(g.dim):
+        ax = g.dim - 1 - a
+        x = np.moveaxis(np.tensordot(mats[a], x, axes=([1], [ax])), 0, ax)
+    return x.reshape(-1)
+
+
+def tensor_mode(g: Grid, k):
+    """Tensor mode with 0-based mode indices k = (kx, ky[, kz]) of ``axis_modes``, as an active vector."""
+    out = axis_modes(g, 0)[1][:, k[0]]
+    for a in range(1, g.dim):
+        out = np.multiply.outer(axis_modes(g, a)[1][:, k[a]], out)
+    return np.ascontiguousarray(out.reshape(-1))
+
+
+def trapezoid_weights(g: Grid):
+    """Weights of the discrete L_2 inner product on the active points: the
+    trapezoid rule, 1/2 per Neumann wall coordinate (all 1 on Dirichlet
+    boxes, whose walls are not active).  L_h is symmetric in these weights."""
+    w = np.ones(1)
+    for a in range(g.dim):
+        wa = np.ones(g.nact[a])
+        if g.bc[2 * a] == "N":
+            wa[0] = 0.5
+        if g.bc[2 * a + 1] == "N":
+            wa[-1] = 0.5
+        w = np.multiply.outer(wa, w)
+    return w.reshape(-1)
+
+
 def implicit_solve_closed_form(g: Grid, a, b):
     """M^{-1} b on a box: divide each sine coefficient by 1 + a lambda^2 (eq. impMatrix)."""
+    g.dirichlet_only()
     lam2, _ = spectrum(g)
     return idst(g, dst(g, b) / (1.0 + a * lam2))
 
@@ -317,9 +424,11 @@ def implicit_solve_closed_form(g: Grid, a, b):
 
 def rayleigh_lambda(g: Grid, phi):
     """lambda from the unweighted Rayleigh quotient eq. simpleRayleighQuotient:
-    -lambda^2 = sum phi L phi / sum phi^2 over active points."""
+    -lambda^2 = sum phi L phi / sum phi^2 over active points; with Neumann
+    faces both sums carry the trapezoid weights (eq. discreteRayleighQuotient)."""
     phi = np.asarray(phi, dtype=np.float64).reshape(-1)
-    lam2 = -np.dot(phi, apply_L(g, phi)) / np.dot(phi, phi)
+    w = trapezoid_weights(g)
+    lam2 = -np.dot(w * phi, apply_L(g, phi)) / np.dot(w * phi, phi)
     return math.sqrt(max(lam2, 0.0))
 
 
@@ -355,6 +464,7 @@ def mg_solve(g: Grid, a, b, x0=None, nu1=2, nu2=2, wJ=0.8, ncycles=1, net=None):
     interpolation, CG on the coarsest level) is spelled out in ew_oracle_mg.c.
     ``net`` is None or an array (levels x NET_WEIGHTS) of learned-smoother
     weights for the finest levels.  Returns (x, residual 2-norm history)."""
+    g.dirichlet_only()
     b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64).reshape(-1)
     hist = np.zeros(ncycles + 1)
