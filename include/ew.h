@@ -25,7 +25,9 @@
  *  - All GPU work is issued on the caller's `stream`.  Calls return when the
  *    work is queued, except where the comment says the call synchronises.
  *  - Inner products are the unweighted Euclidean sums over active points
- *    (simple Rayleigh quotient, eq. simpleRayleighQuotient).
+ *    (simple Rayleigh quotient, eq. simpleRayleighQuotient) on boxes with
+ *    Dirichlet faces; with a Neumann face they carry the trapezoid weights
+ *    (the discrete L_2 inner product of eq. discreteRayleighQuotient).
  *  - Errors: every call returns an ew_status; on failure ew_last_error()
  *    returns a message for the calling thread.  No exception crosses the ABI.
  *    Device-side waits are bounded and report EW_ETIMEOUT.  A wave-solve
@@ -54,7 +56,7 @@ typedef enum {
     EW_EUNSUPPORTED = 7  /* valid request this build does not implement */
 } ew_status;
 
-typedef enum { EW_BC_DIRICHLET = 0, EW_BC_NEUMANN = 1 /* reserved, not implemented */ } ew_bc;
+typedef enum { EW_BC_DIRICHLET = 0, EW_BC_NEUMANN = 1 } ew_bc;
 typedef enum { EW_FP32 = 0, EW_FP64 = 1 } ew_prec;
 typedef enum { EW_EXPLICIT = 0, EW_IMPLICIT = 1 } ew_scheme;
 
@@ -63,14 +65,25 @@ typedef struct ew_grid ew_grid; /* opaque, library-owned */
 /* Create a Cartesian box grid (Section "Discrete approximations", eq.
  * eigBVPdiscrete, restricted to one Cartesian component grid).
  *   dim         2 or 3
- *   n_interior  active points per axis (n_interior[2] ignored in 2D), each >= 1
+ *   n_interior  interior points per axis (n_interior[2] ignored in 2D), each
+ *               >= 1: the vertices strictly between the two walls
  *   length      box side lengths; h_i = length_i / (n_i + 1)
  *   order       2: the 5/7-point Laplacian; 4: the fourth-order 9/13-point
- *               wide cross, closed at the wall by the odd reflection
- *               u_{-j} = -u_{j} (u = 0 and u_xx = 0 on the boundary; the
- *               paper's compatibility conditions are not spelled out)
- *   bc          six faces (-x, +x, -y, +y, -z, +z); only EW_BC_DIRICHLET is
- *               implemented (EW_EUNSUPPORTED otherwise); NULL = all Dirichlet
+ *               wide cross.  Both close at a wall by reflection (the paper's
+ *               compatibility conditions are not spelled out): odd at a
+ *               Dirichlet wall, u_{-j} = -u_{j} (u = 0 and u_xx = 0 there)
+ *   bc          six faces (-x, +x, -y, +y, -z, +z); NULL = all Dirichlet.
+ *               EW_BC_DIRICHLET: u = 0 on the wall, whose points are not
+ *               active.  EW_BC_NEUMANN: a symmetry plane (the paper's Neumann
+ *               condition, Section "Numerical results"): the wall points are
+ *               active and the points beyond the wall are the even reflection
+ *               u_{-j} = u_{j} (centred u_n = 0; order 4 also u_nnn = 0), so
+ *               an axis has n_i + (its Neumann faces) active points.  With a
+ *               Neumann face L_h is symmetric in the trapezoid-weighted sums
+ *               (weight 1/2 per wall coordinate), not in the plain ones;
+ *               ew_rayleigh and ew_arnoldi_eigs use those weights.  The
+ *               implicit scheme and the multigrid entry points take
+ *               Dirichlet boxes only (EW_EUNSUPPORTED otherwise)
  *   prec        field precision of every kernel run on this grid
  * The handle binds to the CUDA device current at creation (or, if none is
  * visible then, to the device current at its first GPU call); later calls
@@ -205,10 +218,11 @@ ew_status ew_apply_L(const ew_grid* grid, const void* u_dev, void* Lu_dev, int n
 
 /* Stage 2 of the EigenWave approach (Arnoldi section): for each of nvec
  * vectors phi, lambda = sqrt(-sum phi L phi / sum phi^2) (eq.
- * simpleRayleighQuotient) and eig-res = ||L phi + lambda^2 phi||_inf /
- * (lambda^2 ||phi||_inf) (accuracy metrics, Section "Numerical results").
- * Reductions run on the device in FP64.  Synchronises `stream`.
- * eig_res_host may be NULL. */
+ * simpleRayleighQuotient; on a box with a Neumann face both sums carry the
+ * trapezoid weights, eq. discreteRayleighQuotient) and eig-res =
+ * ||L phi + lambda^2 phi||_inf / (lambda^2 ||phi||_inf) (accuracy metrics,
+ * Section "Numerical results").  Reductions run on the device in FP64.
+ * Synchronises `stream`.  eig_res_host may be NULL. */
 ew_status ew_rayleigh(const ew_grid* grid, const void* phi_dev, int nvec, double* lambda_host,
                       double* eig_res_host, cudaStream_t stream);
 
@@ -275,7 +289,8 @@ typedef struct {
 
 /* lambda_host (n_wanted) receives lambda per pair in the order of descending
  * beta; vecs_dev (may be NULL) receives the FP64 eigenvectors, N x n_wanted
- * column-major, unit 2-norm.  start_dev (may be NULL) is an FP64 N x block
+ * column-major, unit 2-norm (with a Neumann face: unit trapezoid-weighted
+ * norm, the eigenvectors orthonormal in those weights).  start_dev (may be NULL) is an FP64 N x block
  * start block.  Allocates its own workspace (basis N x (krylov_dim + 2 block)
  * FP64) for the duration of the call and synchronises `stream`.  Returns
  * EW_ENOCONV (results still filled) when the budget ran out first,

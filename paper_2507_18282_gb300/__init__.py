@@ -16,7 +16,7 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (EW_EXPLICIT, EW_FP32, EW_FP64, EW_IMPLICIT, EWError, check, lib,
+from ._lib import (EW_BC_DIRICHLET, EW_BC_NEUMANN, EW_EXPLICIT, EW_FP32, EW_FP64, EW_IMPLICIT, EWError, check, lib,
                    ew_filter_info, ew_filter_params, ew_mg_params)
 
 __all__ = ["Grid", "EWError", "ew_grid_create", "ew_grid_destroy", "filter_params", "mg_params",
@@ -48,11 +48,19 @@ def _ptr(t, dtype, numel=None):
 
 
 class Grid:
-    """Owner of an ew_grid* handle (ew_grid_create / ew_grid_destroy)."""
+    """Owner of an ew_grid* handle (ew_grid_create / ew_grid_destroy).
 
-    def __init__(self, handle, dim, n, length, order, prec):
+    ``n_interior`` are the interior points per axis, ``bc`` the six face kinds
+    (EW_BC_DIRICHLET / EW_BC_NEUMANN), ``n`` the active points per axis (a
+    Neumann face's wall points are active) and ``size`` their product."""
+
+    def __init__(self, handle, dim, n_interior, length, order, prec, bc):
         self.handle = handle
-        self.dim, self.n, self.length, self.order, self.prec = dim, tuple(n), tuple(length), order, prec
+        self.dim, self.length, self.order, self.prec = dim, tuple(length), order, prec
+        self.n_interior = tuple(n_interior)
+        self.bc = tuple(bc)
+        self.n = tuple(m + int(bc[2 * a] == EW_BC_NEUMANN) + int(bc[2 * a + 1] == EW_BC_NEUMANN)
+                       for a, m in enumerate(self.n_interior))
         self.size = int(np.prod(self.n))
 
     @property
@@ -72,13 +80,23 @@ class Grid:
             pass
 
 
-def ew_grid_create(dim, n, length, order=2, prec="fp32"):
+def ew_grid_create(dim, n, length, order=2, prec="fp32", bc=None):
+    """``n``: interior points per axis; ``bc``: None (all Dirichlet) or 2 dim face
+    kinds (-x, +x, -y, +y[, -z, +z]), each "D" / "N" or EW_BC_DIRICHLET / EW_BC_NEUMANN."""
     p = {"fp32": EW_FP32, "fp64": EW_FP64, EW_FP32: EW_FP32, EW_FP64: EW_FP64}[prec]
+    kinds = {"D": EW_BC_DIRICHLET, "N": EW_BC_NEUMANN, EW_BC_DIRICHLET: EW_BC_DIRICHLET,
+             EW_BC_NEUMANN: EW_BC_NEUMANN}
+    faces = [EW_BC_DIRICHLET] * 6
+    if bc is not None:
+        if len(bc) != 2 * dim:
+            raise ValueError("bc needs %d face kinds" % (2 * dim))
+        faces[:2 * dim] = [kinds.get(f, f) for f in bc]
     n3 = (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
     l3 = (ctypes.c_double * 3)(*(list(length) + [1.0] * (3 - len(length))))
+    b6 = (ctypes.c_int * 6)(*faces)
     h = ctypes.c_void_p()
-    check(lib.ew_grid_create(int(dim), n3, l3, int(order), None, p, ctypes.byref(h)))
-    return Grid(h, dim, n[:dim], length[:dim], order, p)
+    check(lib.ew_grid_create(int(dim), n3, l3, int(order), b6, p, ctypes.byref(h)))
+    return Grid(h, dim, n[:dim], length[:dim], order, p, faces[:2 * dim])
 
 
 def ew_grid_destroy(grid: Grid):

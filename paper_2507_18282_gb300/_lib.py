@@ -20,6 +20,7 @@ EW_OK, EW_EINVAL, EW_ENOMEM, EW_ECUDA, EW_ENOCONV, EW_EBREAKDOWN, EW_ETIMEOUT, E
 STATUS_NAMES = ["EW_OK", "EW_EINVAL", "EW_ENOMEM", "EW_ECUDA", "EW_ENOCONV", "EW_EBREAKDOWN",
                 "EW_ETIMEOUT", "EW_EUNSUPPORTED"]
 EW_FP32, EW_FP64 = 0, 1
+EW_BC_DIRICHLET, EW_BC_NEUMANN = 0, 1
 EW_EXPLICIT, EW_IMPLICIT = 0, 1
 
 

@@ -15,7 +15,8 @@
 // k Ritz vectors and the residual block (Krylov-Schur form).
 //
 // Stage 2 (Arnoldi section): lambda from the Rayleigh quotient of L_h
-// (eq. simpleRayleighQuotient) and the eig-res metric.  With refine_fp64 on an
+// (eq. simpleRayleighQuotient; on grids with Neumann faces the weighted form
+// eq. discreteRayleighQuotient) and the eig-res metric.  With refine_fp64 on an
 // FP32 grid the result is refined in FP64: mixed-precision iterative
 // refinement of the invariant subspace (refine_ir) or a second Krylov-Schur
 // run with FP64 wave-solves.
@@ -138,6 +139,7 @@ struct KSRun {
     double* W = nullptr;     // N x b
     void* fin = nullptr;     // filter input (grid precision), N x b
     void* fout = nullptr;    // filter output
+    double* symtmp = nullptr;  // FP64 grids with Neumann faces: W^{-1/2} X, N x b
     double* part = nullptr;  // gram partials
     double* dC = nullptr;    // small device matrices
     // host
@@ -170,6 +172,8 @@ struct KSRun {
         if (g->prec == EW_FP32) {
             EW_TRY(alloc(&fin, es * (size_t)N * b));
             EW_TRY(alloc(&fout, es * (size_t)N * b));
+        } else if (g->geom.bc) {
+            EW_TRY(alloc((void**)&symtmp, sizeof(double) * (size_t)N * b));
         }
         int wmax = m + 3 * b;
         EW_TRY(alloc((void**)&part, sizeof(double) * gram_part_doubles(wmax, wmax)));
@@ -198,15 +202,28 @@ struct KSRun {
         return update(N, A, N, ma, Bin, N, mb, dC, alpha, beta, Out, N, st);
     }
 
-    // W = S X (b vectors)
+    // W = S X (b vectors).  On a grid with Neumann faces S is symmetric in the
+    // trapezoid-weighted sums only, so the run works with the similar operator
+    // W^{1/2} S W^{-1/2}, symmetric in the plain sums that the Gram kernels and
+    // the Rayleigh-Ritz step use (same eigenvalues; eigenvectors W^{1/2} phi).
     ew_status apply_S(const double* X) {
+        const bool sym = g->geom.bc != 0;
         if (g->prec == EW_FP32) {
-            EW_TRY((convert<double, float>(N * b, X, (float*)fin, st)));
+            const double* Xs = X;
+            if (sym) {  // W is free until the result lands in it
+                EW_TRY(launch_wsqrt<double>(g->geom, X, W, b, -1, st));
+                Xs = W;
+            }
+            EW_TRY((convert<double, float>(N * b, Xs, (float*)fin, st)));
             EW_TRY(filter_apply_any(g, p, plan, fin, fout, b, st));
             EW_TRY((convert<float, double>(N * b, (const float*)fout, W, st)));
+        } else if (sym) {
+            EW_TRY(launch_wsqrt<double>(g->geom, X, symtmp, b, -1, st));
+            EW_TRY(filter_apply_any(g, p, plan, symtmp, W, b, st));
         } else {
             EW_TRY(filter_apply_any(g, p, plan, X, W, b, st));
         }
+        if (sym) EW_TRY(launch_wsqrt<double>(g->geom, W, W, b, 1, st));
         wave_solves += b;
         return EW_OK;
     }
@@ -282,8 +299,12 @@ struct KSRun {
     }
 
     // start block: columns 0..b-1 of V, orthonormalised
-    ew_status start(const double* start_dev, uint64_t seed) {
-        if (start_dev)
+    // start_dev: a caller's block (grid variables) or, with sym_vars, one
+    // already in the variables of the symmetrised operator
+    ew_status start(const double* start_dev, uint64_t seed, bool sym_vars = false) {
+        if (start_dev && g->geom.bc && !sym_vars)
+            EW_TRY(launch_wsqrt<double>(g->geom, start_dev, V, b, 1, st));
+        else if (start_dev)
             EW_CUDA_TRY(cudaMemcpyAsync(V, start_dev, sizeof(double) * (size_t)N * b, cudaMemcpyDeviceToDevice, st));
         else
             EW_TRY(splitmix_uniform(N * b, seed, V, st));
@@ -458,8 +479,16 @@ static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, int p, int max_ou
     // Rayleigh-Ritz with L_h inside span[X] (separates pairs that S cannot),
     // rank by beta_d(lambda) of the filter, then eig-res of the wanted pairs:
     // all FP64 and no wave-solve, so it doubles as the stopping test
+    const bool sym = g64->geom.bc != 0;  // the vectors are W^{1/2} phi (see KSRun::apply_S)
+    double* Qfree = kr.V + (size_t)nw * N;  // columns nw .. 2 nw - 1, free outside an outer step's expansion
     auto lrr_check = [&](double* worst) -> ew_status {
-        EW_TRY(launch_apply_L<double>(g64->geom, kr.V, W64, nw, 1.0, kr.st));
+        if (sym) {  // W^{1/2} L_h W^{-1/2} X
+            EW_TRY(launch_wsqrt<double>(g64->geom, kr.V, Qfree, nw, -1, kr.st));
+            EW_TRY(launch_apply_L<double>(g64->geom, Qfree, W64, nw, 1.0, kr.st));
+            EW_TRY(launch_wsqrt<double>(g64->geom, W64, W64, nw, 1, kr.st));
+        } else {
+            EW_TRY(launch_apply_L<double>(g64->geom, kr.V, W64, nw, 1.0, kr.st));
+        }
         std::vector<double> G, Z, w;
         EW_TRY(kr.gram_host(kr.V, nw, W64, nw, G));
         for (int i = 0; i < nw; ++i)
@@ -485,7 +514,12 @@ static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, int p, int max_ou
         for (int c = 0; c < nw; ++c) sc[c] = scr[ord[c]];
         lam_out.resize(nwant);
         res_out.resize(nwant);
-        EW_TRY(rayleigh_any(g64, kr.V, nwant, lam_out.data(), res_out.data(), kr.st));
+        if (sym) {  // eig-res of phi = W^{-1/2} x in the grid variables
+            EW_TRY(launch_wsqrt<double>(g64->geom, kr.V, W64, nwant, -1, kr.st));
+            EW_TRY(rayleigh_any(g64, W64, nwant, lam_out.data(), res_out.data(), kr.st));
+        } else {
+            EW_TRY(rayleigh_any(g64, kr.V, nwant, lam_out.data(), res_out.data(), kr.st));
+        }
         *worst = *std::max_element(res_out.begin(), res_out.end());
         if (getenv("EW_KS_LOG")) fprintf(stderr, "[ew refine] eig-res of the wanted pairs %.3e\n", *worst);
         return EW_OK;
@@ -499,7 +533,14 @@ static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, int p, int max_ou
         // exact image of X in FP64: S X = X Theta + E
         for (int c0 = 0; c0 < nw; c0 += 16) {
             int nb = std::min(16, nw - c0);
-            EW_TRY(filter_apply_any(g64, ks.p, ks.plan, kr.V + (size_t)c0 * N, W64 + (size_t)c0 * N, nb, kr.st));
+            if (sym) {
+                EW_TRY(launch_wsqrt<double>(g64->geom, kr.V + (size_t)c0 * N, Qfree, nb, -1, kr.st));
+                EW_TRY(filter_apply_any(g64, ks.p, ks.plan, Qfree, W64 + (size_t)c0 * N, nb, kr.st));
+                EW_TRY(launch_wsqrt<double>(g64->geom, W64 + (size_t)c0 * N, W64 + (size_t)c0 * N, nb, 1, kr.st));
+            } else {
+                EW_TRY(filter_apply_any(g64, ks.p, ks.plan, kr.V + (size_t)c0 * N, W64 + (size_t)c0 * N, nb,
+                                        kr.st));
+            }
         }
         *ws64 += nw;
         std::vector<double> T1, T2;
@@ -570,8 +611,15 @@ static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, int p, int max_ou
 }
 
 static ew_status make_twin_fp64(const ew_grid* g, ew_grid** out) {
-    int64_t n[3] = {g->geom.n[0], g->geom.n[1], g->geom.n[2]};
-    return ew_grid_create(g->geom.dim, n, g->length, g->geom.order, nullptr, EW_FP64, out);
+    ew_bc bc[6];
+    int64_t n[3];
+    for (int a = 0; a < 3; ++a) {
+        const int lo = (g->geom.bc >> (2 * a)) & 1, hi = (g->geom.bc >> (2 * a + 1)) & 1;
+        bc[2 * a] = lo ? EW_BC_NEUMANN : EW_BC_DIRICHLET;
+        bc[2 * a + 1] = hi ? EW_BC_NEUMANN : EW_BC_DIRICHLET;
+        n[a] = g->geom.n[a] - (a < g->geom.dim ? lo + hi : 0);  // back to interior points
+    }
+    return ew_grid_create(g->geom.dim, n, g->length, g->geom.order, bc, EW_FP64, out);
 }
 
 }  // namespace ew
@@ -623,11 +671,21 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
     r.wave_solves = ks.wave_solves;
     r.restarts = ks.restarts;
     // stage 2 on the grid-precision result
+    // with Neumann faces the basis holds W^{1/2} phi (KSRun::apply_S): the
+    // quotients and eig-res are taken of phi, in the grid variables
+    const bool sym = g->geom.bc != 0;
+    double* phis = nullptr;
+    if (sym) EW_TRY(ks.alloc((void**)&phis, sizeof(double) * (size_t)ks.N * nw));
+    auto rq = [&](ew_grid* g64, const double* X, double* lam_h, double* res_h) -> ew_status {
+        if (!sym) return rayleigh_any(g64, X, nw, lam_h, res_h, st);
+        EW_TRY(launch_wsqrt<double>(g64->geom, X, phis, nw, -1, st));
+        return rayleigh_any(g64, phis, nw, lam_h, res_h, st);
+    };
     std::vector<double> lam1(nw), res1(nw);
     {
         ew_grid* g64 = nullptr;
         EW_TRY(make_twin_fp64(g, &g64));
-        ew_status s = rayleigh_any(g64, ks.V, nw, lam1.data(), res1.data(), st);
+        ew_status s = rq(g64, ks.V, lam1.data(), res1.data());
         ew_grid_destroy(g64);
         EW_TRY(s);
     }
@@ -680,11 +738,11 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
         ks2.max_ws = std::max(ks.max_ws / 2, 8 * nw);
         ks2.st = st;
         ew_status s = ks2.setup();
-        if (s == EW_OK) s = ks2.start(ks.V, 0);
+        if (s == EW_OK) s = ks2.start(ks.V, 0, true);
         int nconv2 = 0;
         std::vector<double> theta2;
         if (s == EW_OK) s = ks2.run(theta2, &nconv2);
-        if (s == EW_OK) s = rayleigh_any(g64, ks2.V, nw, lam.data(), res.data(), st);
+        if (s == EW_OK) s = rq(g64, ks2.V, lam.data(), res.data());
         if (s != EW_OK) {
             ew_grid_destroy(g64);
             return s;
@@ -710,9 +768,17 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
         r.lambda_rel_change[j] = lam[j] > 0 ? best / lam[j] : 0.0;
     }
     r.n_converged = nconv;
+    if (vecs_dev && sym) {
+        ew_status s = launch_wsqrt<double>(g->geom, final_vecs, vecs_dev, nw, -1, st);
+        if (s != EW_OK) {
+            if (g64) ew_grid_destroy(g64);
+            return s;
+        }
+    }
     if (vecs_dev) {
-        cudaError_t e = cudaMemcpyAsync(vecs_dev, final_vecs, sizeof(double) * (size_t)ks.N * nw,
-                                        cudaMemcpyDeviceToDevice, st);
+        cudaError_t e = sym ? cudaSuccess
+                            : cudaMemcpyAsync(vecs_dev, final_vecs, sizeof(double) * (size_t)ks.N * nw,
+                                              cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
             if (g64) ew_grid_destroy(g64);

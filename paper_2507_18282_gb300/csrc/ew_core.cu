@@ -262,11 +262,13 @@ ew_status ew_grid_create(int dim, const int64_t n_interior[3], const double leng
     if (dim != 2 && dim != 3) return set_error(EW_EINVAL, "dim must be 2 or 3");
     if (order != 2 && order != 4) return set_error(EW_EINVAL, "order must be 2 or 4");
     if (prec != EW_FP32 && prec != EW_FP64) return set_error(EW_EINVAL, "bad precision");
-    if (bc)
-        for (int f = 0; f < 2 * dim; ++f)
-            if (bc[f] != EW_BC_DIRICHLET)
-                return set_error(EW_EUNSUPPORTED, "only homogeneous Dirichlet boundaries are implemented");
     GridGeom geom;
+    geom.bc = 0;
+    if (bc)
+        for (int f = 0; f < 2 * dim; ++f) {
+            if (bc[f] != EW_BC_DIRICHLET && bc[f] != EW_BC_NEUMANN) return set_error(EW_EINVAL, "bad boundary kind");
+            if (bc[f] == EW_BC_NEUMANN) geom.bc |= 1 << f;
+        }
     geom.dim = dim;
     geom.order = order;
     geom.N = 1;
@@ -275,7 +277,8 @@ ew_status ew_grid_create(int dim, const int64_t n_interior[3], const double leng
             if (n_interior[a] < 1) return set_error(EW_EINVAL, "n_interior must be >= 1");
             if (n_interior[a] > (int64_t)1 << 30) return set_error(EW_EINVAL, "axis too long");
             if (!(length[a] > 0.0)) return set_error(EW_EINVAL, "length must be > 0");
-            geom.n[a] = n_interior[a];
+            // a Neumann face's wall point is active (a symmetry plane of the vertex grid)
+            geom.n[a] = n_interior[a] + ((geom.bc >> (2 * a)) & 1) + ((geom.bc >> (2 * a + 1)) & 1);
             geom.h[a] = length[a] / (double)(n_interior[a] + 1);
         } else {
             geom.n[a] = 1;
@@ -370,7 +373,8 @@ static ew_status rayleigh_t(ew_grid* g, const T* phi, int nvec, double* lam_host
                             cudaStream_t st) {
     const int64_t N = g->geom.N;
     // scratch: Lphi (nvec * N of T) in fields; reduction partials and results in reduce
-    EW_TRY(g->fields.reserve((size_t)nvec * N * sizeof(T)));
+    const bool weighted = g->geom.bc != 0;
+    EW_TRY(g->fields.reserve((weighted ? 3 : 1) * (size_t)nvec * N * sizeof(T)));
     size_t part = (size_t)2 * nvec * kReduceBlocks;
     EW_TRY(g->reduce.reserve((part + 6 * (size_t)nvec) * sizeof(double)));
     double* dpart = (double*)g->reduce.ptr;
@@ -380,8 +384,20 @@ static ew_status rayleigh_t(ew_grid* g, const T* phi, int nvec, double* lam_host
     double* dres = dlam2 + nvec;     // 2 * nvec: (resid, xinf)
     T* Lphi = (T*)g->fields.ptr;
     EW_TRY(launch_apply_L<T>(g->geom, phi, Lphi, nvec, 1.0, st));
-    EW_TRY(launch_dots<T>(phi, Lphi, N, nvec, dpart, dnum, st));
-    EW_TRY(launch_dots<T>(phi, phi, N, nvec, dpart, dden, st));
+    if (weighted) {
+        // Neumann faces: the sums of the quotient carry the trapezoid weights W
+        // (the discrete L_2 inner product, in which L_h is symmetric there):
+        // (W^{1/2} phi) . (W^{1/2} L phi) and |W^{1/2} phi|^2
+        T* wp = Lphi + (size_t)nvec * N;
+        T* wl = wp + (size_t)nvec * N;
+        EW_TRY(launch_wsqrt<T>(g->geom, phi, wp, nvec, 1, st));
+        EW_TRY(launch_wsqrt<T>(g->geom, Lphi, wl, nvec, 1, st));
+        EW_TRY(launch_dots<T>(wp, wl, N, nvec, dpart, dnum, st));
+        EW_TRY(launch_dots<T>(wp, wp, N, nvec, dpart, dden, st));
+    } else {
+        EW_TRY(launch_dots<T>(phi, Lphi, N, nvec, dpart, dnum, st));
+        EW_TRY(launch_dots<T>(phi, phi, N, nvec, dpart, dden, st));
+    }
     void* hp = nullptr;
     EW_TRY(pinned(g, sizeof(double) * 4 * (size_t)nvec, &hp));
     double* h = (double*)hp;

@@ -45,19 +45,24 @@ void fused_end(cudaEvent_t start, cudaStream_t st, int64_t points, int64_t cell_
 // order 2: c1 = scale / h^2, c2 = 0,          c0 = -2 sum c1
 // order 4: c1 = scale 16 / (12 h^2), c2 = -scale / (12 h^2), c0 = -scale 30/12 sum 1/h^2
 // ---------------------------------------------------------------------------
+// bc: the grid's face mask (bit 2a: lower face of axis a is a Neumann face,
+// bit 2a+1: its upper face), which decides how points beyond the box are
+// extended (ew_bc_dev.cuh)
 template <typename T>
 struct Stencil {
     T c0;
     T c1[3];
     T c2[3];
+    int bc;
 };
 
 struct GridGeom {
     int dim;
     int order;
-    int64_t n[3];  // active points per axis (n[2] = 1 in 2D)
+    int64_t n[3];  // active points per axis (n[2] = 1 in 2D): interior points plus Neumann wall points
     double h[3];
     int64_t N;     // active points
+    int bc = 0;    // face mask, as in Stencil
 };
 
 template <typename T>
@@ -174,6 +179,10 @@ ew_status launch_resid_inf(const T* Lx, const T* x, int64_t N, int nvec, const d
                            double* part, double* out_res, double* out_xinf, cudaStream_t st);
 template <typename T>
 ew_status launch_scale(T* x, int64_t N, int nvec, const double* s, cudaStream_t st);
+// out = W^{e/2} in (e = +1 / -1) for nvec vectors: W the trapezoid weights of
+// the active points (1/2 per Neumann wall coordinate); in == out allowed
+template <typename T>
+ew_status launch_wsqrt(const GridGeom& g, const T* in, T* out, int nvec, int e, cudaStream_t st);
 // y += alpha x (FP32)
 ew_status axpy_f(int64_t n, float alpha, const float* x, float* y, cudaStream_t st);
 // y = a * x + y with device scalar: y_j -= s_j * x_j

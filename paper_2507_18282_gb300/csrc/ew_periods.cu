@@ -14,9 +14,10 @@
 // factor e of residual reduction), and the cheapest N_p is returned.
 //
 // On the boxes of this library the discrete spectrum is known exactly: the
-// eigenvectors are tensor sine modes with lambda^2 = sum_a mu_a(k_a), mu_a the
-// 1D symbol of the stencil, (4/h^2) s (order 2) or (4/h^2)(s + s^2/3)
-// (order 4, odd-reflection closure), s = sin^2(k pi / (2 (n + 1))).  The
+// eigenvectors are tensor sine / cosine modes with lambda^2 = sum_a mu_a(k_a),
+// mu_a the 1D symbol of the stencil, (4/h^2) s (order 2) or
+// (4/h^2)(s + s^2/3) (order 4), s = sin^2(theta / 2), theta set per axis by
+// its faces (axis_symbol).  The
 // eigenvalues near omega are enumerated from these (per row of modes a binary
 // search of the monotone last-axis symbol), so no GPU is needed.
 #include <math.h>
@@ -31,15 +32,33 @@ namespace ew {
 
 double filter_beta(const FilterPlan& plan, ew_scheme scheme, double lam);
 
-// 1D symbol of axis a: mu(k), k = 1..n, increasing
+// 1D symbol of axis a over its modes, increasing.  With M = (interior points
+// + 1) the modes are sin(theta j) / cos(theta j) of the vertex index j, at
+//   theta = k pi / M, k = 1 .. M-1      (two Dirichlet faces: sine modes)
+//   theta = k pi / M, k = 0 .. M        (two Neumann faces: cosine modes)
+//   theta = (k - 1/2) pi / M, k = 1 .. M  (one of each)
+// and mu = (4/h^2) s (order 2) or (4/h^2)(s + s^2/3) (order 4), s = sin^2(theta/2).
 static std::vector<double> axis_symbol(const GridGeom& g, int a) {
-    const int64_t n = g.n[a];
+    const int code = (g.bc >> (2 * a)) & 3;
+    const int nn = (code & 1) + ((code >> 1) & 1);
+    const int64_t M = g.n[a] - nn + 1;
     const double h = g.h[a];
-    std::vector<double> mu((size_t)n);
-    for (int64_t k = 1; k <= n; ++k) {
-        const double s = sin(k * M_PI / (2.0 * (n + 1)));
-        const double s2 = s * s;
-        mu[(size_t)k - 1] = 4.0 / (h * h) * (g.order == 4 ? s2 + s2 * s2 / 3.0 : s2);
+    std::vector<double> mu;
+    mu.reserve((size_t)g.n[a]);
+    for (int64_t k = 0; k <= M; ++k) {
+        double th;
+        if (nn == 0) {
+            if (k < 1 || k > M - 1) continue;
+            th = k * M_PI / M;
+        } else if (nn == 2) {
+            th = k * M_PI / M;
+        } else {
+            if (k < 1) continue;
+            th = (k - 0.5) * M_PI / M;
+        }
+        const double sn = sin(0.5 * th);
+        const double s2 = sn * sn;
+        mu.push_back(4.0 / (h * h) * (g.order == 4 ? s2 + s2 * s2 / 3.0 : s2));
     }
     return mu;
 }
@@ -102,8 +121,8 @@ ew_status ew_choose_num_periods(const ew_grid* grid, const ew_filter_params* par
         // Widen a window [omega - w, omega + w] until the filter cannot put an
         // eigenvalue outside it among the top N_a + 1: beyond distance d of omega
         // (in time-corrected frequency) the filter's sum of cosines is bounded by
-        // 2 [1 / (T d) + 1 / (T omega) + 1 / (2 T lambda~_1)] (Dirichlet-kernel bound
-        // with a factor 2 of margin), compared with the window's beta_{N_a+1}.
+        // 2 [1 / (T d) + 1 / (T omega) + min(0.11, 1 / (2 T lambda~_1))] (Dirichlet-kernel
+        // bound with a factor 2 of margin), compared with the window's beta_{N_a+1}.
         const double T = plan.Tf;
         const ew_scheme sch = (ew_scheme)params->scheme;
         auto lt = [&](double l) {  // time-corrected frequency (monotone in l)
@@ -112,6 +131,9 @@ ew_status ew_choose_num_periods(const ew_grid* grid, const ew_filter_params* par
             return x >= 1.0 ? M_PI / plan.dt : 2.0 / plan.dt * asin(x);
         };
         const double lt1 = lt(sqrt(mu[0][0] + mu[1][0] + (g.dim == 3 ? mu[2][0] : 0.0)));
+        // the positive part of -sinc(x)/2 never exceeds 0.109 (sinc >= -0.2173),
+        // which bounds the third term also when lambda_1 = 0 (all faces Neumann)
+        const double t3 = lt1 > 0.0 ? std::min(0.11, 0.5 / (T * lt1)) : 0.11;
         std::vector<double> lam, beta;
         double w = 2.0 * plan.omega / np, cr = 1.0;
         for (;;) {
@@ -132,7 +154,7 @@ ew_status ew_choose_num_periods(const ew_grid* grid, const ew_filter_params* par
             if (all) break;
             const double d = std::min(plan.omega - (lo > 0.0 ? lt(lo) : 0.0), lt(hi) - plan.omega);
             const double env =
-                d > 0.0 ? 2.0 * (1.0 / (T * d) + 1.0 / (T * plan.omega) + 0.5 / (T * lt1)) : INFINITY;
+                d > 0.0 ? 2.0 * (1.0 / (T * d) + 1.0 / (T * plan.omega) + t3) : INFINITY;
             if (env < bn) break;
             w *= 2.0;
         }

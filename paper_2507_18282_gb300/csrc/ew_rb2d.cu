@@ -22,9 +22,9 @@
 // left/right edge and warps at the top/bottom edge see wrong neighbours, and
 // the wrong values spread R points per step, so after b <= B steps the tile
 // minus a rim of H = R B points is exact; that TX x TY interior is the owned
-// tile.  Points outside the box are staged with the odd extension of the grid
-// function (zero on the boundary lines, -u(mirror) beyond), which the linear
-// update keeps exact, as in the shared-memory form.  Every point performs the
+// tile.  Points outside the box are staged with the box closure's extension of
+// the grid function (ew_bc_dev.cuh), which the linear update keeps exact, as in
+// the shared-memory form.  Every point performs the
 // same operations in the same order as in the shared-memory form, so both
 // forms give bit-identical results.
 #include <stdio.h>
@@ -229,11 +229,12 @@ __device__ __forceinline__ void rb_issue(const float* __restrict__ Ain, const fl
     }
 }
 
-// Points of the staged region outside the box: the odd extension, read from
-// the staged mirror point (0 when the mirror is not staged: such a point is
-// farther than H from the owned tile and cannot reach it within B steps).
+// Points of the staged region outside the box: the box closure's extension
+// (ew_bc_dev.cuh), read from the staged mirror point (0 when the mirror is not
+// staged: such a point is farther than H from the owned tile and cannot reach
+// it within B steps).
 template <int CH, int CW, int PITCH, int NT>
-__device__ __forceinline__ void rb_fixup(int nx, int ny, int x0, int y0, float* stage, int tid) {
+__device__ __forceinline__ void rb_fixup(int nx, int ny, int bc, int x0, int y0, float* stage, int tid) {
     if (x0 >= 0 && y0 >= 0 && x0 + CW <= nx && y0 + CH <= ny) return;
     for (int q = tid; q < 2 * CH * CW; q += NT) {
         const int f = q / (CH * CW);
@@ -242,7 +243,7 @@ __device__ __forceinline__ void rb_fixup(int nx, int ny, int x0, int y0, float* 
         const int gx = x0 + c, gy = y0 + r;
         if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) continue;
         int sx = 1, sy = 1;
-        const int ix = odd_ext(gx, nx, sx), iy = odd_ext(gy, ny, sy);
+        const int ix = ext_axis<int>(gx, nx, axis_bc(bc, 0), sx), iy = ext_axis<int>(gy, ny, axis_bc(bc, 1), sy);
         float val = 0.f;
         if (ix >= 0 && iy >= 0) {
             const int mc = ix - x0, mr = iy - y0;
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(32 * NTY, 1)
             if (tid == 0) atomicExch(&g_rb2d_timeout, 1);
             return;
         }
-        rb_fixup<CH, CW, PITCH, NT>(nx, ny, x0, y0, stage, tid);
+        rb_fixup<CH, CW, PITCH, NT>(nx, ny, st.bc, x0, y0, stage, tid);
         __syncthreads();
         const int64_t vo = (int64_t)v * fstride, va = (int64_t)v * N;
 #pragma unroll

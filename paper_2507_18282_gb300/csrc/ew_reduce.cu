@@ -3,6 +3,7 @@
 // residuals).  Two passes with a fixed block count, so every result is
 // deterministic: pass 1 reduces a grid-stride slice per block (warp shuffles,
 // then shared memory), pass 2 sums the per-block partials in block order.
+#include "ew_bc_dev.cuh"
 #include "ew_internal.h"
 
 namespace ew {
@@ -175,5 +176,36 @@ template ew_status launch_diffnorm_sign<float>(const float*, const float*, int64
                                                double*, cudaStream_t);
 template ew_status launch_diffnorm_sign<double>(const double*, const double*, int64_t, const double*, double*,
                                                 double*, cudaStream_t);
+
+// out = W^{e/2} in (e = +1 or -1) for nvec vectors of N active points: W the
+// trapezoid weights of the box, 1/2 for each Neumann wall coordinate of a
+// point (so 1/4 on a 2D corner of two Neumann faces), 1 elsewhere.  On a grid
+// with Neumann faces L_h is symmetric in the W-weighted sums (the discrete
+// L_2 inner product), and W^{1/2} L_h W^{-1/2} in the plain ones.
+template <typename T>
+__global__ void k_wsqrt(const T* __restrict__ in, T* __restrict__ out, int64_t nx, int64_t ny, int64_t N,
+                        int64_t total, int bc, T f) {
+    const int bx = axis_bc(bc, 0), by = axis_bc(bc, 1), bz = axis_bc(bc, 2);
+    const int64_t nz = N / (nx * ny);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = q % N, i = r % nx, j = (r / nx) % ny, k = r / (nx * ny);
+        T s = T(1);
+        if (((bx & 1) && i == 0) || ((bx & 2) && i == nx - 1)) s *= f;
+        if (((by & 1) && j == 0) || ((by & 2) && j == ny - 1)) s *= f;
+        if (((bz & 1) && k == 0) || ((bz & 2) && k == nz - 1)) s *= f;
+        out[q] = s * in[q];
+    }
+}
+
+template <typename T>
+ew_status launch_wsqrt(const GridGeom& g, const T* in, T* out, int nvec, int e, cudaStream_t st) {
+    const T f = e > 0 ? T(0.70710678118654752440) : T(1.41421356237309504880);
+    k_wsqrt<T><<<kReduceBlocks * 4, 256, 0, st>>>(in, out, g.n[0], g.n[1], g.N, g.N * (int64_t)nvec, g.bc, f);
+    EW_CUDA_TRY(cudaGetLastError());
+    count_launch();
+    return EW_OK;
+}
+template ew_status launch_wsqrt<float>(const GridGeom&, const float*, float*, int, int, cudaStream_t);
+template ew_status launch_wsqrt<double>(const GridGeom&, const double*, double*, int, int, cudaStream_t);
 
 }  // namespace ew

@@ -19,9 +19,11 @@
 // 30 .. 300 of accuracy in the first form.
 //
 // Fields are stored in the active-point layout (x fastest, no padding): the
-// Dirichlet closure is applied on the fly.  A point one step outside the box
-// is a boundary point (value 0); for the fourth-order stencil the point two
-// steps outside is a ghost holding the odd reflection -u(mirror).
+// box closure is applied on the fly.  Beyond a Dirichlet face the point one
+// step outside is the wall (value 0) and the point two steps outside a ghost
+// holding the odd reflection -u(mirror); a Neumann face's wall point is
+// active and the points beyond it hold the even reflection u(mirror)
+// (ew_bc_dev.cuh).
 //
 // Kernels:
 //   k_first_step      : a3, writes D^1, W^1 and V_out = c_0 W^0 + c_1 W^1.
@@ -56,6 +58,7 @@ namespace ew {
 template <typename T>
 Stencil<T> make_stencil(const GridGeom& g, double scale) {
     Stencil<T> s;
+    s.bc = g.bc;
     double a1[3] = {0, 0, 0}, a2[3] = {0, 0, 0};
     double tot = 0.0;
     for (int a = 0; a < g.dim; ++a) {
@@ -154,21 +157,29 @@ __global__ void k_step_simple(int64_t nx, int64_t ny, int64_t nz, const T* __res
 // ---------------------------------------------------------------------------
 // whole wave-solve of a small 2D grid in one CTA
 // ---------------------------------------------------------------------------
-// ghost fix-up of a whole padded 2D grid (pitch PX, 2 ghost layers), order 4 only
+// boundary and ghost layers of a whole padded 2D grid (pitch PX, G = 2
+// layers on every side) from the box closure: Dirichlet walls 0, beyond them
+// the odd reflection, Neumann ghosts the even reflection.  The cross-shaped
+// stencils never read the corner blocks.
 template <typename T, int R>
-__device__ __forceinline__ void resident_fix(T* buf, int nx, int ny, int PX, int tid, int nthr) {
+__device__ __forceinline__ void resident_fix(T* buf, int nx, int ny, int PX, int bc, int tid, int nthr) {
     constexpr int G = 2;
-    if (R != 2) return;
-    for (int q = tid; q < 2 * ny + 2 * nx; q += nthr) {
-        if (q < 2 * ny) {
-            int y = q >> 1, side = q & 1;
-            int gx = side ? nx + 1 : -2, mx = side ? nx - 1 : 0;
-            buf[(y + G) * PX + gx + G] = -buf[(y + G) * PX + mx + G];
-        } else {
-            int r = q - 2 * ny;
-            int x = r >> 1, side = r & 1;
-            int gy = side ? ny + 1 : -2, my = side ? ny - 1 : 0;
-            buf[(gy + G) * PX + x + G] = -buf[(my + G) * PX + x + G];
+    if (R != 2 && bc == 0) return;  // order 2 with Dirichlet walls reads only the zero wall layer
+    const int bx = axis_bc(bc, 0), by = axis_bc(bc, 1);
+    for (int q = tid; q < 2 * G * (ny + nx); q += nthr) {
+        const int layer = q % G + 1, side = (q / G) & 1, r = q / (2 * G);
+        int sg = 1;
+        if (r < ny) {  // x-ghost of row r
+            const int gx = side ? nx - 1 + layer : -layer;
+            const int ix = ext_axis<int>(gx, nx, bx, sg);
+            const T v = ix < 0 ? T(0) : buf[(r + G) * PX + ix + G];
+            buf[(r + G) * PX + gx + G] = sg < 0 ? -v : v;
+        } else {  // y-ghost of column x
+            const int x = r - ny;
+            const int gy = side ? ny - 1 + layer : -layer;
+            const int iy = ext_axis<int>(gy, ny, by, sg);
+            const T v = iy < 0 ? T(0) : buf[(iy + G) * PX + x + G];
+            buf[(gy + G) * PX + x + G] = sg < 0 ? -v : v;
         }
     }
 }
@@ -189,7 +200,7 @@ __global__ void __launch_bounds__(1024)
     const int nthr = blockDim.x;
     const int tid = threadIdx.x;
 
-    auto fix = [&](T* buf) { resident_fix<T, R>(buf, nx, ny, PX, tid, nthr); };
+    auto fix = [&](T* buf) { resident_fix<T, R>(buf, nx, ny, PX, st.bc, tid, nthr); };
     auto lap = [&](const T* c, int p, const Stencil<T>& s) {
         T r = s.c0 * c[p] + s.c1[0] * (c[p - 1] + c[p + 1]) + s.c1[1] * (c[p - PX] + c[p + PX]);
         if (R == 2) r += s.c2[0] * (c[p - 2] + c[p + 2]) + s.c2[1] * (c[p - 2 * PX] + c[p + 2 * PX]);

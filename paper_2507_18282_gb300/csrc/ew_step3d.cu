@@ -7,38 +7,35 @@
 // A thread owns one (x, y) column of a z-chunk and marches up z, keeping the
 // column's z-neighbours of W^n in a register queue (one new load per point);
 // the x- and y-neighbours come through L1 from the neighbouring threads' rows.
-// The Dirichlet closure is folded into per-thread constants: since x and y
-// are fixed for the whole march, each x/y neighbour is "offset o with sign s"
-// (s = 1 inside, 0 on a boundary line, -1 for the odd-reflected ghost of the
-// fourth-order stencil), so the step has no branch.  Per point and step the
+// The box closure is folded into per-thread constants: since x and y are
+// fixed for the whole march, each x/y neighbour is "offset o with sign s"
+// (s = 1 inside or for an even-reflected Neumann ghost, 0 on a Dirichlet wall,
+// -1 for an odd-reflected ghost), so the step has no branch.  Per point and step the
 // kernel moves W^n, D^n and the filter sum in and D^{n+1}, W^{n+1} and the sum
 // out: 24 B (FP32), the unblocked algorithmic traffic.
 #include <algorithm>
 
+#include "ew_bc_dev.cuh"
 #include "ew_internal.h"
 
 namespace ew {
 
 constexpr int kS3X = 32, kS3Y = 8, kS3Z = 32;  // CTA = 32 x 8 columns, 32 planes per chunk
 
-// neighbour of coordinate i at offset d along an axis of length n: the
-// in-range coordinate holding its value and the sign (0: boundary line)
-__device__ __forceinline__ void nb(int i, int d, int n, int& j, int& s) {
-    int p = i + d;
+// neighbour of coordinate i at offset d along an axis of length n with face
+// code `code`: the in-range coordinate holding its value and the sign (0: a
+// Dirichlet wall, ew_bc_dev.cuh)
+__device__ __forceinline__ void nb(int i, int d, int n, int code, int& j, int& s) {
+    const int p = i + d;
     if (p >= 0 && p < n) {
         j = p;
         s = 1;
-    } else if (p == -1 || p == n) {
-        j = i;
-        s = 0;
-    } else {  // ghost two outside: odd reflection
-        j = p < 0 ? -2 - p : 2 * n - p;
-        s = -1;
-        if (j < 0 || j >= n) {  // axis shorter than the stencil: value 0
-            j = i;
-            s = 0;
-        }
+        return;
     }
+    int sg = 1;
+    const int q = ext_axis<int>(p, n, code, sg);
+    j = q < 0 ? i : q;
+    s = q < 0 ? 0 : sg;
 }
 
 template <typename T, int R>
@@ -51,28 +48,30 @@ __global__ void __launch_bounds__(kS3X* kS3Y)
     if (x >= nx || y >= ny || z0 >= nz) return;
     const int64_t plane = (int64_t)nx * ny;
     // x / y neighbour offsets (in elements, within a plane) and signs
+    const int bx = axis_bc(st.bc, 0), by = axis_bc(st.bc, 1), bz = axis_bc(st.bc, 2);
     int jx, sx_m1, sx_p1, sx_m2 = 0, sx_p2 = 0, sy_m1, sy_p1, sy_m2 = 0, sy_p2 = 0;
     int ox_m1, ox_p1, ox_m2 = 0, ox_p2 = 0, oy_m1, oy_p1, oy_m2 = 0, oy_p2 = 0;
-    nb(x, -1, nx, jx, sx_m1); ox_m1 = jx - x;
-    nb(x, 1, nx, jx, sx_p1); ox_p1 = jx - x;
-    nb(y, -1, ny, jx, sy_m1); oy_m1 = (jx - y) * nx;
-    nb(y, 1, ny, jx, sy_p1); oy_p1 = (jx - y) * nx;
+    nb(x, -1, nx, bx, jx, sx_m1); ox_m1 = jx - x;
+    nb(x, 1, nx, bx, jx, sx_p1); ox_p1 = jx - x;
+    nb(y, -1, ny, by, jx, sy_m1); oy_m1 = (jx - y) * nx;
+    nb(y, 1, ny, by, jx, sy_p1); oy_p1 = (jx - y) * nx;
     if (R == 2) {
-        nb(x, -2, nx, jx, sx_m2); ox_m2 = jx - x;
-        nb(x, 2, nx, jx, sx_p2); ox_p2 = jx - x;
-        nb(y, -2, ny, jx, sy_m2); oy_m2 = (jx - y) * nx;
-        nb(y, 2, ny, jx, sy_p2); oy_p2 = (jx - y) * nx;
+        nb(x, -2, nx, bx, jx, sx_m2); ox_m2 = jx - x;
+        nb(x, 2, nx, bx, jx, sx_p2); ox_p2 = jx - x;
+        nb(y, -2, ny, by, jx, sy_m2); oy_m2 = (jx - y) * nx;
+        nb(y, 2, ny, by, jx, sy_p2); oy_p2 = (jx - y) * nx;
     }
     const T fx_m1 = (T)sx_m1, fx_p1 = (T)sx_p1, fy_m1 = (T)sy_m1, fy_p1 = (T)sy_p1;
     const T fx_m2 = (T)sx_m2, fx_p2 = (T)sx_p2, fy_m2 = (T)sy_m2, fy_p2 = (T)sy_p2;
     const int64_t col = (int64_t)y * nx + x;
-    // z queue: q[0..2R] = W at z-R .. z+R (odd extension in z)
+    // z queue: q[0..2R] = W at z-R .. z+R (the closure's extension in z)
     auto zval = [&](int z) -> T {
         if (z >= 0 && z < nz) return W[(int64_t)z * plane + col];
-        if (z == -1 || z == nz) return T(0);
-        int m = z < 0 ? -2 - z : 2 * nz - z;
-        if (m < 0 || m >= nz) return T(0);
-        return -W[(int64_t)m * plane + col];
+        int sg = 1;
+        const int m = ext_axis<int>(z, nz, bz, sg);
+        if (m < 0) return T(0);
+        const T v = W[(int64_t)m * plane + col];
+        return sg < 0 ? -v : v;
     };
     T q[2 * R + 1];
 #pragma unroll

@@ -21,13 +21,15 @@
 // one barrier.
 //
 // Boundary conditions without branches.  Points of the staged region outside
-// the box are loaded with the odd extension of the grid function about the
-// boundary lines (zero on the boundary lines, -u(mirror) beyond them, applied
-// per axis and periodically with period 2(n+1) for tiny boxes).  The update
-// is linear and uses the same instruction sequence at every point, and IEEE
-// negation is exact, so the updated values stay the exact odd extension: the
-// boundary lines stay 0 and the ghosts (two outside, read by the 4th-order
-// stencil) stay -u(mirror), with no fix-up pass.
+// the box are loaded with the box closure's extension of the grid function
+// (ew_bc_dev.cuh: beyond a Dirichlet face zero on the wall and -u(mirror)
+// further out, beyond a Neumann face +u(mirror); applied per axis and
+// periodically for tiny boxes).  The update is linear, uses the same
+// instruction sequence at every point and forms every neighbour sum as a
+// (left + right) pair, which a mirror only swaps; IEEE addition is commutative
+// and negation exact, so the updated values stay the exact extension: the
+// Dirichlet walls stay 0 and the ghosts stay -u(mirror) or u(mirror), with no
+// fix-up pass.
 #include <stdio.h>
 #include <stdlib.h>
 

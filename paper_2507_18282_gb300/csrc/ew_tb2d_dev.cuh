@@ -3,34 +3,20 @@
 // and the single-grid kernel.  See ew_tb2d.cu for the design.
 #pragma once
 
+#include "ew_bc_dev.cuh"
 #include "ew_internal.h"
 
 namespace ew {
 
-// odd extension of an axis of length n about -1 and n: returns the interior
-// index holding the value and its sign, or -1 for a zero (boundary line).
-__device__ __forceinline__ int odd_ext(int p, int n, int& sign) {
-    const int P = 2 * (n + 1);
-    int q = (p + 1) % P;
-    if (q < 0) q += P;
-    q -= 1;  // q in [-1, 2n]
-    if (q == -1 || q == n) return -1;
-    if (q < n) {
-        sign = 1;
-        return q;
-    }
-    sign = -1;
-    return 2 * n - q;
-}
-
+// value of point (gx, gy) of the box closure's extension (ew_bc_dev.cuh)
 template <typename T>
-__device__ __forceinline__ T load_ext(const T* __restrict__ u, int gx, int gy, int nx, int ny) {
+__device__ __forceinline__ T load_ext(const T* __restrict__ u, int gx, int gy, int nx, int ny, int bc) {
     if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) return u[(int64_t)gy * nx + gx];
     int sx = 1, sy = 1;
-    int ix = odd_ext(gx, nx, sx);
-    int iy = odd_ext(gy, ny, sy);
+    const int ix = ext_axis<int>(gx, nx, axis_bc(bc, 0), sx);
+    const int iy = ext_axis<int>(gy, ny, axis_bc(bc, 1), sy);
     if (ix < 0 || iy < 0) return T(0);
-    T v = u[(int64_t)iy * nx + ix];
+    const T v = u[(int64_t)iy * nx + ix];
     return (sx * sy < 0) ? -v : v;
 }
 
@@ -111,8 +97,8 @@ __device__ __forceinline__ void tb2d_tile(int nx, int ny, const T* __restrict__ 
     const int y0 = tile_y * TY - H;
     const int tid = threadIdx.x;
 
-    // ---- stage D^n, W^n: asynchronous copies inside the box, the odd
-    //      extension outside it ---------------------------------------------
+    // ---- stage D^n, W^n: asynchronous copies inside the box, the box
+    //      closure's extension outside it -----------------------------------
     const bool inside = x0 >= 0 && y0 >= 0 && x0 + RX <= nx && y0 + RY <= ny;
     for (int q = tid; q < RX * RY; q += NT) {
         const int sy = q / RX, sx = q - sy * RX;
@@ -128,8 +114,8 @@ __device__ __forceinline__ void tb2d_tile(int nx, int ny, const T* __restrict__ 
                 cp_async4(sC + d, Bin + g);
             }
         } else {
-            sP[d] = load_ext(Ain, gx, gy, nx, ny);
-            sC[d] = load_ext(Bin, gx, gy, nx, ny);
+            sP[d] = load_ext(Ain, gx, gy, nx, ny, st.bc);
+            sC[d] = load_ext(Bin, gx, gy, nx, ny, st.bc);
         }
     }
 

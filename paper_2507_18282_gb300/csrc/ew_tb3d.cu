@@ -18,9 +18,10 @@
 // points.  Wrong x/y neighbours at the region's edge spread one point per
 // level and stay inside the rim.
 //
-// Points outside the box (x, y or z) are loaded with the odd extension of the
-// field (0 on the boundary planes, -u(mirror) beyond); the update keeps it
-// exact, as in the 2D kernel, so planes beyond the box are simply computed.
+// Points outside the box (x, y or z) are loaded with the box closure's
+// extension of the field (ew_bc_dev.cuh: 0 on a Dirichlet wall, -u(mirror)
+// beyond it, +u(mirror) beyond a Neumann face); the update keeps it exact, as
+// in the 2D kernel, so planes beyond the box are simply computed.
 // Global traffic per point and launch: W^n, D^n, acc in, W^{n+b}, D^{n+b}, acc
 // out (24 B in FP32), i.e. 24/b B per cell-step.
 #include <stdio.h>
@@ -31,27 +32,12 @@
 #include <mutex>
 #include <tuple>
 
+#include "ew_bc_dev.cuh"
 #include "ew_internal.h"
 
 namespace ew {
 
 constexpr int kT3 = 32;  // compute region edge (threads per axis)
-
-// odd extension of an axis of length n (period 2(n+1)): interior index and
-// sign, or -1 on a boundary line
-__device__ __forceinline__ int odd_ext3(int p, int n, int& sign) {
-    const int P = 2 * (n + 1);
-    int q = (p + 1) % P;
-    if (q < 0) q += P;
-    q -= 1;
-    if (q == -1 || q == n) return -1;
-    if (q < n) {
-        sign = 1;
-        return q;
-    }
-    sign = -1;
-    return 2 * n - q;
-}
 
 // FULL: b == B (every launch but the last of a wave-solve)
 template <typename T, int B, bool FULL>
@@ -72,9 +58,9 @@ __global__ void __launch_bounds__(kT3* kT3, 1)
     Dout += v * fstride;
     Wout += v * fstride;
     acc += v * N;
-    // x/y odd extension of this column: source column and sign (0: boundary line)
+    // x/y extension of this column: source column and sign (0: a Dirichlet wall)
     int sx = 1, sy = 1;
-    const int ix = odd_ext3(gx, nx, sx), iy = odd_ext3(gy, ny, sy);
+    const int ix = ext_axis<int>(gx, nx, axis_bc(st.bc, 0), sx), iy = ext_axis<int>(gy, ny, axis_bc(st.bc, 1), sy);
     const int sxy = (ix < 0 || iy < 0) ? 0 : sx * sy;
     const int64_t col = sxy ? (int64_t)iy * nx + ix : 0;
     const bool own = tx >= H && tx < H + TO && ty >= H && ty < H + TO && gx < nx && gy < ny;
@@ -85,14 +71,14 @@ __global__ void __launch_bounds__(kT3* kT3, 1)
     const int nxm = ty * kT3 + ixm, nxp = ty * kT3 + ixp, nym = iym * kT3 + tx, nyp = iyp * kT3 + tx;
 
     // plane z's inputs are loaded kPF steps ahead into slot z mod kPF, raw, with
-    // the odd-extension sign kept beside them (applying it at load time would
+    // the extension's sign kept beside them (applying it at load time would
     // make the warp wait for the load right away); the march is unrolled by kPF
     // so every slot is a fixed register
     constexpr int kPF = 4;
     T pw[kPF], pd[kPF], pa[kPF], sg[kPF];
     auto issue = [&](int z, T& w, T& d, T& a, T& sgn) {
         int szz = 1, iz = z;
-        if (z < 0 || z >= nz) iz = odd_ext3(z, nz, szz);
+        if (z < 0 || z >= nz) iz = ext_axis<int>(z, nz, axis_bc(st.bc, 2), szz);
         const bool live = sxy != 0 && iz >= 0 && z < nz + B;
         const int64_t gi = (int64_t)(live ? iz : 0) * plane + col;
         w = T(0);

@@ -90,3 +90,24 @@ def test_bad_arguments_are_refused(ew):
         assert e.value.status == 1
         assert ew.ew_last_error()
     g.close()
+
+
+def test_neumann_faces_add_active_wall_points(ew):
+    """A Neumann face's wall points are active: one more point per Neumann
+    face along its axis; h stays length / (n + 1), so the explicit step limit
+    (the largest eigenvalue is the same 4 sum 1/h^2, resp. 16/3 sum 1/h^2) and
+    the parameters of a wave-solve do not change."""
+    g = ew.ew_grid_create(3, (10, 12, 7), (1.0, 1.2, 0.7), order=4, bc=("N", "D", "N", "N", "D", "N"))
+    assert g.n == (11, 14, 8) and g.size == 11 * 14 * 8
+    gd = ew.ew_grid_create(3, (10, 12, 7), (1.0, 1.2, 0.7), order=4)
+    p = ew.filter_params(7.0, num_periods=3)
+    a, wa = ew.ew_filter_setup(g, p)
+    b, wb = ew.ew_filter_setup(gd, p)
+    assert a == b and np.array_equal(wa, wb)
+    g.close()
+    gd.close()
+    with pytest.raises(ValueError):
+        ew.ew_grid_create(2, (3, 3), (1, 1), bc=("N", "D"))
+    with pytest.raises(ew.EWError) as e:
+        ew.ew_grid_create(2, (3, 3), (1, 1), bc=(0, 1, 2, 0))   # 2 is not a boundary kind
+    assert e.value.status == 1

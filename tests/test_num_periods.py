@@ -25,9 +25,9 @@ def ew():
     return ew
 
 
-def _reference(n, L, order, omega, nw, na, spp, max_periods):
-    og = O.Grid(n, L, order)
-    lam = np.sqrt(O.spectrum(og)[0])
+def _reference(n, L, order, omega, nw, na, spp, max_periods, bc=None):
+    og = O.Grid(n, L, order, bc)
+    lam = np.sqrt(O.spectrum_modes(og) if og.neumann else O.spectrum(og)[0])
     crs, costs = [], []
     npv = 1
     while npv <= max_periods:
@@ -50,6 +50,24 @@ def test_matches_closed_form_spectrum(ew, n, L, order, omega, nw, na):
     info, _ = ew.ew_filter_setup(g, p)
     npv, cr = ew.ew_choose_num_periods(g, p, nw, na, max_periods=64)
     ref_cr, ref_np = _reference(n, L, order, omega, nw, na, info["steps_per_period"], 64)
+    np.testing.assert_allclose(cr, ref_cr, rtol=1e-8, atol=1e-12)
+    assert npv == ref_np
+    g.close()
+
+
+@pytest.mark.parametrize("n,L,order,omega,nw,na,bc", [
+    ((63, 95), (1.0, 1.5), 4, 40.0, 8, 24, ("N", "D", "D", "N")),
+    ((40, 30), (1.0, 0.7), 2, 3.0, 3, 10, ("N", "N", "N", "N")),   # lambda = 0 in the spectrum
+    ((15, 17, 19), (1.0, 1.1, 1.2), 2, 25.0, 6, 18, ("D", "N", "N", "D", "N", "N")),
+])
+def test_matches_closed_form_spectrum_with_neumann_faces(ew, n, L, order, omega, nw, na, bc):
+    """Neumann faces change the per-axis mode angles (tensor cosine / mixed
+    modes, one more active point per Neumann face)."""
+    g = ew.ew_grid_create(len(n), n, L, order=order, prec="fp32", bc=bc)
+    p = ew.filter_params(omega)
+    info, _ = ew.ew_filter_setup(g, p)
+    npv, cr = ew.ew_choose_num_periods(g, p, nw, na, max_periods=64)
+    ref_cr, ref_np = _reference(n, L, order, omega, nw, na, info["steps_per_period"], 64, bc)
     np.testing.assert_allclose(cr, ref_cr, rtol=1e-8, atol=1e-12)
     assert npv == ref_np
     g.close()
