@@ -124,7 +124,10 @@ typedef struct {
  *                     N_its > 4); the filter then peaks at lambda = omega for
  *                     the implicit scheme
  *   temporal_block    explicit steps fused per launch (0: library default)
- *   mg                implicit scheme only */
+ *   mg                implicit scheme only: each time step's system gets
+ *                     mg->max_cycles V-cycles, or, when mg->rtol > 0, cycles
+ *                     until ||b - M x||_2 <= rtol ||b||_2 (at most max_cycles;
+ *                     the test synchronises the stream once per cycle) */
 typedef struct {
     double omega;
     int num_periods;
@@ -368,6 +371,8 @@ typedef struct {
     double fused_ms;           /* summed event time of those launches */
     int64_t fused_cell_steps;  /* active points x time steps they advanced */
     int64_t fused_points;      /* active points they covered, summed over launches */
+    int64_t mg_cycles;         /* V-cycles run by the implicit time steps' multigrid solves */
+    int64_t mg_solves;         /* those solves (one per implicit time step) */
 } ew_profile;
 ew_status ew_profile_enable(int on);
 ew_status ew_profile_read(ew_profile* out_host);

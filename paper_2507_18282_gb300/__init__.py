@@ -269,11 +269,13 @@ def ew_profile_enable(on=True):
 
 
 def ew_profile_read():
-    """Totals since the last read: launches, fused_launches, fused_ms, fused_cell_steps, fused_points."""
+    """Totals since the last read: launches, fused_launches, fused_ms, fused_cell_steps, fused_points,
+    mg_cycles, mg_solves."""
     p = _lib.ew_profile()
     check(lib.ew_profile_read(ctypes.byref(p)))
     return dict(launches=p.launches, fused_launches=p.fused_launches, fused_ms=p.fused_ms,
-                fused_cell_steps=p.fused_cell_steps, fused_points=p.fused_points)
+                fused_cell_steps=p.fused_cell_steps, fused_points=p.fused_points, mg_cycles=p.mg_cycles,
+                mg_solves=p.mg_solves)
 
 
 def ew_last_error() -> str:

@@ -93,7 +93,7 @@ class ew_train_report(ctypes.Structure):
 class ew_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("fused_launches", ctypes.c_int64),
                 ("fused_ms", ctypes.c_double), ("fused_cell_steps", ctypes.c_int64),
-                ("fused_points", ctypes.c_int64)]
+                ("fused_points", ctypes.c_int64), ("mg_cycles", ctypes.c_int64), ("mg_solves", ctypes.c_int64)]
 
 
 _vp, _i, _d, _i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64

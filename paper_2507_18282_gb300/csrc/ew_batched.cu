@@ -46,13 +46,13 @@ struct BatchItem {
     int tile;
 };
 
-template <typename T, int R, int NWX, int NTY, int KY, int B, int MINB>
+template <typename T, int R, int NWX, int NTY, int KY, int B, int MINB, bool GEN>
 __global__ void __launch_bounds__(32 * NWX * NTY, MINB)
     k_step_tb2d_batched(const BatchDesc<T>* __restrict__ descs, const BatchItem* __restrict__ items, int nitems) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const BatchItem w = items[it];
         const BatchDesc<T> d = descs[w.desc];
-        tb2d_tile<T, R, NWX, NTY, KY, B>(d.nx, d.ny, d.Ain, d.Bin, d.Aout, d.Bout, d.acc, d.cw, d.b, d.st,
+        tb2d_tile<T, R, NWX, NTY, KY, B, GEN>(d.nx, d.ny, d.Ain, d.Bin, d.Aout, d.Bout, d.acc, d.cw, d.b, d.st,
                                          w.tile % d.ntx, w.tile / d.ntx);
         __syncthreads();  // the next item restages the shared buffers
     }
@@ -61,13 +61,15 @@ __global__ void __launch_bounds__(32 * NWX * NTY, MINB)
 struct BVariant {
     int B, TX, TY, threads;
     size_t smem;
-    void* fn;
+    void* fn;      // boxes with Dirichlet faces only
+    void* fn_gen;  // any faces (see ext2 in ew_tb2d_dev.cuh)
 };
 #define EW_BVAR(T, R, NWX, NTY, KY, B, MINB)                                                               \
     BVariant {                                                                                            \
         B, Tb2dShape<T, R, NWX, NTY, KY, B>::TX, Tb2dShape<T, R, NWX, NTY, KY, B>::TY,                    \
             Tb2dShape<T, R, NWX, NTY, KY, B>::NT, Tb2dShape<T, R, NWX, NTY, KY, B>::SMEM,                 \
-            (void*)k_step_tb2d_batched<T, R, NWX, NTY, KY, B, MINB>                                      \
+            (void*)k_step_tb2d_batched<T, R, NWX, NTY, KY, B, MINB, false>,                              \
+            (void*)k_step_tb2d_batched<T, R, NWX, NTY, KY, B, MINB, true>                                \
     }
 
 template <typename T, int R>
@@ -122,7 +124,7 @@ template <typename T>
 static ew_status run_rounds(const std::vector<BProblem>& P, const BVariant& var, T* base, int nsm, cudaStream_t cs,
                             std::vector<BatchDesc<T>>& hd, std::vector<BatchItem>& hi,
                             std::vector<std::pair<size_t, size_t>>& ranges, bool build_only, BatchDesc<T>* ddesc,
-                            BatchItem* ditem) {
+                            BatchItem* ditem, bool gen) {
     // ping-pong state per problem: fields 0..3, level L
     const int np = (int)P.size();
     std::vector<int> prv(np, 0), cur(np, 1), spa(np, 2), spb(np, 3);
@@ -167,7 +169,7 @@ static ew_status run_rounds(const std::vector<BProblem>& P, const BVariant& var,
         int nitems = (int)(ranges[r + 1].second - ranges[r].second);
         int grid = std::min(nitems, nsm);
         void* args[] = {(void*)&dd, (void*)&di, (void*)&nitems};
-        EW_CUDA_TRY(cudaLaunchKernel(var.fn, dim3(grid), dim3(var.threads), args, var.smem, cs));
+        EW_CUDA_TRY(cudaLaunchKernel(gen ? var.fn_gen : var.fn, dim3(grid), dim3(var.threads), args, var.smem, cs));
         count_launch();
     }
     return EW_OK;
@@ -181,9 +183,13 @@ static ew_status batched_t(std::vector<BProblem>& P, int order, cudaStream_t st)
     EW_CUDA_TRY(cudaGetDevice(&dev));
     int nsm = 0;
     EW_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    // any problem with a Neumann face: the general instantiation for the whole batch
+    bool gen = false;
+    for (const auto& p : P) gen = gen || p.g.bc != 0;
     for (const auto& v : vars) {
         if (!g_batch.occ.count(v.fn)) {
             EW_CUDA_TRY(cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
+            EW_CUDA_TRY(cudaFuncSetAttribute(v.fn_gen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
             int occ = 0;
             EW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn, v.threads, v.smem));
             g_batch.occ[v.fn] = std::max(occ, 1);
@@ -206,7 +212,7 @@ static ew_status batched_t(std::vector<BProblem>& P, int order, cudaStream_t st)
     std::vector<std::vector<std::pair<size_t, size_t>>> rgs(vars.size());
     size_t tbl = 0;
     for (size_t v = 0; v < vars.size(); ++v) {
-        EW_TRY(run_rounds<T>(P, vars[v], nullptr, nsm, nullptr, hds[v], his[v], rgs[v], true, nullptr, nullptr));
+        EW_TRY(run_rounds<T>(P, vars[v], nullptr, nsm, nullptr, hds[v], his[v], rgs[v], true, nullptr, nullptr, gen));
         tbl = std::max(tbl, hds[v].size() * sizeof(BatchDesc<T>) + 256 + his[v].size() * sizeof(BatchItem));
     }
     size_t need = field_bytes + tbl + 256;
@@ -255,7 +261,7 @@ static ew_status batched_t(std::vector<BProblem>& P, int order, cudaStream_t st)
         std::vector<BatchDesc<T>> hd;
         std::vector<BatchItem> hi;
         std::vector<std::pair<size_t, size_t>> rg;
-        EW_TRY(run_rounds<T>(P, vars[v], base, nsm, nullptr, hd, hi, rg, true, nullptr, nullptr));
+        EW_TRY(run_rounds<T>(P, vars[v], base, nsm, nullptr, hd, hi, rg, true, nullptr, nullptr, gen));
         BatchDesc<T>* ddesc = (BatchDesc<T>*)tdev;
         BatchItem* ditem = (BatchItem*)(tdev + ((hd.size() * sizeof(BatchDesc<T>) + 255) / 256) * 256);
         char* hstage = (char*)g_batch.host + field_bytes;
@@ -279,7 +285,7 @@ static ew_status batched_t(std::vector<BProblem>& P, int order, cudaStream_t st)
             std::vector<BatchDesc<T>> d2;
             std::vector<BatchItem> i2;
             std::vector<std::pair<size_t, size_t>> r2;
-            rs = run_rounds<T>(P, vars[v], base, nsm * grid_mult, s, d2, i2, r2, false, ddesc, ditem);
+            rs = run_rounds<T>(P, vars[v], base, nsm * grid_mult, s, d2, i2, r2, false, ddesc, ditem, gen);
         }
         g_profile_on = prof;
         cudaGraph_t graph = nullptr;

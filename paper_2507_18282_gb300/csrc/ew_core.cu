@@ -21,6 +21,7 @@ static thread_local std::string g_last_error;
 bool g_profile_on = false;
 static std::mutex g_prof_mu;
 static int64_t g_launches = 0, g_fused_launches = 0, g_fused_cells = 0, g_fused_points = 0;
+static int64_t g_mg_cycles = 0, g_mg_solves = 0;
 static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_fused_events;
 static std::vector<cudaEvent_t> g_event_pool;
 
@@ -28,6 +29,13 @@ void count_launch(int64_t k) {
     if (!g_profile_on) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_launches += k;
+}
+
+void count_mg_solve(int cycles) {
+    if (!g_profile_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_mg_cycles += cycles;
+    g_mg_solves += 1;
 }
 
 static cudaEvent_t pool_event() {
@@ -73,6 +81,7 @@ static void profile_reset_locked() {
     }
     g_fused_events.clear();
     g_launches = g_fused_launches = g_fused_cells = g_fused_points = 0;
+    g_mg_cycles = g_mg_solves = 0;
 }
 
 ew_status set_error(ew_status s, const std::string& msg) {
@@ -250,6 +259,8 @@ ew_status ew_profile_read(ew_profile* out) {
     out->fused_ms = ms;
     out->fused_cell_steps = g_fused_cells;
     out->fused_points = g_fused_points;
+    out->mg_cycles = g_mg_cycles;
+    out->mg_solves = g_mg_solves;
     profile_reset_locked();
     return EW_OK;
 }

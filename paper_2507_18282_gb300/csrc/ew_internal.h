@@ -35,6 +35,8 @@ void clear_error();
 // ---------------------------------------------------------------------------
 extern bool g_profile_on;
 void count_launch(int64_t k = 1);
+// one multigrid solve of an implicit time step that ran `cycles` V-cycles
+void count_mg_solve(int cycles);
 // brackets a fused-step launch: returns the start event (or null when off)
 cudaEvent_t fused_begin(cudaStream_t st);
 void fused_end(cudaEvent_t start, cudaStream_t st, int64_t points, int64_t cell_steps);
@@ -130,7 +132,8 @@ ew_status tb3d_advance(const GridGeom& g, const FilterPlan& plan, const T* cdev,
 
 // register-blocked persistent form of the 2D FP32 blocked step (ew_rb2d.cu)
 struct Rb2dDesc {
-    void* fn;
+    void* fn;      // boxes with Dirichlet faces only
+    void* fn_gen;  // any faces
     int nty, ky, B, TX, TY, threads;
     size_t smem;
 };

@@ -249,11 +249,13 @@ struct MGSolver {
     T* B[16];
     T* R[16];
     double a = 0.0;
+    ew_grid* gr = nullptr;
     const ew_mg_params* p = nullptr;
     double wJ = 0.8;
     cudaStream_t st = nullptr;
 
     ew_status setup(ew_grid* g, double a_, const ew_mg_params* params, cudaStream_t s) {
+        gr = g;
         a = a_;
         p = params;
         st = s;
@@ -369,6 +371,42 @@ struct MGSolver {
         for (int c = 0; c < ncyc; ++c) EW_TRY(vcycle(0));
         return EW_OK;
     }
+
+    // ||v||_2 of a finest-level vector (FP64 reduction, synchronises)
+    ew_status norm2(const T* v, double* out) {
+        EW_TRY(gr->reduce.reserve(sizeof(double) * (kReduceBlocks + 8)));
+        double* dpart = (double*)gr->reduce.ptr;
+        double* dres = dpart + kReduceBlocks;
+        EW_TRY(launch_dots<T>(v, v, lv[0].N, 1, dpart, dres, st));
+        double h = 0.0;
+        EW_CUDA_TRY(cudaMemcpyAsync(&h, dres, sizeof(double), cudaMemcpyDeviceToHost, st));
+        EW_CUDA_TRY(cudaStreamSynchronize(st));
+        *out = sqrt(h);
+        return EW_OK;
+    }
+
+    // V-cycles until ||B - M X||_2 <= rtol ||B||_2, tested after every cycle,
+    // or max_cycles; rtol <= 0 runs max_cycles without a test
+    ew_status solve(int max_cycles, double rtol, int* used) {
+        if (!(rtol > 0.0)) {
+            *used = max_cycles;
+            return cycles(max_cycles);
+        }
+        double bn = 0.0;
+        EW_TRY(norm2(B[0], &bn));
+        Stencil<T> sa = make_stencil<T>(lv[0], a);
+        int c = 0;
+        while (c < max_cycles) {
+            EW_TRY(vcycle(0));
+            ++c;
+            EW_MG_DISPATCH(k_mg_resid, lv[0], X[0], B[0], R[0], sa);
+            double rk = 0.0;
+            EW_TRY(norm2(R[0], &rk));
+            if (rk <= rtol * bn) break;
+        }
+        *used = c;
+        return EW_OK;
+    }
 };
 
 template <typename T>
@@ -408,7 +446,9 @@ static ew_status implicit_wave_solve_t(ew_grid* g, const FilterPlan& plan, const
         EW_CUDA_TRY(cudaMemcpyAsync(Wm, x, N * sizeof(T), cudaMemcpyDeviceToDevice, st));
         k_guess_rhs<T><<<blocks, 256, 0, st>>>(N, x, mg.B[0], mg.X[0], T(1));
         count_launch();
-        EW_TRY(mg.cycles(p->mg->max_cycles));
+        int used = 0;
+        EW_TRY(mg.solve(p->mg->max_cycles, p->mg->rtol, &used));
+        count_mg_solve(used);
         EW_CUDA_TRY(cudaMemcpyAsync(W0, mg.X[0], N * sizeof(T), cudaMemcpyDeviceToDevice, st));
         k_implicit_first<T><<<blocks, 256, 0, st>>>(N, Wm, W0, acc, (T)plan.c[0], (T)plan.c[1]);
         count_launch();
@@ -416,7 +456,8 @@ static ew_status implicit_wave_solve_t(ew_grid* g, const FilterPlan& plan, const
             // M y = 2 W^n from y = 2 W^n; W^{n+1} = y - W^{n-1} over W^{n-1}
             k_guess_rhs<T><<<blocks, 256, 0, st>>>(N, W0, mg.B[0], mg.X[0], T(2));
             count_launch();
-            EW_TRY(mg.cycles(p->mg->max_cycles));
+            EW_TRY(mg.solve(p->mg->max_cycles, p->mg->rtol, &used));
+            count_mg_solve(used);
             k_implicit_update<T><<<blocks, 256, 0, st>>>(N, mg.X[0], Wm, acc, (T)plan.c[(size_t)n + 1]);
             count_launch();
             std::swap(Wm, W0);

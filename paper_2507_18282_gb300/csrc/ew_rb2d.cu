@@ -233,7 +233,7 @@ __device__ __forceinline__ void rb_issue(const float* __restrict__ Ain, const fl
 // (ew_bc_dev.cuh), read from the staged mirror point (0 when the mirror is not
 // staged: such a point is farther than H from the owned tile and cannot reach
 // it within B steps).
-template <int CH, int CW, int PITCH, int NT>
+template <int CH, int CW, int PITCH, int NT, bool GEN>
 __device__ __forceinline__ void rb_fixup(int nx, int ny, int bc, int x0, int y0, float* stage, int tid) {
     if (x0 >= 0 && y0 >= 0 && x0 + CW <= nx && y0 + CH <= ny) return;
     for (int q = tid; q < 2 * CH * CW; q += NT) {
@@ -243,7 +243,7 @@ __device__ __forceinline__ void rb_fixup(int nx, int ny, int bc, int x0, int y0,
         const int gx = x0 + c, gy = y0 + r;
         if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) continue;
         int sx = 1, sy = 1;
-        const int ix = ext_axis<int>(gx, nx, axis_bc(bc, 0), sx), iy = ext_axis<int>(gy, ny, axis_bc(bc, 1), sy);
+        const int ix = ext2<GEN>(gx, nx, axis_bc(bc, 0), sx), iy = ext2<GEN>(gy, ny, axis_bc(bc, 1), sy);
         float val = 0.f;
         if (ix >= 0 && iy >= 0) {
             const int mc = ix - x0, mr = iy - y0;
@@ -278,7 +278,8 @@ __device__ __forceinline__ void rb_step(float4 (&Wn)[KY], float4 (&Dn)[KY], floa
 }
 
 // MINB is 1: the register file holds one CTA of 32 NTY threads per SM.
-template <int R, int NTY, int KY, int B>
+// GEN: any faces (false: Dirichlet faces only, see ext2 in ew_tb2d_dev.cuh).
+template <int R, int NTY, int KY, int B, bool GEN>
 __global__ void __launch_bounds__(32 * NTY, 1)
     k_step_rb2d(int nx, int ny, const float* __restrict__ Ain, const float* __restrict__ Bin, float* __restrict__ Aout,
                 float* __restrict__ Bout, float* __restrict__ acc, const float* __restrict__ cw, int b, Stencil<float> st,
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(32 * NTY, 1)
             if (tid == 0) atomicExch(&g_rb2d_timeout, 1);
             return;
         }
-        rb_fixup<CH, CW, PITCH, NT>(nx, ny, st.bc, x0, y0, stage, tid);
+        rb_fixup<CH, CW, PITCH, NT, GEN>(nx, ny, st.bc, x0, y0, stage, tid);
         __syncthreads();
         const int64_t vo = (int64_t)v * fstride, va = (int64_t)v * N;
 #pragma unroll
@@ -396,7 +397,8 @@ __global__ void __launch_bounds__(32 * NTY, 1)
 // ---------------------------------------------------------------------------
 #define EW_RB2D(R, NTY, KY, B)                                                                              \
     Rb2dDesc {                                                                                              \
-        (void*)k_step_rb2d<R, NTY, KY, B>, NTY, KY, B, Rb2dShape<R, NTY, KY, B>::TX,                         \
+        (void*)k_step_rb2d<R, NTY, KY, B, false>, (void*)k_step_rb2d<R, NTY, KY, B, true>, NTY, KY, B,       \
+            Rb2dShape<R, NTY, KY, B>::TX,                                                                   \
             Rb2dShape<R, NTY, KY, B>::TY, Rb2dShape<R, NTY, KY, B>::NT, Rb2dShape<R, NTY, KY, B>::SMEM        \
     }
 
@@ -417,13 +419,14 @@ ew_status rb2d_launch(const Rb2dDesc& d, const GridGeom& g, const float* Ain, co
     if (b < 1 || b > d.B) return set_error(EW_EINVAL, "register-blocked step: depth out of range");
     int dev = 0, nsm = 0;
     EW_CUDA_TRY(cudaGetDevice(&dev));
+    void* fn = g.bc ? d.fn_gen : d.fn;
     {
         static std::map<std::pair<void*, int>, int> sms;
         std::lock_guard<std::mutex> lk(g_rb_mu);
-        auto key = std::make_pair(d.fn, dev);
+        auto key = std::make_pair(fn, dev);
         auto it = sms.find(key);
         if (it == sms.end()) {
-            EW_CUDA_TRY(cudaFuncSetAttribute(d.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.smem));
+            EW_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.smem));
             EW_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
             sms[key] = nsm;
         } else {
@@ -443,7 +446,7 @@ ew_status rb2d_launch(const Rb2dDesc& d, const GridGeom& g, const float* Ain, co
                     (void*)&acc,  (void*)&cw, (void*)&b,   (void*)&s,       (void*)&fstride,       (void*)&tiles_x,
                     (void*)&tiles_per_vec, (void*)&ntiles, (void*)&stall_tx};
     cudaEvent_t ev = fused_begin(st);
-    EW_CUDA_TRY(cudaLaunchKernel(d.fn, dim3(grid), dim3(d.threads), args, d.smem, st));
+    EW_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(d.threads), args, d.smem, st));
     fused_end(ev, st, g.N * nvec, g.N * nvec * b);
     return EW_OK;
 }

@@ -50,7 +50,8 @@ struct Tb2dVariant {
     int nwx, nty, ky, B;
     int TX, TY, threads;
     size_t smem;
-    void* fn;  // kernel pointer
+    void* fn;  // kernel pointer, boxes with Dirichlet faces only
+    void* fn_gen;  // the same kernel for any faces (see ext2 in ew_tb2d_dev.cuh)
     int minb, fence;
     int kind = 0;  // 0: shared-memory form (k_step_tb2d), 1: register-blocked persistent form (k_step_rb2d)
     int rb = -1;   // index into rb2d_variants(R) for kind 1
@@ -60,7 +61,8 @@ struct Tb2dVariant {
 static std::vector<Tb2dVariant> with_rb2d(std::vector<Tb2dVariant> v, int R) {
     const auto& rb = rb2d_variants(R);
     for (size_t i = 0; i < rb.size(); ++i) {
-        Tb2dVariant x{1, rb[i].nty, rb[i].ky, rb[i].B, rb[i].TX, rb[i].TY, rb[i].threads, rb[i].smem, rb[i].fn, 1, 0};
+        Tb2dVariant x{1, rb[i].nty, rb[i].ky, rb[i].B, rb[i].TX, rb[i].TY, rb[i].threads, rb[i].smem, rb[i].fn,
+                      rb[i].fn_gen, 1, 0};
         x.kind = 1;
         x.rb = (int)i;
         v.push_back(x);
@@ -72,7 +74,8 @@ static std::vector<Tb2dVariant> with_rb2d(std::vector<Tb2dVariant> v, int R) {
     Tb2dVariant {                                                                                     \
         NWX, NTY, KY, B, Tb2dShape<T, R, NWX, NTY, KY, B>::TX, Tb2dShape<T, R, NWX, NTY, KY, B>::TY,  \
             Tb2dShape<T, R, NWX, NTY, KY, B>::NT, Tb2dShape<T, R, NWX, NTY, KY, B>::SMEM,              \
-            (void*)k_step_tb2d<T, R, NWX, NTY, KY, B, MINB>, MINB, 0                                   \
+            (void*)k_step_tb2d<T, R, NWX, NTY, KY, B, MINB, false>,                                   \
+            (void*)k_step_tb2d<T, R, NWX, NTY, KY, B, MINB, true>, MINB, 0                             \
     }
 
 template <typename T, int R>
@@ -140,15 +143,16 @@ static ew_status launch_variant(const Tb2dVariant& var, const GridGeom& g, const
                                s, nvec, fstride, st);
         return set_error(EW_EUNSUPPORTED, "register-blocked step is FP32 only");
     }
+    void* fn = g.bc ? var.fn_gen : var.fn;
     {
         // raise the dynamic shared-memory limit once per kernel and device
         static std::map<std::pair<void*, int>, bool> done;
         int dev = 0;
         EW_CUDA_TRY(cudaGetDevice(&dev));
         std::lock_guard<std::mutex> lk(g_attr_mu);
-        auto key = std::make_pair(var.fn, dev);
+        auto key = std::make_pair(fn, dev);
         if (!done.count(key)) {
-            EW_CUDA_TRY(cudaFuncSetAttribute(var.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)var.smem));
+            EW_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)var.smem));
             done[key] = true;
         }
     }
@@ -157,7 +161,7 @@ static ew_status launch_variant(const Tb2dVariant& var, const GridGeom& g, const
     void* args[] = {(void*)&nx, (void*)&ny, (void*)&Ain, (void*)&Bin, (void*)&Aout, (void*)&Bout,
                     (void*)&acc, (void*)&cw, (void*)&b, (void*)&s, (void*)&fstride};
     cudaEvent_t ev = fused_begin(st);
-    EW_CUDA_TRY(cudaLaunchKernel(var.fn, grid, dim3(var.threads), args, var.smem, st));
+    EW_CUDA_TRY(cudaLaunchKernel(fn, grid, dim3(var.threads), args, var.smem, st));
     fused_end(ev, st, g.N * nvec, g.N * nvec * b);
     return EW_OK;
 }
