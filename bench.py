@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--temporal-block", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--workload", choices=["rect2d", "cube3d", "batched", "implicit3d", "mg3d", "eigs2d"],
+    ap.add_argument("--workload", choices=["rect2d", "cube3d", "batched", "implicit3d", "mg3d", "eigs2d", "scaling2d",
+                                           "mgtol"],
                     default="rect2d",
                     help="rect2d is the headline line; the others print their own line")
     ap.add_argument("--eigs-arm", choices=["both", "fp32", "plain"], default="both",
@@ -371,6 +372,46 @@ def _timed(fn, steps, warmup, flush):
     return total
 
 
+def closed_form_all(n, length, order):
+    """Every discrete Dirichlet eigenvalue lambda of a 2D box (the tensor sine
+    modes; per-axis symbols as in closed_form_lambdas), flattened."""
+    import numpy as np
+    per_axis = []
+    for nd, ld in zip(n, length):
+        h = ld / (nd + 1)
+        k = np.arange(1, nd + 1, dtype=np.float64)
+        s = np.sin(k * np.pi * h / (2 * ld)) ** 2
+        per_axis.append(4.0 / h ** 2 * (s + s * s / 3.0 if order == 4 else s))
+    return np.sqrt(per_axis[0][:, None] + per_axis[1][None, :]).reshape(-1)
+
+
+def _nearest_rel_err(sorted_exact, x):
+    import numpy as np
+    i = int(np.searchsorted(sorted_exact, x))
+    cand = sorted_exact[max(i - 1, 0):i + 1]
+    return float(np.min(np.abs(cand - x)) / x)
+
+
+def _unit_square_mode_distance(m, lam, v):
+    """Max-norm distance of v (scaled to max |v| = 1) from the span of the
+    order-2 sine modes of the unit square (m x m interior points) of the
+    closed-form eigenvalue nearest lam (with its multiplicity): the
+    eigenvector error of a possibly multiple eigenvalue."""
+    import numpy as np
+    h = 1.0 / (m + 1)
+    k = np.arange(1, m + 1, dtype=np.float64)
+    mu = 4.0 / h ** 2 * np.sin(k * np.pi * h / 2) ** 2
+    lam_all = np.sqrt(mu[:, None] + mu[None, :])
+    near = lam_all.flat[np.argmin(np.abs(lam_all - lam))]
+    kk, ll = np.nonzero(np.abs(lam_all - near) < 1e-9 * near)
+    x = np.arange(1, m + 1) * h
+    B = np.stack([np.outer(np.sin(l_ * np.pi * x), np.sin(k_ * np.pi * x)).reshape(-1)
+                  for k_, l_ in zip(kk + 1, ll + 1)], axis=1)
+    v = v / np.max(np.abs(v))
+    c, *_ = np.linalg.lstsq(B, v, rcond=None)
+    return float(np.max(np.abs(v - B @ c)))
+
+
 def closed_form_lambdas(n, length, order, omega, count):
     """Discrete Dirichlet eigenvalues lambda = sqrt(sum_d lambda_d^2) of the
     box with n[d] active points per axis (h_d = length_d / (n_d + 1)): per axis
@@ -488,6 +529,70 @@ def run_extra(args):
         # fine-level sweep traffic: a Jacobi sweep reads x, b and writes x (12 B per point)
         line = dict(workload="mg3d_255_order4_fp32_vcycle22", unit="ms", plain=res["plain"], learned=res["learned"],
                     points=g.size, fine_sweep_bytes=12 * g.size)
+    elif w == "scaling2d":
+        # grid scaling of EigenWave with the implicit scheme and multigrid (the paper's
+        # unit-square runs: omega = 12, 16 eigenpairs, N_p = 1, 10 steps per period, every
+        # implicit system solved to a relative residual of 1e-10), h = 1/32 .. 1/2048,
+        # orders 2 and 4, FP64
+        rows = {}
+        for order in (2, 4):
+            rows[order], prev = [], None
+            for k in range(5, 12):
+                m = 2 ** k - 1
+                g = ew.ew_grid_create(2, (m, m), (1.0, 1.0), order=order, prec="fp64")
+                mg = ew.mg_params(pre=2, post=2, max_cycles=40, rtol=1e-10)
+                p = ew.filter_params(12.0, num_periods=1, steps_per_period=10, scheme="implicit", adjust_omega=True,
+                                     mg=mg)
+                e = ew.eigs_params(16, krylov_dim=48, block=2, tol=1e-10, seed=7, max_wave_solves=1000)
+                ew.ew_profile_enable(True)
+                torch.cuda.synchronize()
+                t0 = time.time()
+                lam, rep, st = ew.ew_arnoldi_eigs(g, p, e, allow_noconv=True)
+                torch.cuda.synchronize()
+                sec = time.time() - t0
+                prof = ew.ew_profile_read()
+                ew.ew_profile_enable(False)
+                g.close()
+                exact = np.sort(closed_form_all((m, m), (1.0, 1.0), order))
+                err = max(_nearest_rel_err(exact, x) for x in lam)
+                rows[order].append(dict(
+                    h="1/%d" % (m + 1), points=m * m, eigenpairs=int(rep["n_converged"]),
+                    wave_solves=int(rep["wave_solves"]),
+                    mg_cycles_per_solve=prof["mg_cycles"] / max(prof["mg_solves"], 1), seconds=sec,
+                    ratio=(sec / prev) if prev else None,
+                    us_per_point_and_wave_solve=sec / (rep["wave_solves"] * m * m) * 1e6,
+                    max_eig_res=float(rep["eig_res"][:16].max()), max_rel_err_vs_closed_form=err))
+                prev = sec
+        line = dict(workload="scaling2d_square_implicit_mg_omega12_16pairs", unit="s", rows=rows)
+    elif w == "mgtol":
+        # eigenpair accuracy against the tolerance of the implicit solves (the paper's
+        # square128 order-2 runs with the scaling parameters): tau = 1e-1 .. 1e-12
+        m, order = 127, 2
+        exact = np.sort(closed_form_all((m, m), (1.0, 1.0), order))
+        rows = []
+        # two series: the Krylov-Schur tolerance (Ritz residual of S) fixed at 1e-10, and tied to
+        # tau (max(1e-10, tau)): an inexact S cannot give Ritz residuals far below tau
+        for series, e10 in [(sr, e) for sr in ("fixed", "tied") for e in range(1, 13)]:
+            tau = 10.0 ** -e10
+            ks_tol = 1e-10 if series == "fixed" else max(1e-10, tau)
+            g = ew.ew_grid_create(2, (m, m), (1.0, 1.0), order=order, prec="fp64")
+            mg = ew.mg_params(pre=2, post=2, max_cycles=60, rtol=tau)
+            p = ew.filter_params(12.0, num_periods=1, steps_per_period=10, scheme="implicit", adjust_omega=True, mg=mg)
+            e = ew.eigs_params(16, krylov_dim=48, block=2, tol=ks_tol, seed=7, max_wave_solves=1000)
+            V = torch.zeros(g.size * 16, dtype=torch.float64, device="cuda")
+            ew.ew_profile_enable(True)
+            lam, rep, st = ew.ew_arnoldi_eigs(g, p, e, vecs=V, allow_noconv=True)
+            prof = ew.ew_profile_read()
+            ew.ew_profile_enable(False)
+            g.close()
+            X = V.cpu().numpy().reshape(16, -1)
+            rows.append(dict(
+                series=series, ks_tol=ks_tol, tau=tau, eigenpairs=int(rep["n_converged"]), wave_solves=int(rep["wave_solves"]),
+                mg_cycles_per_solve=prof["mg_cycles"] / max(prof["mg_solves"], 1),
+                max_rel_err_lambda=max(_nearest_rel_err(exact, x) for x in lam),
+                max_err_vector=max(_unit_square_mode_distance(m, x, X[j]) for j, x in enumerate(lam)),
+                max_eig_res=float(rep["eig_res"][:16].max())))
+        line = dict(workload="mgtol_square128_order2_implicit_omega12_16pairs", unit="relative error", rows=rows)
     elif w == "eigs2d":
         # time to the 8 eigenpairs nearest omega = 150 on the 2047 x 3071 order-4 rectangle:
         # FP32 wave-solves + FP64 refinement against FP64 wave-solves throughout
