@@ -70,3 +70,31 @@ def batched_boxes(seed: int, count: int = 64, n_min: int = 255, n_max: int = 204
 def learned_init(seed: int, scale: float = 0.05) -> np.ndarray:
     """Initial learned-smoother weights (2 x 8 x 27), uniform in [-scale, scale)."""
     return scale * uniform_pm1(seed, 2 * 8 * 27)
+
+
+# ----------------------------------------------------------------------------
+# curvilinear grids (vertex coordinates of a map x = G(r) from the unit square)
+# ----------------------------------------------------------------------------
+
+def mapped_vertices(n1: int, n2: int, kind: str = "square_warp", eps: float = 0.1, theta: float = 0.3,
+                    lx: float = 1.0, ly: float = 1.0) -> np.ndarray:
+    """Vertex coordinates, shape (n2 + 2, n1 + 2, 2) with the r1 index fastest,
+    boundary vertices included, of one of the test geometries:
+      square_warp   x = r + eps sin(pi r) cos(pi s), y = s + eps sin(pi s) cos(pi r):
+                    a smooth map of the unit square onto itself (boundary onto
+                    boundary), so the continuous eigenvalues are pi^2 (k^2 + l^2)
+      rotated_box   the box [0, lx] x [0, ly] rotated by theta about the origin
+    Geometry only: nothing here computes the method."""
+    r = np.linspace(0.0, 1.0, n1 + 2)
+    s = np.linspace(0.0, 1.0, n2 + 2)
+    R, S = np.meshgrid(r, s)  # (n2 + 2, n1 + 2), r fastest
+    if kind == "square_warp":
+        x = R + eps * np.sin(np.pi * R) * np.cos(np.pi * S)
+        y = S + eps * np.sin(np.pi * S) * np.cos(np.pi * R)
+    elif kind == "rotated_box":
+        c, sn = np.cos(theta), np.sin(theta)
+        x = c * lx * R - sn * ly * S
+        y = sn * lx * R + c * ly * S
+    else:
+        raise ValueError(kind)
+    return np.ascontiguousarray(np.stack([x, y], axis=-1))

@@ -353,3 +353,199 @@ out:
     free(y);
     return rc;
 }
+
+/* ------------------------------------------------------------------------
+ * Single curvilinear grid by the mapping method (Section "Discrete
+ * approximations": a smooth invertible map x = G(r) from the unit square,
+ * the equations transformed by the chain rule and discretised by
+ * conservative centred differences).  Two dimensions, second order, u = 0
+ * on the boundary vertices.
+ *
+ * xy: the (n1 + 2) x (n2 + 2) vertex coordinates, interleaved (x, y), the r1
+ * index fastest, boundary vertices included; the active points are the
+ * n1 x n2 interior vertices; dr = 1 / (n1 + 1), ds = 1 / (n2 + 1).
+ *
+ * In the r coordinates
+ *   J Lap u = d/dr (A11 u_r + A12 u_s) + d/ds (A12 u_r + A22 u_s),
+ *   J = x_r y_s - x_s y_r,  A11 = (x_s^2 + y_s^2) / J,
+ *   A22 = (x_r^2 + y_r^2) / J,  A12 = -(x_r x_s + y_r y_s) / J,
+ * with the metric derivatives at every vertex by centred differences
+ * (second-order one-sided ones on the boundary vertices).  At an active
+ * vertex (i, j), with A at half points the average of its two vertices:
+ *   J L u = [A11(i+1/2,j)(u(i+1,j) - u) - A11(i-1/2,j)(u - u(i-1,j))] / dr^2
+ *         + [A22(i,j+1/2)(u(i,j+1) - u) - A22(i,j-1/2)(u - u(i,j-1))] / ds^2
+ *         + [A12(i+1,j)(u(i+1,j+1) - u(i+1,j-1)) - A12(i-1,j)(u(i-1,j+1) - u(i-1,j-1))] / (4 dr ds)
+ *         + [A12(i,j+1)(u(i+1,j+1) - u(i-1,j+1)) - A12(i,j-1)(u(i+1,j-1) - u(i-1,j-1))] / (4 dr ds)
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+    long n1, n2;             /* active vertices per direction */
+    long p1, p2;             /* vertices per direction (n + 2) */
+    double dr, ds;
+    double *J, *A11, *A12, *A22; /* at every vertex, p1 x p2, r1 fastest */
+} om_grid;
+
+static void om_free(om_grid* m) {
+    free(m->J);
+    free(m->A11);
+    free(m->A12);
+    free(m->A22);
+}
+
+/* derivative along one direction of the vertex line f(t) = xy[(base + t s) 2 + c],
+ * t = 0 .. p-1, at t: centred inside, second-order one-sided at the ends */
+static double om_diff(const double* xy, long base, long s, long p, long t, int c, double d) {
+#define F(k) xy[2 * (base + (k) * s) + c]
+    if (t == 0) return (-3.0 * F(0) + 4.0 * F(1) - F(2)) / (2.0 * d);
+    if (t == p - 1) return (3.0 * F(p - 1) - 4.0 * F(p - 2) + F(p - 3)) / (2.0 * d);
+    return (F(t + 1) - F(t - 1)) / (2.0 * d);
+#undef F
+}
+
+static int om_init(om_grid* m, long n1, long n2, const double* xy) {
+    if (n1 < 1 || n2 < 1) return -1;
+    m->n1 = n1;
+    m->n2 = n2;
+    m->p1 = n1 + 2;
+    m->p2 = n2 + 2;
+    m->dr = 1.0 / (double)(n1 + 1);
+    m->ds = 1.0 / (double)(n2 + 1);
+    size_t np = (size_t)m->p1 * (size_t)m->p2;
+    m->J = (double*)malloc(sizeof(double) * np);
+    m->A11 = (double*)malloc(sizeof(double) * np);
+    m->A12 = (double*)malloc(sizeof(double) * np);
+    m->A22 = (double*)malloc(sizeof(double) * np);
+    if (!m->J || !m->A11 || !m->A12 || !m->A22) {
+        om_free(m);
+        return -2;
+    }
+    for (long j = 0; j < m->p2; ++j)
+        for (long i = 0; i < m->p1; ++i) {
+            long q = j * m->p1 + i;
+            double xr = om_diff(xy, j * m->p1, 1, m->p1, i, 0, m->dr);
+            double yr = om_diff(xy, j * m->p1, 1, m->p1, i, 1, m->dr);
+            double xs = om_diff(xy, i, m->p1, m->p2, j, 0, m->ds);
+            double ys = om_diff(xy, i, m->p1, m->p2, j, 1, m->ds);
+            double J = xr * ys - xs * yr;
+            if (!(J > 0.0)) {
+                om_free(m);
+                return -3; /* the map must preserve orientation */
+            }
+            m->J[q] = J;
+            m->A11[q] = (xs * xs + ys * ys) / J;
+            m->A22[q] = (xr * xr + yr * yr) / J;
+            m->A12[q] = -(xr * xs + yr * ys) / J;
+        }
+    return 0;
+}
+
+/* L u at active vertex (i, j) (vertex indices 1..n) of a vertex array U with
+ * zeros on the boundary vertices */
+static double om_lap_point(const om_grid* m, const double* U, long i, long j) {
+    long p = m->p1;
+#define V(a, b) U[(b) * p + (a)]
+#define A(arr, a, b) m->arr[(b) * p + (a)]
+    double u = V(i, j);
+    double a11p = 0.5 * (A(A11, i, j) + A(A11, i + 1, j)), a11m = 0.5 * (A(A11, i, j) + A(A11, i - 1, j));
+    double a22p = 0.5 * (A(A22, i, j) + A(A22, i, j + 1)), a22m = 0.5 * (A(A22, i, j) + A(A22, i, j - 1));
+    double t_rr = (a11p * (V(i + 1, j) - u) - a11m * (u - V(i - 1, j))) / (m->dr * m->dr);
+    double t_ss = (a22p * (V(i, j + 1) - u) - a22m * (u - V(i, j - 1))) / (m->ds * m->ds);
+    double t_rs = (A(A12, i + 1, j) * (V(i + 1, j + 1) - V(i + 1, j - 1)) -
+                   A(A12, i - 1, j) * (V(i - 1, j + 1) - V(i - 1, j - 1))) / (4.0 * m->dr * m->ds);
+    double t_sr = (A(A12, i, j + 1) * (V(i + 1, j + 1) - V(i - 1, j + 1)) -
+                   A(A12, i, j - 1) * (V(i + 1, j - 1) - V(i - 1, j - 1))) / (4.0 * m->dr * m->ds);
+    return (t_rr + t_ss + t_rs + t_sr) / A(J, i, j);
+#undef V
+#undef A
+}
+
+static void om_scatter(const om_grid* m, const double* v, double* U) {
+    memset(U, 0, sizeof(double) * (size_t)m->p1 * (size_t)m->p2);
+    long q = 0;
+    for (long j = 1; j <= m->n2; ++j)
+        for (long i = 1; i <= m->n1; ++i) U[j * m->p1 + i] = v[q++];
+}
+
+/* Lu = L u on active vectors of the mapped grid */
+int og_mapped_apply_L(long n1, long n2, const double* xy, const double* u, double* Lu) {
+    om_grid m;
+    int rc = om_init(&m, n1, n2, xy);
+    if (rc) return rc;
+    double* U = (double*)malloc(sizeof(double) * (size_t)m.p1 * (size_t)m.p2);
+    if (!U) {
+        om_free(&m);
+        return -2;
+    }
+    om_scatter(&m, u, U);
+    long q = 0;
+    for (long j = 1; j <= n2; ++j)
+        for (long i = 1; i <= n1; ++i) Lu[q++] = om_lap_point(&m, U, i, j);
+    free(U);
+    om_free(&m);
+    return 0;
+}
+
+/* J at the active vertices: the weights of the discrete L2 inner product in
+ * which the conservative L is symmetric */
+int og_mapped_jacobian(long n1, long n2, const double* xy, double* J) {
+    om_grid m;
+    int rc = om_init(&m, n1, n2, xy);
+    if (rc) return rc;
+    long q = 0;
+    for (long j = 1; j <= n2; ++j)
+        for (long i = 1; i <= n1; ++i) J[q++] = m.J[j * m.p1 + i];
+    om_free(&m);
+    return 0;
+}
+
+/* S v on the mapped grid with explicit leapfrog (eqs. explicitScheme,
+ * explicitStep1, filterQuadrature), as og_filter_explicit */
+int og_mapped_filter_explicit(long n1, long n2, const double* xy, long Nt, double dt, const double* c,
+                              const double* v, double* out) {
+    om_grid m;
+    int rc = om_init(&m, n1, n2, xy);
+    if (rc) return rc;
+    if (Nt < 1) {
+        om_free(&m);
+        return -1;
+    }
+    size_t np = (size_t)m.p1 * (size_t)m.p2;
+    double* Wm = (double*)malloc(sizeof(double) * np);
+    double* W0 = (double*)malloc(sizeof(double) * np);
+    double* Wp = (double*)malloc(sizeof(double) * np);
+    if (!Wm || !W0 || !Wp) {
+        free(Wm);
+        free(W0);
+        free(Wp);
+        om_free(&m);
+        return -2;
+    }
+    double dt2 = dt * dt;
+    om_scatter(&m, v, Wm);
+    memcpy(W0, Wm, sizeof(double) * np);
+    for (long j = 1; j <= n2; ++j)
+        for (long i = 1; i <= n1; ++i) W0[j * m.p1 + i] = Wm[j * m.p1 + i] + 0.5 * dt2 * om_lap_point(&m, Wm, i, j);
+    long q = 0;
+    for (long j = 1; j <= n2; ++j)
+        for (long i = 1; i <= n1; ++i, ++q) out[q] = c[0] * Wm[j * m.p1 + i] + c[1] * W0[j * m.p1 + i];
+    memset(Wp, 0, sizeof(double) * np);
+    for (long step = 1; step < Nt; ++step) {
+        for (long j = 1; j <= n2; ++j)
+            for (long i = 1; i <= n1; ++i) {
+                long k = j * m.p1 + i;
+                Wp[k] = 2.0 * W0[k] - Wm[k] + dt2 * om_lap_point(&m, W0, i, j);
+            }
+        q = 0;
+        for (long j = 1; j <= n2; ++j)
+            for (long i = 1; i <= n1; ++i, ++q) out[q] += c[step + 1] * Wp[j * m.p1 + i];
+        double* t = Wm;
+        Wm = W0;
+        W0 = Wp;
+        Wp = t;
+    }
+    free(Wm);
+    free(W0);
+    free(Wp);
+    om_free(&m);
+    return 0;
+}

@@ -61,6 +61,9 @@ def _load():
             lib.og_filter_implicit.argtypes = [i, lp, dp, i, l, d, dp, dp, dp, d]
             lib.og_cg_solve_M.argtypes = [i, lp, dp, i, d, dp, dp, d, i]
             lib.og_mg_solve.argtypes = [i, lp, dp, i, d, dp, dp, i, i, d, i, dp, i, dp]
+            lib.og_mapped_apply_L.argtypes = [l, l, dp, dp, dp]
+            lib.og_mapped_jacobian.argtypes = [l, l, dp, dp]
+            lib.og_mapped_filter_explicit.argtypes = [l, l, dp, l, d, dp, dp, dp]
             lib.og_conv_net_forward.argtypes = [lp, dp, dp, dp, dp]
             lib.og_conv_net_backward.argtypes = [lp, dp, dp, dp, dp, dp, dp]
             _lib = lib
@@ -416,6 +419,60 @@ def implicit_solve_closed_form(g: Grid, a, b):
     g.dirichlet_only()
     lam2, _ = spectrum(g)
     return idst(g, dst(g, b) / (1.0 + a * lam2))
+
+
+# ----------------------------------------------------------------------------
+# single curvilinear grid by the mapping method (ew_oracle.c: og_mapped_*)
+# ----------------------------------------------------------------------------
+
+class MappedGrid:
+    """A 2D curvilinear grid x = G(r) of the unit square (Section "Discrete
+    approximations", the mapping method), second order, u = 0 on the boundary
+    vertices.  ``n`` = (n1, n2) interior vertices; ``xy`` = vertex coordinates,
+    shape (n2 + 2, n1 + 2, 2), r1 index fastest.  Vectors hold the interior
+    vertices, r1 fastest."""
+
+    def __init__(self, n, xy):
+        self.n = (int(n[0]), int(n[1]))
+        self.xy = np.ascontiguousarray(xy, dtype=np.float64)
+        assert self.xy.shape == (self.n[1] + 2, self.n[0] + 2, 2)
+        self.size = self.n[0] * self.n[1]
+
+
+def mapped_apply_L(m: MappedGrid, u):
+    """L u in the conservative form of the transformed Laplacian (ew_oracle.c)."""
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+    out = np.empty_like(u)
+    rc = _load().og_mapped_apply_L(m.n[0], m.n[1], _dp(m.xy), _dp(u), _dp(out))
+    assert rc == 0, rc
+    return out
+
+
+def mapped_jacobian(m: MappedGrid):
+    """J = det(dx/dr) at the active vertices: the weights in which L is symmetric."""
+    out = np.empty(m.size)
+    rc = _load().og_mapped_jacobian(m.n[0], m.n[1], _dp(m.xy), _dp(out))
+    assert rc == 0, rc
+    return out
+
+
+def mapped_filter_explicit(m: MappedGrid, prm, v):
+    """S v on the mapped grid with explicit leapfrog (eqs. explicitScheme, explicitStep1, filterQuadrature)."""
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+    c = np.ascontiguousarray(prm["c"], dtype=np.float64)
+    out = np.empty_like(v)
+    rc = _load().og_mapped_filter_explicit(m.n[0], m.n[1], _dp(m.xy), int(prm["Nt"]), float(prm["dt"]),
+                                           _dp(c), _dp(v), _dp(out))
+    assert rc == 0, rc
+    return out
+
+
+def mapped_rayleigh_lambda(m: MappedGrid, phi):
+    """lambda from the Rayleigh quotient in the J-weighted sums (eq. discreteRayleighQuotient)."""
+    phi = np.asarray(phi, dtype=np.float64).reshape(-1)
+    w = mapped_jacobian(m)
+    lam2 = -np.dot(w * phi, mapped_apply_L(m, phi)) / np.dot(w * phi, phi)
+    return math.sqrt(max(lam2, 0.0))
 
 
 # ----------------------------------------------------------------------------
