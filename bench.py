@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--workload", choices=["rect2d", "cube3d", "batched", "implicit3d", "mg3d", "eigs2d", "scaling2d",
-                                           "mgtol"],
+                                           "mgtol", "mapped2d"],
                     default="rect2d",
                     help="rect2d is the headline line; the others print their own line")
     ap.add_argument("--eigs-arm", choices=["both", "fp32", "plain"], default="both",
@@ -529,6 +529,34 @@ def run_extra(args):
         # fine-level sweep traffic: a Jacobi sweep reads x, b and writes x (12 B per point)
         line = dict(workload="mg3d_255_order4_fp32_vcycle22", unit="ms", plain=res["plain"], learned=res["learned"],
                     points=g.size, fine_sweep_bytes=12 * g.size)
+    elif w == "mapped2d":
+        # one explicit wave-solve on a 2047 x 2047 curvilinear grid (the unit square warped onto
+        # itself, the mapping method), FP32, omega = 150, one period: the 9-point kernel with
+        # per-point couplings, one step per launch
+        n = (2047, 2047)
+        xy = ew_inputs.mapped_vertices(*n, "square_warp", eps=0.1)
+        g = ew.ew_grid_create_mapped(n, xy, prec="fp32")
+        p = ew.filter_params(150.0, num_periods=1)
+        info, _ = ew.ew_filter_setup(g, p)
+        v = torch.tensor(ew_inputs.uniform_pm1(ew_inputs.BASE_SEED + 6, g.size), dtype=torch.float32, device="cuda")
+        o = torch.empty_like(v)
+        ew.ew_profile_enable(True)
+        ms = _timed(lambda: ew.ew_filter_apply(g, p, v, o), args.steps, args.warmup, flush)
+        prof = ew.ew_profile_read()
+        ew.ew_profile_enable(False)
+        g.close()
+        cells = g.size * info["Nt"] * args.steps
+        launches = max(prof["fused_launches"], 1)
+        mean = prof["fused_ms"] / launches
+        # per point and step: W^n, D^n, acc, the five couplings and 1/J in; D, W^{n+1}, acc out
+        bytes_launch = 48 * prof["fused_points"] / launches
+        line = dict(workload="mapped2d_2047x2047_warped_square_order2_fp32_explicit", metric=METRIC, unit=UNIT,
+                    value=cells / (ms / 1e3) / 1e9, ms_per_step=ms / args.steps, time_steps_per_step=info["Nt"],
+                    steps_per_period=info["steps_per_period"],
+                    roofline=dict(bound="hbm", kernel="k_mapped_step<float>", bytes_per_launch=bytes_launch,
+                                  achieved=bytes_launch / (mean / 1e3) / 1e9, peak=pk["hbm_gbs"], unit="GB/s",
+                                  frac=bytes_launch / (mean / 1e3) / 1e9 / pk["hbm_gbs"], peak_source=pk_kind,
+                                  mean_launch_ms=mean))
     elif w == "scaling2d":
         # grid scaling of EigenWave with the implicit scheme and multigrid (the paper's
         # unit-square runs: omega = 12, 16 eigenpairs, N_p = 1, 10 steps per period, every

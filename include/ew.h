@@ -93,6 +93,34 @@ ew_status ew_grid_create(int dim, const int64_t n_interior[3], const double leng
                          const ew_bc bc[6], ew_prec prec, ew_grid** out);
 void ew_grid_destroy(ew_grid* grid);
 
+/* Create a single curvilinear grid by the mapping method (Section "Discrete
+ * approximations": a smooth invertible map x = G(r) from the unit square, the
+ * equations transformed by the chain rule and discretised by conservative
+ * centred differences).  Two dimensions, second order, u = 0 on every
+ * boundary vertex.
+ *   n_interior  interior vertices per direction (each >= 1); the active points
+ *               and the vector layout are those of a 2D box with these counts
+ *   xy_host     the (n1 + 2) x (n2 + 2) vertex coordinates, interleaved
+ *               (x, y), r1 index fastest, boundary vertices included (host
+ *               memory, read during the call and kept for the grid's life)
+ *   prec        field precision
+ * The operator: J L u = d_r(A11 u_r + A12 u_s) + d_s(A12 u_r + A22 u_s) with
+ * J = x_r y_s - x_s y_r, A11 = (x_s^2 + y_s^2)/J, A22 = (x_r^2 + y_r^2)/J,
+ * A12 = -(x_r x_s + y_r y_s)/J from centred differences of the vertex
+ * coordinates (second-order one-sided ones on the boundary vertices); the
+ * diagonal fluxes at half points (A averaged over two vertices), the cross
+ * fluxes centred: a 9-point stencil, symmetric in the J-weighted sums, which
+ * ew_rayleigh and ew_arnoldi_eigs use (its eigenvectors come back orthonormal
+ * in those weights).  The explicit step limit comes from a Gershgorin bound
+ * of rho(-L).  EW_EINVAL if J <= 0 at some vertex.  Like ew_grid_create it
+ * needs no GPU; the couplings are copied to the device on first use.
+ * ew_filter_apply (explicit scheme, one step per launch; temporal_block is
+ * ignored), ew_filter_apply_batched, ew_apply_L, ew_rayleigh,
+ * ew_power_iteration and ew_arnoldi_eigs accept such grids; the implicit
+ * scheme, multigrid, ew_filter_apply_noalloc and ew_choose_num_periods return
+ * EW_EUNSUPPORTED. */
+ew_status ew_grid_create_mapped(const int64_t n_interior[2], const double* xy_host, ew_prec prec, ew_grid** out);
+
 /* Multigrid options for the implicit systems M x = b, M = I - (dt^2/2) L_h
  * (eq. impMatrix).  The cycle: damped Jacobi (weight jacobi_weight, constant
  * interior diagonal) or the learned smoother on the finest `learned_levels`

@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import (EW_BC_DIRICHLET, EW_BC_NEUMANN, EW_EXPLICIT, EW_FP32, EW_FP64, EW_IMPLICIT, EWError, check, lib,
                    ew_filter_info, ew_filter_params, ew_mg_params)
 
-__all__ = ["Grid", "EWError", "ew_grid_create", "ew_grid_destroy", "filter_params", "mg_params",
+__all__ = ["Grid", "EWError", "ew_grid_create", "ew_grid_create_mapped", "ew_grid_destroy", "filter_params", "mg_params",
            "ew_filter_setup", "ew_choose_num_periods", "ew_filter_apply", "ew_apply_L", "ew_rayleigh",
            "ew_power_iteration",
            "ew_last_error", "LIB_PATH"]
@@ -97,6 +97,22 @@ def ew_grid_create(dim, n, length, order=2, prec="fp32", bc=None):
     h = ctypes.c_void_p()
     check(lib.ew_grid_create(int(dim), n3, l3, int(order), b6, p, ctypes.byref(h)))
     return Grid(h, dim, n[:dim], length[:dim], order, p, faces[:2 * dim])
+
+
+def ew_grid_create_mapped(n, xy, prec="fp32"):
+    """A curvilinear grid of the unit square's map x = G(r): ``n`` = (n1, n2)
+    interior vertices, ``xy`` = vertex coordinates, shape (n2 + 2, n1 + 2, 2)
+    (r1 index fastest, boundary vertices included)."""
+    p = {"fp32": EW_FP32, "fp64": EW_FP64, EW_FP32: EW_FP32, EW_FP64: EW_FP64}[prec]
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    if xy.shape != (int(n[1]) + 2, int(n[0]) + 2, 2):
+        raise ValueError("xy must have shape (n2 + 2, n1 + 2, 2)")
+    n2_ = (ctypes.c_int64 * 2)(int(n[0]), int(n[1]))
+    h = ctypes.c_void_p()
+    check(lib.ew_grid_create_mapped(n2_, xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), p, ctypes.byref(h)))
+    g = Grid(h, 2, (int(n[0]), int(n[1])), (1.0, 1.0), 2, p, [EW_BC_DIRICHLET] * 4)
+    g.mapped = True
+    return g
 
 
 def ew_grid_destroy(grid: Grid):

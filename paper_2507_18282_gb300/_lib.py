@@ -102,6 +102,7 @@ _ip = ctypes.POINTER(ctypes.c_int)
 
 lib.ew_last_error.restype = ctypes.c_char_p
 lib.ew_grid_create.argtypes = [_i, ctypes.POINTER(_i64), _dp, _i, _ip, _i, ctypes.POINTER(_vp)]
+lib.ew_grid_create_mapped.argtypes = [ctypes.POINTER(_i64), _dp, _i, ctypes.POINTER(_vp)]
 lib.ew_grid_destroy.argtypes = [_vp]
 lib.ew_grid_destroy.restype = None
 lib.ew_filter_setup.argtypes = [_vp, ctypes.POINTER(ew_filter_params), ctypes.POINTER(ew_filter_info), _dp, _i64]
@@ -124,7 +125,7 @@ lib.ew_smoother_forward.argtypes = [_vp, _vp, _vp, _vp, _vp]
 lib.ew_smoother_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
 lib.ew_smoother_train.argtypes = [_vp, _d, ctypes.POINTER(ew_train_params), _vp, ctypes.POINTER(ew_train_report),
                                   _vp]
-for _name in ["ew_grid_create", "ew_filter_setup", "ew_choose_num_periods", "ew_filter_apply", "ew_apply_L", "ew_rayleigh",
+for _name in ["ew_grid_create", "ew_grid_create_mapped", "ew_filter_setup", "ew_choose_num_periods", "ew_filter_apply", "ew_apply_L", "ew_rayleigh",
               "ew_power_iteration", "ew_profile_enable", "ew_profile_read", "ew_arnoldi_eigs",
               "ew_implicit_step_mg", "ew_smoother_forward", "ew_smoother_backward", "ew_smoother_train"]:
     getattr(lib, _name).restype = ctypes.c_int

@@ -172,7 +172,7 @@ struct KSRun {
         if (g->prec == EW_FP32) {
             EW_TRY(alloc(&fin, es * (size_t)N * b));
             EW_TRY(alloc(&fout, es * (size_t)N * b));
-        } else if (g->geom.bc) {
+        } else if (weighted_sums(g->geom)) {
             EW_TRY(alloc((void**)&symtmp, sizeof(double) * (size_t)N * b));
         }
         int wmax = m + 3 * b;
@@ -207,7 +207,7 @@ struct KSRun {
     // W^{1/2} S W^{-1/2}, symmetric in the plain sums that the Gram kernels and
     // the Rayleigh-Ritz step use (same eigenvalues; eigenvectors W^{1/2} phi).
     ew_status apply_S(const double* X) {
-        const bool sym = g->geom.bc != 0;
+        const bool sym = weighted_sums(g->geom);
         if (g->prec == EW_FP32) {
             const double* Xs = X;
             if (sym) {  // W is free until the result lands in it
@@ -302,7 +302,7 @@ struct KSRun {
     // start_dev: a caller's block (grid variables) or, with sym_vars, one
     // already in the variables of the symmetrised operator
     ew_status start(const double* start_dev, uint64_t seed, bool sym_vars = false) {
-        if (start_dev && g->geom.bc && !sym_vars)
+        if (start_dev && weighted_sums(g->geom) && !sym_vars)
             EW_TRY(launch_wsqrt<double>(g->geom, start_dev, V, b, 1, st));
         else if (start_dev)
             EW_CUDA_TRY(cudaMemcpyAsync(V, start_dev, sizeof(double) * (size_t)N * b, cudaMemcpyDeviceToDevice, st));
@@ -479,7 +479,7 @@ static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, int p, int max_ou
     // Rayleigh-Ritz with L_h inside span[X] (separates pairs that S cannot),
     // rank by beta_d(lambda) of the filter, then eig-res of the wanted pairs:
     // all FP64 and no wave-solve, so it doubles as the stopping test
-    const bool sym = g64->geom.bc != 0;  // the vectors are W^{1/2} phi (see KSRun::apply_S)
+    const bool sym = weighted_sums(g64->geom);  // the vectors are W^{1/2} phi (see KSRun::apply_S)
     double* Qfree = kr.V + (size_t)nw * N;  // columns nw .. 2 nw - 1, free outside an outer step's expansion
     auto lrr_check = [&](double* worst) -> ew_status {
         if (sym) {  // W^{1/2} L_h W^{-1/2} X
@@ -611,6 +611,10 @@ static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, int p, int max_ou
 }
 
 static ew_status make_twin_fp64(const ew_grid* g, ew_grid** out) {
+    if (g->geom.map) {
+        const int64_t n[2] = {g->geom.map->n1, g->geom.map->n2};
+        return ew_grid_create_mapped(n, g->geom.map->xy.data(), EW_FP64, out);
+    }
     ew_bc bc[6];
     int64_t n[3];
     for (int a = 0; a < 3; ++a) {
@@ -673,7 +677,7 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
     // stage 2 on the grid-precision result
     // with Neumann faces the basis holds W^{1/2} phi (KSRun::apply_S): the
     // quotients and eig-res are taken of phi, in the grid variables
-    const bool sym = g->geom.bc != 0;
+    const bool sym = weighted_sums(g->geom);
     double* phis = nullptr;
     if (sym) EW_TRY(ks.alloc((void**)&phis, sizeof(double) * (size_t)ks.N * nw));
     auto rq = [&](ew_grid* g64, const double* X, double* lam_h, double* res_h) -> ew_status {

@@ -360,7 +360,7 @@ extern "C" ew_status ew_filter_apply_batched(int nprob, const ew_grid* const* gr
         FilterPlan plan;
         EW_TRY(plan_filter(g->geom, &params[q], &plan));
         if (g->geom.dim != 2 || params[q].scheme != EW_EXPLICIT || g->prec != g0->prec ||
-            g->geom.order != g0->geom.order)
+            g->geom.order != g0->geom.order || g->geom.map)
             uniform = false;
         size_t es = g->prec == EW_FP32 ? 4 : 8;
         for (int v = 0; v < nv; ++v) {
@@ -373,7 +373,7 @@ extern "C" ew_status ew_filter_apply_batched(int nprob, const ew_grid* const* gr
         }
     }
     if (!uniform) {
-        // mixed batches (3D, implicit, mixed precision or order): one call per problem
+        // mixed batches (3D, implicit, curvilinear, mixed precision or order): one call per problem
         for (int q = 0; q < nprob; ++q)
             EW_TRY(ew_filter_apply(grids[q], &params[q], v_in[q], v_out[q], nvec ? nvec[q] : 1, stream));
         return EW_OK;

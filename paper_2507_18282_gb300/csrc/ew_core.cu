@@ -117,6 +117,7 @@ void Scratch::release() {
 // Largest eigenvalue of -L_h: the 1D symbols 4 s (order 2) and 4 s + (4/3) s^2
 // (order 4) at s = sin^2 = 1, summed over the axes.
 static double rho_bound(const GridGeom& g) {
+    if (g.map) return g.map->rho;
     double inv = 0.0;
     for (int a = 0; a < g.dim; ++a) inv += 1.0 / (g.h[a] * g.h[a]);
     return (g.order == 2 ? 4.0 : 16.0 / 3.0) * inv;
@@ -318,6 +319,11 @@ ew_status ew_grid_create(int dim, const int64_t n_interior[3], const double leng
 
 void ew_grid_destroy(ew_grid* g) {
     if (!g) return;
+    if (g->geom.map) {
+        mapped_release(g->geom.map);
+        delete g->geom.map;
+        g->geom.map = nullptr;
+    }
     g->fields.release();
     g->reduce.release();
     g->misc.release();
@@ -384,7 +390,7 @@ static ew_status rayleigh_t(ew_grid* g, const T* phi, int nvec, double* lam_host
                             cudaStream_t st) {
     const int64_t N = g->geom.N;
     // scratch: Lphi (nvec * N of T) in fields; reduction partials and results in reduce
-    const bool weighted = g->geom.bc != 0;
+    const bool weighted = weighted_sums(g->geom);
     EW_TRY(g->fields.reserve((weighted ? 3 : 1) * (size_t)nvec * N * sizeof(T)));
     size_t part = (size_t)2 * nvec * kReduceBlocks;
     EW_TRY(g->reduce.reserve((part + 6 * (size_t)nvec) * sizeof(double)));

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -58,6 +59,21 @@ struct Stencil {
     int bc;
 };
 
+// a single curvilinear grid (ew_mapped.cu): couplings of J L on the vertex
+// lattice (vertex (I, J) to (I+1, J), (I, J+1), (I+1, J+1), (I+1, J-1)), J at
+// the active vertices, the vertex coordinates, the Gershgorin bound of
+// rho(-L), and device copies made on first use
+struct MappedData {
+    int64_t n1 = 0, n2 = 0;
+    std::vector<double> E, N, NE, SE;
+    std::vector<double> J;
+    std::vector<double> xy;
+    double rho = 0.0;
+    void* dev[2] = {nullptr, nullptr};  // [cC | cE | cN | cNE | cSE | 1/J] in FP32 / FP64
+    double* sqrtJ = nullptr;
+    std::mutex mu;
+};
+
 struct GridGeom {
     int dim;
     int order;
@@ -65,7 +81,11 @@ struct GridGeom {
     double h[3];
     int64_t N;     // active points
     int bc = 0;    // face mask, as in Stencil
+    MappedData* map = nullptr;  // a curvilinear grid (2D, order 2, Dirichlet): the couplings replace the stencil
 };
+
+// the sums of inner products carry weights (Neumann faces: trapezoid; mapped grids: J)
+inline bool weighted_sums(const GridGeom& g) { return g.bc != 0 || g.map != nullptr; }
 
 template <typename T>
 Stencil<T> make_stencil(const GridGeom& g, double scale);
@@ -153,6 +173,17 @@ template <typename T>
 ew_status explicit_wave_solve(const GridGeom& g, const FilterPlan& plan, const T* cdev,
                               const T* vin, T* vout, int nvec, T* fields, int temporal_block,
                               cudaStream_t st);
+
+// --- curvilinear grids (ew_mapped.cu) ----------------------------------------
+ew_status mapped_build(int64_t n1, int64_t n2, const double* xy, MappedData* m);
+void mapped_release(MappedData* m);
+template <typename T>
+ew_status mapped_apply_L(const GridGeom& g, const T* u, T* Lu, int nvec, double scale, cudaStream_t st);
+template <typename T>
+ew_status mapped_wave_solve(const GridGeom& g, const FilterPlan& plan, const T* vin, T* vout, int nvec, T* fields,
+                            cudaStream_t st);
+template <typename T>
+ew_status mapped_wsqrt(const GridGeom& g, const T* in, T* out, int nvec, int e, cudaStream_t st);
 
 // --- temporally blocked 2D steps (ew_tb2d.cu) -----------------------------
 // choose (and cache) the tile / depth variant for this grid shape by timing

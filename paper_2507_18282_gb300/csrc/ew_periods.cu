@@ -106,6 +106,7 @@ ew_status ew_choose_num_periods(const ew_grid* grid, const ew_filter_params* par
     if (n_wanted < 1 || krylov_dim <= n_wanted) return set_error(EW_EINVAL, "need 1 <= n_wanted < krylov_dim");
     if (max_periods < 1 || max_periods > (1 << 20)) return set_error(EW_EINVAL, "max_periods out of range");
     const GridGeom& g = grid->geom;
+    if (g.map) return set_error(EW_EUNSUPPORTED, "the spectrum of a mapped grid has no closed form");
     if ((int64_t)krylov_dim + 1 > g.N) return set_error(EW_EINVAL, "krylov_dim + 1 exceeds the number of points");
     std::vector<std::vector<double>> mu;
     for (int a = 0; a < g.dim; ++a) mu.push_back(axis_symbol(g, a));

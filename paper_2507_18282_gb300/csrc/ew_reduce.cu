@@ -199,6 +199,7 @@ __global__ void k_wsqrt(const T* __restrict__ in, T* __restrict__ out, int64_t n
 
 template <typename T>
 ew_status launch_wsqrt(const GridGeom& g, const T* in, T* out, int nvec, int e, cudaStream_t st) {
+    if (g.map) return mapped_wsqrt<T>(g, in, out, nvec, e, st);
     const T f = e > 0 ? T(0.70710678118654752440) : T(1.41421356237309504880);
     k_wsqrt<T><<<kReduceBlocks * 4, 256, 0, st>>>(in, out, g.n[0], g.n[1], g.N, g.N * (int64_t)nvec, g.bc, f);
     EW_CUDA_TRY(cudaGetLastError());

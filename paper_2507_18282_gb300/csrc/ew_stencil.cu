@@ -285,6 +285,7 @@ static ew_status pt_check(const GridGeom& g, int nvec) {
 template <typename T>
 ew_status launch_apply_L(const GridGeom& g, const T* u, T* Lu, int nvec, double scale,
                          cudaStream_t st) {
+    if (g.map) return mapped_apply_L<T>(g, u, Lu, nvec, scale, st);
     Stencil<T> s = make_stencil<T>(g, scale);
     EW_TRY(pt_check(g, nvec));
     dim3 grid = pt_grid(g, nvec), blk(pt_threads(g.n[0]));
@@ -386,6 +387,7 @@ template <typename T>
 ew_status explicit_wave_solve(const GridGeom& g, const FilterPlan& plan, const T* cdev, const T* vin, T* vout,
                               int nvec, T* fields, int temporal_block, cudaStream_t st) {
     if (temporal_block < 0) return set_error(EW_EINVAL, "temporal_block < 0");
+    if (g.map) return mapped_wave_solve<T>(g, plan, vin, vout, nvec, fields, st);  // one step per launch
     if (use_resident<T>(g, nvec) && temporal_block == 0) return resident<T>(g, vin, vout, cdev, plan, nvec, st);
     // fields are laid out [field][vector][point]
     const int64_t fstride = field_stride(g.N);

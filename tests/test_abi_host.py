@@ -111,3 +111,27 @@ def test_neumann_faces_add_active_wall_points(ew):
     with pytest.raises(ew.EWError) as e:
         ew.ew_grid_create(2, (3, 3), (1, 1), bc=(0, 1, 2, 0))   # 2 is not a boundary kind
     assert e.value.status == 1
+
+
+def test_mapped_grid_creation_and_step_limit(ew):
+    """Creating a curvilinear grid needs no GPU; a map that folds over (J <= 0)
+    is refused; the explicit step limit comes from a Gershgorin bound of
+    rho(-L), which must not be below the true spectral radius (the oracle's
+    dense operator)."""
+    import ew_inputs
+    from oracle import oracle as O
+    n = (14, 11)
+    xy = ew_inputs.mapped_vertices(*n, "square_warp", eps=0.15)
+    g = ew.ew_grid_create_mapped(n, xy, prec="fp64")
+    assert g.size == n[0] * n[1]
+    info, _ = ew.ew_filter_setup(g, ew.filter_params(9.0, steps_per_period=0))
+    g.close()
+    L = np.stack([O.mapped_apply_L(O.MappedGrid(n, xy), e) for e in np.eye(n[0] * n[1])], axis=1)
+    rho = np.max(np.abs(np.linalg.eigvals(L)))
+    # leapfrog is stable for dt^2 rho / 4 <= 1; the library's dt must satisfy it
+    assert info["dt"] ** 2 * rho / 4.0 <= 1.0
+    bad = xy.copy()
+    bad[..., 0] = -bad[..., 0]  # mirror: orientation reversed, J < 0
+    with pytest.raises(ew.EWError) as e:
+        ew.ew_grid_create_mapped(n, bad)
+    assert e.value.status == 1
