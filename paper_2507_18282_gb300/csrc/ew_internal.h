@@ -69,7 +69,7 @@ struct MappedData {
     std::vector<double> J;
     std::vector<double> xy;
     double rho = 0.0;
-    void* dev[2] = {nullptr, nullptr};  // [cC | cE | cN | cNE | cSE | 1/J] in FP32 / FP64
+    void* dev[2] = {nullptr, nullptr};  // per vertex (E, N, NE, SE), then (centre, 1/J): FP32 / FP64
     double* sqrtJ = nullptr;
     std::mutex mu;
 };

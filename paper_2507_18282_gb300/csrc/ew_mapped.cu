@@ -16,7 +16,8 @@
 // coupling of a vertex to its east neighbour equals the east neighbour's
 // coupling back, and likewise north, north-east and south-east.  So per
 // active vertex the library stores the centre and the E, N, NE, SE couplings
-// of J L (the W, S, SW, NW ones are the neighbours' E, N, NE, SE) and 1/J.
+// of J L (the W, S, SW, NW ones are the neighbours' E, N, NE, SE) and 1/J, as
+// one 4-wide record (E, N, NE, SE) and one 2-wide record (centre, 1/J) per vertex.
 // The off-diagonal couplings are rounded to a common grid and the centre is
 // minus their exact sum, so L 1 = 0 holds exactly in the stored precision
 // (the same consistency as the box stencils).
@@ -134,9 +135,11 @@ static void mapped_round(const MappedData& m, std::vector<T>& out) {
     frexp(16.0 * mx, &e);
     double q2 = 0.5 * ldexp(1.0, e - mant);
     auto rnd = [&](double c) { return nearbyint(c / q2) * q2; };
+    // layout: N records (E, N, NE, SE) then N records (centre, 1/J), so a point's
+    // own couplings are one 4-wide and one 2-wide load
     out.assign((size_t)(6 * N), T(0));
-    T* cC = out.data();
-    T *cE = cC + N, *cN = cE + N, *cNE = cN + N, *cSE = cNE + N, *rJ = cSE + N;
+    T* quad = out.data();
+    T* pair = quad + 4 * N;
     auto c = [&](const std::vector<double>& a, int64_t i, int64_t j) { return rnd(a[(size_t)(j * p1 + i)]); };
     for (int64_t J = 1; J <= n2; ++J)
         for (int64_t I = 1; I <= n1; ++I) {
@@ -145,12 +148,12 @@ static void mapped_round(const MappedData& m, std::vector<T>& out) {
                                    c(m.NE, I, J),    c(m.NE, I - 1, J - 1), c(m.SE, I, J), c(m.SE, I - 1, J + 1)};
             double centre = 0.0;
             for (double o : off) centre -= o;  // exact: multiples of q/2 far below 2^53 q/2
-            cC[q] = T(centre);
-            cE[q] = T(off[0]);
-            cN[q] = T(off[2]);
-            cNE[q] = T(off[4]);
-            cSE[q] = T(off[6]);
-            rJ[q] = T(1.0 / m.J[q]);
+            quad[4 * q + 0] = T(off[0]);
+            quad[4 * q + 1] = T(off[2]);
+            quad[4 * q + 2] = T(off[4]);
+            quad[4 * q + 3] = T(off[6]);
+            pair[2 * q + 0] = T(centre);
+            pair[2 * q + 1] = T(1.0 / m.J[q]);
         }
 }
 
@@ -201,23 +204,40 @@ void mapped_release(MappedData* m) {
     m->sqrtJ = nullptr;
 }
 
-// J L u at active vertex (i, j) (0-based), x fastest; neighbours beyond the
-// active set are boundary vertices (u = 0)
+// a point's own couplings: (E, N, NE, SE) and (centre, 1/J)
+template <typename T>
+struct Own {
+    T e, n, ne, se, c, rj;
+};
+__device__ __forceinline__ Own<float> own_couplings(const float* __restrict__ c, int64_t N, int64_t q) {
+    const float4 a = reinterpret_cast<const float4*>(c)[q];
+    const float2 b = reinterpret_cast<const float2*>(c + 4 * N)[q];
+    return Own<float>{a.x, a.y, a.z, a.w, b.x, b.y};
+}
+__device__ __forceinline__ Own<double> own_couplings(const double* __restrict__ c, int64_t N, int64_t q) {
+    const double2 a = reinterpret_cast<const double2*>(c)[2 * q];
+    const double2 a2 = reinterpret_cast<const double2*>(c)[2 * q + 1];
+    const double2 b = reinterpret_cast<const double2*>(c + 4 * N)[q];
+    return Own<double>{a.x, a.y, a2.x, a2.y, b.x, b.y};
+}
+
+// J L u at active vertex (i, j) (0-based), x fastest, and 1/J there; neighbours
+// beyond the active set are boundary vertices (u = 0)
 template <typename T>
 __device__ __forceinline__ T mapped_jlap(const T* __restrict__ u, const T* __restrict__ c, int64_t N, int nx,
-                                         int ny, int i, int j, int64_t q) {
-    const T* cC = c;
-    const T *cE = c + N, *cN = cE + N, *cNE = cN + N, *cSE = cNE + N;
+                                         int ny, int i, int j, int64_t q, T& rj) {
+    const Own<T> o = own_couplings(c, N, q);
+    rj = o.rj;
     const bool w = i > 0, e = i + 1 < nx, s = j > 0, n = j + 1 < ny;
-    T r = cC[q] * u[q];
-    if (e) r += cE[q] * u[q + 1];
-    if (w) r += cE[q - 1] * u[q - 1];
-    if (n) r += cN[q] * u[q + nx];
-    if (s) r += cN[q - nx] * u[q - nx];
-    if (e && n) r += cNE[q] * u[q + 1 + nx];
-    if (w && s) r += cNE[q - 1 - nx] * u[q - 1 - nx];
-    if (e && s) r += cSE[q] * u[q + 1 - nx];
-    if (w && n) r += cSE[q - 1 + nx] * u[q - 1 + nx];
+    T r = o.c * u[q];
+    if (e) r += o.e * u[q + 1];
+    if (w) r += c[4 * (q - 1) + 0] * u[q - 1];
+    if (n) r += o.n * u[q + nx];
+    if (s) r += c[4 * (q - nx) + 1] * u[q - nx];
+    if (e && n) r += o.ne * u[q + 1 + nx];
+    if (w && s) r += c[4 * (q - 1 - nx) + 2] * u[q - 1 - nx];
+    if (e && s) r += o.se * u[q + 1 - nx];
+    if (w && n) r += c[4 * (q - 1 + nx) + 3] * u[q - 1 + nx];
     return r;
 }
 
@@ -228,8 +248,9 @@ __global__ void __launch_bounds__(128) k_mapped_apply(int nx, int ny, const T* _
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= nx) return;
     const int64_t N = (int64_t)nx * ny, q = (int64_t)j * nx + i, v = blockIdx.z;
-    const T* rJ = c + 5 * N;
-    Lu[v * N + q] = scale * rJ[q] * mapped_jlap<T>(u + v * N, c, N, nx, ny, i, j, q);
+    T rj;
+    const T jl = mapped_jlap<T>(u + v * N, c, N, nx, ny, i, j, q, rj);
+    Lu[v * N + q] = scale * rj * jl;
 }
 
 // first step: D^1 = (dt^2/2) L V, W^1 = V + D^1, out = c0 V + c1 W^1
@@ -241,9 +262,10 @@ __global__ void __launch_bounds__(128) k_mapped_first(int nx, int ny, const T* _
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= nx) return;
     const int64_t N = (int64_t)nx * ny, q = (int64_t)j * nx + i, v = blockIdx.z;
-    const T* rJ = c + 5 * N;
     const T x = vin[v * N + q];
-    const T d = half_dt2 * rJ[q] * mapped_jlap<T>(vin + v * N, c, N, nx, ny, i, j, q);
+    T rj;
+    const T jl = mapped_jlap<T>(vin + v * N, c, N, nx, ny, i, j, q, rj);
+    const T d = half_dt2 * rj * jl;
     const T w1 = x + d;
     D1[v * fstride + q] = d;
     W1[v * fstride + q] = w1;
@@ -258,9 +280,10 @@ __global__ void __launch_bounds__(128) k_mapped_step(int nx, int ny, const T* __
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= nx) return;
     const int64_t N = (int64_t)nx * ny, q = (int64_t)j * nx + i, v = blockIdx.z;
-    const T* rJ = c + 5 * N;
     const int64_t f = v * fstride + q;
-    const T d = D[f] + dt2 * rJ[q] * mapped_jlap<T>(W + v * fstride, c, N, nx, ny, i, j, q);
+    T rj;
+    const T jl = mapped_jlap<T>(W + v * fstride, c, N, nx, ny, i, j, q, rj);
+    const T d = D[f] + dt2 * rj * jl;
     const T wn = W[f] + d;
     D[f] = d;
     Wout[f] = wn;
