@@ -66,8 +66,8 @@ def parse():
                                            "mgtol", "mapped2d"],
                     default="rect2d",
                     help="rect2d is the headline line; the others print their own line")
-    ap.add_argument("--eigs-arm", choices=["both", "fp32", "plain"], default="both",
-                    help="eigs2d: run both arms (default) or one")
+    ap.add_argument("--eigs-arm", choices=["both", "fp32_fp64", "fp32_pair", "plain"], default="both",
+                    help="eigs2d: every arm (default) or one")
     ap.add_argument("--num-periods", type=int, default=0,
                     help="N_p of the eigs2d workload (0: the library's choice, ew_choose_num_periods)")
     return ap.parse_args()
@@ -633,9 +633,12 @@ def run_extra(args):
             cr_est = float(cr[num_periods.bit_length() - 1])
             g.close()
         # the plain arm stops on the Ritz residual of S: 2e-11 brings every eig-res below 1e-8
-        arms = [("fp32_fp64_refine", "fp32", 1, 0.0), ("plain_fp64", "fp64", 0, 2e-11)]
+        arms = [("fp32_fp64_refine", "fp32", 1, 0.0), ("fp32_pair_refine", "fp32", 3, 0.0),
+                ("plain_fp64", "fp64", 0, 2e-11)]
         if args.eigs_arm != "both":
             arms = [a for a in arms if a[0].startswith(args.eigs_arm)]
+        else:  # the default run: the pair-arithmetic mixed arm against plain FP64
+            arms = [a for a in arms if a[0] != "fp32_fp64_refine"]
         for name, prec, refine, tol in arms:
             g = ew.ew_grid_create(2, n, L, order=4, prec=prec)
             p = ew.filter_params(150.0, num_periods=num_periods)
@@ -655,8 +658,8 @@ def run_extra(args):
             g.close()
         line = dict(workload="eigs_rect2d_2047x3071_order4_8_nearest_omega150", unit="s",
                     num_periods=num_periods, cr_estimate=cr_est, metric="s to 8 eigenpairs at 1e-8 resid vs plain", runs=runs,
-                    speedup=(runs["plain_fp64"]["seconds"] / runs["fp32_fp64_refine"]["seconds"]
-                             if len(runs) == 2 else None))
+                    speedup={k: runs["plain_fp64"]["seconds"] / r["seconds"] for k, r in runs.items()
+                             if k != "plain_fp64"} if "plain_fp64" in runs else None)
     else:
         raise SystemExit("unknown workload %s" % w)
     line.update(dict(n_gpus=1, steps=args.steps, warmup=args.warmup, dtype="f32", data="synthetic",

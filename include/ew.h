@@ -57,7 +57,12 @@ typedef enum {
 } ew_status;
 
 typedef enum { EW_BC_DIRICHLET = 0, EW_BC_NEUMANN = 1 } ew_bc;
-typedef enum { EW_FP32 = 0, EW_FP64 = 1 } ew_prec;
+/* EW_FP32X2: 2D boxes only; vectors are FP64 (double) in and out, the wave-solve
+ * runs in pairs of FP32 numbers (an unevaluated sum hi + lo, about 48
+ * significant bits) on the full-rate FP32 units; ew_filter_apply and
+ * ew_filter_apply_batched only (the FP64 filter applications of the
+ * mixed-precision eigen-solver, refine_fp64 = 3, use it internally). */
+typedef enum { EW_FP32 = 0, EW_FP64 = 1, EW_FP32X2 = 2 } ew_prec;
 typedef enum { EW_EXPLICIT = 0, EW_IMPLICIT = 1 } ew_scheme;
 
 typedef struct ew_grid ew_grid; /* opaque, library-owned */
@@ -299,8 +304,12 @@ typedef struct {
                                  new X.  p = 6 and g = n_wanted where they fit ((p + 2)(n_wanted + g)
                                  <= 128 basis columns), fewer for large n_wanted (n_wanted <= 23).
                               2: a second Krylov-Schur run with FP64 full-filter wave-solves started
-                                 from the FP32 vectors (block n_wanted, basis 3 n_wanted) */
-    double refine_tol;     /* refine_fp64 1: eig-res target of every wanted pair, 0: 5e-9;
+                                 from the FP32 vectors (block n_wanted, basis 3 n_wanted)
+                              3: as 1, with the images S X of each outer step computed in double-FP32
+                                 pairs (EW_FP32X2, about 48 significant bits, on the FP32 units) on 2D
+                                 boxes; once an outer step cuts the worst eig-res by less than 10x the
+                                 remaining images are FP64 */
+    double refine_tol;     /* refine_fp64 1, 3: eig-res target of every wanted pair, 0: 5e-9;
                               refine_fp64 2: FP64 Ritz residual target, 0: 1e-10 */
 } ew_eigs_params;
 

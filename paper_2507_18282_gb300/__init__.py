@@ -16,7 +16,7 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (EW_BC_DIRICHLET, EW_BC_NEUMANN, EW_EXPLICIT, EW_FP32, EW_FP64, EW_IMPLICIT, EWError, check, lib,
+from ._lib import (EW_BC_DIRICHLET, EW_BC_NEUMANN, EW_EXPLICIT, EW_FP32, EW_FP32X2, EW_FP64, EW_IMPLICIT, EWError, check, lib,
                    ew_filter_info, ew_filter_params, ew_mg_params)
 
 __all__ = ["Grid", "EWError", "ew_grid_create", "ew_grid_create_mapped", "ew_grid_destroy", "filter_params", "mg_params",
@@ -83,7 +83,8 @@ class Grid:
 def ew_grid_create(dim, n, length, order=2, prec="fp32", bc=None):
     """``n``: interior points per axis; ``bc``: None (all Dirichlet) or 2 dim face
     kinds (-x, +x, -y, +y[, -z, +z]), each "D" / "N" or EW_BC_DIRICHLET / EW_BC_NEUMANN."""
-    p = {"fp32": EW_FP32, "fp64": EW_FP64, EW_FP32: EW_FP32, EW_FP64: EW_FP64}[prec]
+    p = {"fp32": EW_FP32, "fp64": EW_FP64, "fp32x2": EW_FP32X2, EW_FP32: EW_FP32, EW_FP64: EW_FP64,
+         EW_FP32X2: EW_FP32X2}[prec]
     kinds = {"D": EW_BC_DIRICHLET, "N": EW_BC_NEUMANN, EW_BC_DIRICHLET: EW_BC_DIRICHLET,
              EW_BC_NEUMANN: EW_BC_NEUMANN}
     faces = [EW_BC_DIRICHLET] * 6

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", platform.machine(), "libew.so")
 EW_OK, EW_EINVAL, EW_ENOMEM, EW_ECUDA, EW_ENOCONV, EW_EBREAKDOWN, EW_ETIMEOUT, EW_EUNSUPPORTED = range(8)
 STATUS_NAMES = ["EW_OK", "EW_EINVAL", "EW_ENOMEM", "EW_ECUDA", "EW_ENOCONV", "EW_EBREAKDOWN",
                 "EW_ETIMEOUT", "EW_EUNSUPPORTED"]
-EW_FP32, EW_FP64 = 0, 1
+EW_FP32, EW_FP64, EW_FP32X2 = 0, 1, 2
 EW_BC_DIRICHLET, EW_BC_NEUMANN = 0, 1
 EW_EXPLICIT, EW_IMPLICIT = 0, 1
 

@@ -466,8 +466,11 @@ static bool refine_shape(int nw, int* p, int* guard) {
     return false;
 }
 
-static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, int p, int max_outer, double res_tol,
-                           std::vector<double>& lam_out, std::vector<double>& beta_out,
+// gimg: the grid whose filter applications give the images S X (g64, or its
+// double-FP32 twin); the images fall back to g64 once an outer step with gimg
+// cuts the worst eig-res by less than 10x (its accuracy floor reached)
+static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, ew_grid* gimg, int p, int max_outer,
+                           double res_tol, std::vector<double>& lam_out, std::vector<double>& beta_out,
                            std::vector<double>& res_out, int* ws64, int* outer_done) {
     const int64_t N = ks.N;
     const int nw = kr.nw;      // wanted + guard vectors refined together
@@ -526,19 +529,26 @@ static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, int p, int max_ou
     };
     std::vector<double> theta, Y, resid;
     *outer_done = 0;
+    if (!gimg) gimg = g64;
+    double prev_worst = INFINITY;
     for (int outer = 0; outer < max_outer; ++outer) {
         double worst = 0.0;
         EW_TRY(lrr_check(&worst));
         if (worst <= res_tol) break;
-        // exact image of X in FP64: S X = X Theta + E
+        if (gimg != g64 && worst > 0.1 * prev_worst) {
+            gimg = g64;
+            if (getenv("EW_KS_LOG")) fprintf(stderr, "[ew refine] images in FP64 from here on\n");
+        }
+        prev_worst = worst;
+        // image of X at FP64 accuracy: S X = X Theta + E
         for (int c0 = 0; c0 < nw; c0 += 16) {
             int nb = std::min(16, nw - c0);
             if (sym) {
                 EW_TRY(launch_wsqrt<double>(g64->geom, kr.V + (size_t)c0 * N, Qfree, nb, -1, kr.st));
-                EW_TRY(filter_apply_any(g64, ks.p, ks.plan, Qfree, W64 + (size_t)c0 * N, nb, kr.st));
+                EW_TRY(filter_apply_any(gimg, ks.p, ks.plan, Qfree, W64 + (size_t)c0 * N, nb, kr.st));
                 EW_TRY(launch_wsqrt<double>(g64->geom, W64 + (size_t)c0 * N, W64 + (size_t)c0 * N, nb, 1, kr.st));
             } else {
-                EW_TRY(filter_apply_any(g64, ks.p, ks.plan, kr.V + (size_t)c0 * N, W64 + (size_t)c0 * N, nb,
+                EW_TRY(filter_apply_any(gimg, ks.p, ks.plan, kr.V + (size_t)c0 * N, W64 + (size_t)c0 * N, nb,
                                         kr.st));
             }
         }
@@ -648,7 +658,9 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
     if (m < nw + b) return set_error(EW_EINVAL, "krylov_dim must be >= n_wanted + block");
     if (m + 2 * b > 160) return set_error(EW_EINVAL, "krylov_dim too large (krylov_dim + 2 block <= 160)");
     int ref_p = 0, ref_guard = 0;
-    if (ep->refine_fp64 == 1 && grid->prec == EW_FP32 && !refine_shape(nw, &ref_p, &ref_guard))
+    if (grid->prec == EW_FP32X2) return set_error(EW_EUNSUPPORTED, "double-FP32 grids: ew_filter_apply only");
+    if (ep->refine_fp64 < 0 || ep->refine_fp64 > 3) return set_error(EW_EINVAL, "refine_fp64 must be 0..3");
+    if ((ep->refine_fp64 == 1 || ep->refine_fp64 == 3) && grid->prec == EW_FP32 && !refine_shape(nw, &ref_p, &ref_guard))
         return set_error(EW_EINVAL, "n_wanted too large for the FP64 refinement (n_wanted <= 23)");
     if ((int64_t)m > grid->geom.N) return set_error(EW_EINVAL, "krylov_dim exceeds the number of active points");
     ew_grid* g = const_cast<ew_grid*>(grid);
@@ -698,8 +710,17 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
     KSRun ks2;
     ew_grid* g64 = nullptr;
     ew_status status = nconv >= nw ? EW_OK : EW_ENOCONV;
-    if (ep->refine_fp64 == 1 && g->prec == EW_FP32) {
+    ew_grid* gdd = nullptr;  // refine_fp64 3: the images in double-FP32 pairs
+    if ((ep->refine_fp64 == 1 || ep->refine_fp64 == 3) && g->prec == EW_FP32) {
         EW_TRY(make_twin_fp64(g, &g64));
+        if (ep->refine_fp64 == 3 && g->geom.dim == 2 && !g->geom.map) {
+            ew_status st2 = make_twin_fp64(g, &gdd);
+            if (st2 != EW_OK) {
+                ew_grid_destroy(g64);
+                return st2;
+            }
+            gdd->prec = EW_FP32X2;
+        }
         // guard vectors: a pair just outside the wanted set can share beta with
         // one inside (lambda on the other side of the peak); refining both and
         // ranking by beta_d(lambda) after the L_h projection keeps the right one.
@@ -721,7 +742,8 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
         int ws64 = 0, outer = 0;
         double res_tol = ep->refine_tol > 0 ? ep->refine_tol : 5e-9;
         ew_status s = kr.setup();
-        if (s == EW_OK) s = refine_ir(ks, kr, g64, pexp, 6, res_tol, lam, beta, res, &ws64, &outer);
+        if (s == EW_OK) s = refine_ir(ks, kr, g64, gdd, pexp, 6, res_tol, lam, beta, res, &ws64, &outer);
+        if (gdd) ew_grid_destroy(gdd);
         if (s != EW_OK) {
             ew_grid_destroy(g64);
             return s;

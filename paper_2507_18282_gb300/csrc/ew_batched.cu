@@ -360,7 +360,7 @@ extern "C" ew_status ew_filter_apply_batched(int nprob, const ew_grid* const* gr
         FilterPlan plan;
         EW_TRY(plan_filter(g->geom, &params[q], &plan));
         if (g->geom.dim != 2 || params[q].scheme != EW_EXPLICIT || g->prec != g0->prec ||
-            g->geom.order != g0->geom.order || g->geom.map)
+            g->geom.order != g0->geom.order || g->geom.map || g->prec == EW_FP32X2)
             uniform = false;
         size_t es = g->prec == EW_FP32 ? 4 : 8;
         for (int v = 0; v < nv; ++v) {

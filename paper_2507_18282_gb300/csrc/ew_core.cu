@@ -11,6 +11,7 @@
 #include <cstring>
 #include <string>
 
+#include "ew_dd.cuh"
 #include "ew_internal.h"
 
 namespace ew {
@@ -219,8 +220,40 @@ static ew_status filter_apply_t(ew_grid* g, const ew_filter_params* p, const Fil
     return explicit_wave_solve<T>(g->geom, plan, cdev, vin, vout, nvec, (T*)g->fields.ptr, p->temporal_block, st);
 }
 
+__global__ void k_to_dd(const double* __restrict__ x, dd* __restrict__ y, int64_t n) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        y[q] = dd(x[q]);
+}
+__global__ void k_from_dd(const dd* __restrict__ x, double* __restrict__ y, int64_t n) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        y[q] = (double)x[q];
+}
+
+// EW_FP32X2 grids: FP64 vectors in and out, the wave-solve in double-FP32 pairs
+static ew_status filter_apply_dd(ew_grid* g, const ew_filter_params* p, const FilterPlan& plan, const double* vin,
+                                 double* vout, int nvec, cudaStream_t st) {
+    if (p->scheme == EW_IMPLICIT)
+        return set_error(EW_EUNSUPPORTED, "double-FP32 grids run the explicit scheme only");
+    const int64_t n = g->geom.N * (int64_t)nvec;
+    const dd* cdev = nullptr;
+    EW_TRY(upload_weights<dd>(g, plan, st, &cdev));
+    EW_TRY(g->fields.reserve((size_t)4 * nvec * field_stride(g->geom.N) * sizeof(dd)));
+    EW_TRY(g->mg.reserve((size_t)2 * n * sizeof(dd)));
+    dd* din = (dd*)g->mg.ptr;
+    dd* dout = din + n;
+    k_to_dd<<<kReduceBlocks * 4, 256, 0, st>>>(vin, din, n);
+    EW_CUDA_TRY(cudaGetLastError());
+    count_launch();
+    EW_TRY(explicit_wave_solve<dd>(g->geom, plan, cdev, din, dout, nvec, (dd*)g->fields.ptr, p->temporal_block, st));
+    k_from_dd<<<kReduceBlocks * 4, 256, 0, st>>>(dout, vout, n);
+    EW_CUDA_TRY(cudaGetLastError());
+    count_launch();
+    return EW_OK;
+}
+
 ew_status filter_apply_any(ew_grid* g, const ew_filter_params* p, const FilterPlan& plan, const void* vin,
                            void* vout, int nvec, cudaStream_t st) {
+    if (g->prec == EW_FP32X2) return filter_apply_dd(g, p, plan, (const double*)vin, (double*)vout, nvec, st);
     if (g->prec == EW_FP32) return filter_apply_t<float>(g, p, plan, (const float*)vin, (float*)vout, nvec, st);
     return filter_apply_t<double>(g, p, plan, (const double*)vin, (double*)vout, nvec, st);
 }
@@ -273,7 +306,8 @@ ew_status ew_grid_create(int dim, const int64_t n_interior[3], const double leng
     *out = nullptr;
     if (dim != 2 && dim != 3) return set_error(EW_EINVAL, "dim must be 2 or 3");
     if (order != 2 && order != 4) return set_error(EW_EINVAL, "order must be 2 or 4");
-    if (prec != EW_FP32 && prec != EW_FP64) return set_error(EW_EINVAL, "bad precision");
+    if (prec != EW_FP32 && prec != EW_FP64 && prec != EW_FP32X2) return set_error(EW_EINVAL, "bad precision");
+    if (prec == EW_FP32X2 && dim != 2) return set_error(EW_EUNSUPPORTED, "double-FP32 fields: 2D boxes only");
     GridGeom geom;
     geom.bc = 0;
     if (bc)
@@ -367,9 +401,7 @@ ew_status ew_filter_apply(const ew_grid* grid, const ew_filter_params* params, c
     FilterPlan plan;
     EW_TRY(plan_filter(grid->geom, params, &plan));
     ew_grid* g = const_cast<ew_grid*>(grid);
-    if (grid->prec == EW_FP32)
-        return filter_apply_t<float>(g, params, plan, (const float*)v_in, (float*)v_out, nvec, stream);
-    return filter_apply_t<double>(g, params, plan, (const double*)v_in, (double*)v_out, nvec, stream);
+    return filter_apply_any(g, params, plan, v_in, v_out, nvec, stream);
 }
 
 ew_status ew_apply_L(const ew_grid* grid, const void* u, void* Lu, int nvec, cudaStream_t stream) {
@@ -377,6 +409,7 @@ ew_status ew_apply_L(const ew_grid* grid, const void* u, void* Lu, int nvec, cud
     EW_TRY(check_grid(grid));
     if (!u || !Lu) return set_error(EW_EINVAL, "null vector pointer");
     if (nvec < 1 || nvec > 65535) return set_error(EW_EINVAL, "nvec must be in [1, 65535]");
+    if (grid->prec == EW_FP32X2) return set_error(EW_EUNSUPPORTED, "double-FP32 grids: ew_filter_apply only");
     if (grid->prec == EW_FP32) return launch_apply_L<float>(grid->geom, (const float*)u, (float*)Lu, nvec, 1.0, stream);
     return launch_apply_L<double>(grid->geom, (const double*)u, (double*)Lu, nvec, 1.0, stream);
 }
@@ -508,6 +541,7 @@ ew_status ew_rayleigh(const ew_grid* grid, const void* phi, int nvec, double* la
     EW_TRY(check_grid(grid));
     if (!phi || !lambda_host) return set_error(EW_EINVAL, "null pointer");
     if (nvec < 1 || nvec > 65535) return set_error(EW_EINVAL, "nvec must be in [1, 65535]");
+    if (grid->prec == EW_FP32X2) return set_error(EW_EUNSUPPORTED, "double-FP32 grids: ew_filter_apply only");
     ew_grid* g = const_cast<ew_grid*>(grid);
     if (grid->prec == EW_FP32) return rayleigh_t<float>(g, (const float*)phi, nvec, lambda_host, eig_res_host, stream);
     return rayleigh_t<double>(g, (const double*)phi, nvec, lambda_host, eig_res_host, stream);
@@ -519,6 +553,7 @@ ew_status ew_power_iteration(const ew_grid* grid, const ew_filter_params* params
     EW_TRY(check_grid(grid));
     if (!v || !params) return set_error(EW_EINVAL, "null pointer");
     if (iters < 0) return set_error(EW_EINVAL, "iters < 0");
+    if (grid->prec == EW_FP32X2) return set_error(EW_EUNSUPPORTED, "double-FP32 grids: ew_filter_apply only");
     ew_grid* g = const_cast<ew_grid*>(grid);
     if (grid->prec == EW_FP32)
         return power_t<float>(g, params, (float*)v, iters, tol, beta_host, iters_done, lambda_host, stream);

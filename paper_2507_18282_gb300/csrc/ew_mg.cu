@@ -263,6 +263,7 @@ struct MGSolver {
         if (g->geom.bc)
             return set_error(EW_EUNSUPPORTED, "multigrid: boxes with Neumann faces are not implemented");
         if (g->geom.map) return set_error(EW_EUNSUPPORTED, "multigrid: mapped grids are not implemented");
+        if (g->prec == EW_FP32X2) return set_error(EW_EUNSUPPORTED, "multigrid: FP32 or FP64 grids only");
         nlev = mg_levels(g->geom, lv, 16);
         if (g->geom.n[1] > 65535 || g->geom.n[2] > 65535)
             return set_error(EW_EUNSUPPORTED, "multigrid: axes longer than 65535 points");

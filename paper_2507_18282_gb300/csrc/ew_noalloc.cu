@@ -96,6 +96,7 @@ extern "C" ew_status ew_filter_apply_noalloc(const ew_grid* grid, const ew_filte
     if (params->scheme != EW_EXPLICIT)
         return set_error(EW_EUNSUPPORTED, "ew_filter_apply_noalloc runs the explicit scheme only");
     if (grid->geom.map) return set_error(EW_EUNSUPPORTED, "ew_filter_apply_noalloc takes box grids only");
+    if (grid->prec == EW_FP32X2) return set_error(EW_EUNSUPPORTED, "ew_filter_apply_noalloc: FP32 or FP64 grids only");
     const size_t bytes = (size_t)grid->geom.N * (grid->prec == EW_FP32 ? 4 : 8);
     const char* a = (const char*)v_in;
     const char* b = (const char*)v_out;

@@ -38,8 +38,10 @@
 #include <algorithm>
 #include <cmath>
 #include <limits>
+#include <type_traits>
 #include <utility>
 
+#include "ew_dd.cuh"
 #include "ew_internal.h"
 #include "ew_stencil_dev.cuh"
 
@@ -71,7 +73,7 @@ Stencil<T> make_stencil(const GridGeom& g, double scale) {
         }
         tot += 2.0 * (fabs(a1[a]) + fabs(a2[a]));
     }
-    const int mant = std::numeric_limits<T>::digits;  // 24 or 53
+    const int mant = MantBits<T>::value;  // 24, 53, or 48 for double-FP32 pairs
     int e = 0;
     frexp(2.0 * tot, &e);                               // 2 tot < 2^e
     double q = ldexp(1.0, e - mant);                    // ulp of T just below 2^e
@@ -98,6 +100,7 @@ Stencil<T> make_stencil(const GridGeom& g, double scale) {
 }
 template Stencil<float> make_stencil<float>(const GridGeom&, double);
 template Stencil<double> make_stencil<double>(const GridGeom&, double);
+template Stencil<dd> make_stencil<dd>(const GridGeom&, double);
 
 
 template <typename T, int DIM, int ORDER>
@@ -387,7 +390,12 @@ template <typename T>
 ew_status explicit_wave_solve(const GridGeom& g, const FilterPlan& plan, const T* cdev, const T* vin, T* vout,
                               int nvec, T* fields, int temporal_block, cudaStream_t st) {
     if (temporal_block < 0) return set_error(EW_EINVAL, "temporal_block < 0");
-    if (g.map) return mapped_wave_solve<T>(g, plan, vin, vout, nvec, fields, st);  // one step per launch
+    if constexpr (std::is_same<T, dd>::value) {
+        // double-FP32 pairs: 2D boxes only (the blocked 2D, one-CTA and one-step kernels)
+        if (g.map || g.dim != 2) return set_error(EW_EUNSUPPORTED, "double-FP32 fields: 2D boxes only");
+    } else {
+        if (g.map) return mapped_wave_solve<T>(g, plan, vin, vout, nvec, fields, st);  // one step per launch
+    }
     if (use_resident<T>(g, nvec) && temporal_block == 0) return resident<T>(g, vin, vout, cdev, plan, nvec, st);
     // fields are laid out [field][vector][point]
     const int64_t fstride = field_stride(g.N);
@@ -396,25 +404,31 @@ ew_status explicit_wave_solve(const GridGeom& g, const FilterPlan& plan, const T
     const bool blocked = g.dim == 2 && temporal_block != 1;
     // the tuner writes the spare fields and the filter sum, so it runs before the first step
     if (blocked && temporal_block == 0) EW_TRY(tb2d_tune<T>(g, plan, cdev, F, vout, nvec, fstride, st));
-    if (g.dim == 3 && g.order == 2 && temporal_block == 0)
-        EW_TRY(tb3d_tune<T>(g, plan, cdev, F, vout, nvec, fstride, st));
+    if constexpr (!std::is_same<T, dd>::value)
+        if (g.dim == 3 && g.order == 2 && temporal_block == 0)
+            EW_TRY(tb3d_tune<T>(g, plan, cdev, F, vout, nvec, fstride, st));
     // F[0] = D^n, F[1] = W^n; the unblocked steps write W^{n+1} to F[2] and swap
     EW_TRY(first_step<T>(g, vin, F[0], F[1], vout, plan, nvec, fstride, st));
     if (blocked) {
         int prv = 0, cur = 1;
         return tb2d_advance<T>(g, plan, cdev, F, &prv, &cur, 1, vout, nvec, fstride, temporal_block, st);
     }
-    if (g.dim == 3 && g.order == 2 && temporal_block != 1) {
-        int prv = 0, cur = 1;
-        return tb3d_advance<T>(g, plan, cdev, F, &prv, &cur, 1, vout, nvec, fstride, temporal_block, st);
-    }
+    if constexpr (!std::is_same<T, dd>::value)
+        if (g.dim == 3 && g.order == 2 && temporal_block != 1) {
+            int prv = 0, cur = 1;
+            return tb3d_advance<T>(g, plan, cdev, F, &prv, &cur, 1, vout, nvec, fstride, temporal_block, st);
+        }
     Stencil<T> s = make_stencil<T>(g, plan.dt * plan.dt);
     int cur = 1, nxt = 2;
     for (int64_t L = 1; L < plan.Nt; ++L) {
-        if (g.dim == 3)
-            EW_TRY(step3d<T>(g, F[cur], F[0], F[nxt], vout, T(plan.cn(L + 1)), s, nvec, fstride, st));
-        else
-            EW_TRY(step_simple<T>(g, F[cur], F[0], F[nxt], vout, T(plan.cn(L + 1)), s, nvec, fstride, st));
+        if constexpr (!std::is_same<T, dd>::value) {
+            if (g.dim == 3) {
+                EW_TRY(step3d<T>(g, F[cur], F[0], F[nxt], vout, T(plan.cn(L + 1)), s, nvec, fstride, st));
+                std::swap(cur, nxt);
+                continue;
+            }
+        }
+        EW_TRY(step_simple<T>(g, F[cur], F[0], F[nxt], vout, T(plan.cn(L + 1)), s, nvec, fstride, st));
         std::swap(cur, nxt);
     }
     return EW_OK;
@@ -423,6 +437,8 @@ template ew_status explicit_wave_solve<float>(const GridGeom&, const FilterPlan&
                                               float*, int, float*, int, cudaStream_t);
 template ew_status explicit_wave_solve<double>(const GridGeom&, const FilterPlan&, const double*,
                                                const double*, double*, int, double*, int, cudaStream_t);
+template ew_status explicit_wave_solve<dd>(const GridGeom&, const FilterPlan&, const dd*,
+                                               const dd*, dd*, int, dd*, int, cudaStream_t);
 
 }  // namespace ew
 

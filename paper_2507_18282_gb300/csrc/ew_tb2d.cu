@@ -37,6 +37,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 
 #include "ew_internal.h"
 #include "ew_tb2d_dev.cuh"
@@ -126,6 +127,31 @@ const std::vector<Tb2dVariant>& tb2d_variants<double, 1>() {
     return v;
 }
 
+// double-FP32 pairs: ALU-bound like FP64, so shallow depths (few recomputed halo points)
+template <>
+const std::vector<Tb2dVariant>& tb2d_variants<dd, 2>() {
+    static const std::vector<Tb2dVariant> v = {
+        EW_TB2D_VARIANT(dd, 2, 2, 8, 8, 1, 1), EW_TB2D_VARIANT(dd, 2, 2, 8, 8, 2, 1),
+        EW_TB2D_VARIANT(dd, 2, 2, 8, 8, 3, 1), EW_TB2D_VARIANT(dd, 2, 2, 4, 8, 1, 2),
+        EW_TB2D_VARIANT(dd, 2, 2, 4, 8, 2, 2),
+    };
+    return v;
+}
+template <>
+const std::vector<Tb2dVariant>& tb2d_variants<dd, 1>() {
+    static const std::vector<Tb2dVariant> v = {
+        EW_TB2D_VARIANT(dd, 1, 2, 8, 8, 1, 1), EW_TB2D_VARIANT(dd, 1, 2, 8, 8, 2, 1),
+        EW_TB2D_VARIANT(dd, 1, 2, 8, 8, 4, 1), EW_TB2D_VARIANT(dd, 1, 2, 4, 8, 1, 2),
+        EW_TB2D_VARIANT(dd, 1, 2, 4, 8, 2, 2),
+    };
+    return v;
+}
+
+template <typename T>
+static const char* type_name() {
+    return sizeof(T) == 4 ? "fp32" : std::is_same<T, dd>::value ? "fp32x2" : "fp64";
+}
+
 template <typename T>
 static const std::vector<Tb2dVariant>& variants_for(int order) {
     return order == 2 ? tb2d_variants<T, 1>() : tb2d_variants<T, 2>();
@@ -192,7 +218,7 @@ static ew_status autotune(const GridGeom& g, T* const* F, T* acc, const T* cw, c
     }
     int dev = 0;
     EW_CUDA_TRY(cudaGetDevice(&dev));
-    TuneKey key{g.n[0], g.n[1], g.order, (int)sizeof(T), nvec, dev};
+    TuneKey key{g.n[0], g.n[1], g.order, MantBits<T>::value, nvec, dev};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -231,7 +257,7 @@ static ew_status autotune(const GridGeom& g, T* const* F, T* acc, const T* cw, c
         if (getenv("EW_TUNE_LOG"))
             fprintf(stderr, "[ew tune] %lldx%lld order %d %s: variant %zu (warps %dx%d, rows %d, depth %d, "
                             "minb %d, fence %d, tile %dx%d)%s: %.4f ms/step\n",
-                    (long long)g.n[0], (long long)g.n[1], g.order, sizeof(T) == 4 ? "fp32" : "fp64", i, var.nwx,
+                    (long long)g.n[0], (long long)g.n[1], g.order, type_name<T>(), i, var.nwx,
                     var.nty, var.ky, var.B, var.minb, var.fence, var.TX, var.TY, var.kind ? " register-blocked" : "",
                     1.0 / rate);
         if (rate > best_rate) {
@@ -260,6 +286,8 @@ ew_status tb2d_tune(const GridGeom& g, const FilterPlan& plan, const T* cdev, T*
 template ew_status tb2d_tune<float>(const GridGeom&, const FilterPlan&, const float*, float* const*, float*, int,
                                     int64_t, cudaStream_t);
 template ew_status tb2d_tune<double>(const GridGeom&, const FilterPlan&, const double*, double* const*, double*,
+                                     int, int64_t, cudaStream_t);
+template ew_status tb2d_tune<dd>(const GridGeom&, const FilterPlan&, const dd*, dd* const*, dd*,
                                      int, int64_t, cudaStream_t);
 
 // Advance the explicit scheme from level L (F[cur]) with F[prv] = level L-1
@@ -297,13 +325,15 @@ template ew_status tb2d_advance<float>(const GridGeom&, const FilterPlan&, const
                                        int64_t, float*, int, int64_t, int, cudaStream_t);
 template ew_status tb2d_advance<double>(const GridGeom&, const FilterPlan&, const double*, double* const*, int*,
                                         int*, int64_t, double*, int, int64_t, int, cudaStream_t);
+template ew_status tb2d_advance<dd>(const GridGeom&, const FilterPlan&, const dd*, dd* const*, int*,
+                                        int*, int64_t, dd*, int, int64_t, int, cudaStream_t);
 
 // description of the tuned choice (for reports)
 template <typename T>
 int tb2d_choice(const GridGeom& g, int nvec, int* B, int* TX, int* TY) {
     int dev = 0;
     cudaGetDevice(&dev);
-    TuneKey key{g.n[0], g.n[1], g.order, (int)sizeof(T), nvec, dev};
+    TuneKey key{g.n[0], g.n[1], g.order, MantBits<T>::value, nvec, dev};
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it == g_tune_cache.end()) return -1;
@@ -315,5 +345,6 @@ int tb2d_choice(const GridGeom& g, int nvec, int* B, int* TX, int* TY) {
 }
 template int tb2d_choice<float>(const GridGeom&, int, int*, int*, int*);
 template int tb2d_choice<double>(const GridGeom&, int, int*, int*, int*);
+template int tb2d_choice<dd>(const GridGeom&, int, int*, int*, int*);
 
 }  // namespace ew

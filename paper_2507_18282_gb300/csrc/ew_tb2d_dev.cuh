@@ -4,6 +4,7 @@
 #pragma once
 
 #include "ew_bc_dev.cuh"
+#include "ew_dd.cuh"
 #include "ew_internal.h"
 
 namespace ew {
@@ -57,6 +58,10 @@ template <>
 struct Vec2<double> {
     using type = double2;
 };
+template <>
+struct Vec2<dd> {
+    using type = dd2;
+};
 
 // Shape of one variant.  Each thread owns a PAIR of adjacent columns of the
 // compute region (8- or 16-byte shared-memory accesses) and KY rows.
@@ -104,6 +109,11 @@ __device__ __forceinline__ double2 p_fma(double2 a, double2 b, double2 c) {
     return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
 }
 __device__ __forceinline__ double s_add(double a, double b) { return __dadd_rn(a, b); }
+// double-FP32 pairs: the same operations in the pair arithmetic of ew_dd.cuh
+__device__ __forceinline__ dd2 p_add(dd2 a, dd2 b) { return dd2{dd_add(a.x, b.x), dd_add(a.y, b.y)}; }
+__device__ __forceinline__ dd2 p_mul(dd2 a, dd2 b) { return dd2{dd_mul(a.x, b.x), dd_mul(a.y, b.y)}; }
+__device__ __forceinline__ dd2 p_fma(dd2 a, dd2 b, dd2 c) { return dd2{dd_fma(a.x, b.x, c.x), dd_fma(a.y, b.y, c.y)}; }
+__device__ __forceinline__ dd s_add(dd a, dd b) { return dd_add(a, b); }
 
 // One tile (tile_x, tile_y) of one grid: b <= B steps.  Called by the
 // single-grid kernel below and by the batched persistent kernel.

@@ -135,3 +135,12 @@ def test_mapped_grid_creation_and_step_limit(ew):
     with pytest.raises(ew.EWError) as e:
         ew.ew_grid_create_mapped(n, bad)
     assert e.value.status == 1
+
+
+def test_pair_precision_is_two_dimensional(ew):
+    g = ew.ew_grid_create(2, (20, 30), (1.0, 1.5), order=4, prec="fp32x2")
+    assert g.size == 600
+    g.close()
+    with pytest.raises(ew.EWError) as e:
+        ew.ew_grid_create(3, (8, 8, 8), (1.0, 1.0, 1.0), prec="fp32x2")
+    assert e.value.status == 7
