@@ -3,18 +3,18 @@
 //
 // Why: on this part FP64 arithmetic runs at a small fraction of the FP32 rate,
 // so the FP64 filter applications of the mixed-precision eigen-solver are
-// bound by the FP64 units; the same wave-solve in pairs of FP32 numbers does
-// about 13 FP32 operations per FP64 one and runs on the full-rate FP32 pipes.
+// bound by the FP64 units; the same wave-solve in pairs of FP32 numbers costs
+// 11 FP32 operations per addition and 7 per product, on the full-rate FP32 pipes.
 //
 // The building blocks are the error-free transformations:
 //   two_sum(a, b):  s = fl(a + b) and the exact error e, a + b = s + e
 //                   (Knuth's branch-free form, six additions)
 //   fast_two_sum:   the same when |a| >= |b| (three additions)
 //   two_prod(a, b): p = fl(a b) and e = fma(a, b, -p), a b = p + e
-// and the pair operations built on them: addition carries both errors and
-// renormalises (the "accurate" form, whose error is bounded relative to the
-// result even under cancellation), multiplication adds the cross products to
-// the error of the leading product.  Every rounding is explicit (_rn
+// and the pair operations built on them: addition adds the trailing parts to
+// the error of the leading sum and renormalises (error bounded relative to the
+// operands), multiplication adds the cross products to the error of the
+// leading product.  Every rounding is explicit (_rn
 // intrinsics on the device), so no compiler contraction or reassociation can
 // change a result.
 #pragma once
@@ -62,13 +62,14 @@ __host__ __device__ __forceinline__ void two_prod(float a, float b, float& p, fl
     e = EW_DD_FMA(a, b, -p);
 }
 
+// addition: the error of the leading sum, plus the trailing parts, renormalised;
+// the error is bounded by a few 2^-48 (|x| + |y|) -- relative to the operands,
+// not to the sum, which is what the stencil sums need: their cancelling terms
+// are products that already carry errors of that size
 __host__ __device__ __forceinline__ dd dd_add(dd x, dd y) {
-    float s, e, t, f;
+    float s, e;
     two_sum(x.hi, y.hi, s, e);
-    two_sum(x.lo, y.lo, t, f);
-    e = EW_DD_ADD(e, t);
-    fast_two_sum(s, e, s, e);
-    e = EW_DD_ADD(e, f);
+    e = EW_DD_ADD(e, EW_DD_ADD(x.lo, y.lo));
     fast_two_sum(s, e, s, e);
     return dd(s, e);
 }
