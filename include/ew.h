@@ -108,7 +108,7 @@ void ew_grid_destroy(ew_grid* grid);
  *   xy_host     the (n1 + 2) x (n2 + 2) vertex coordinates, interleaved
  *               (x, y), r1 index fastest, boundary vertices included (host
  *               memory, read during the call and kept for the grid's life)
- *   prec        field precision
+ *   prec        field precision, EW_FP32 or EW_FP64 (EW_EUNSUPPORTED for EW_FP32X2)
  * The operator: J L u = d_r(A11 u_r + A12 u_s) + d_s(A12 u_r + A22 u_s) with
  * J = x_r y_s - x_s y_r, A11 = (x_s^2 + y_s^2)/J, A22 = (x_r^2 + y_r^2)/J,
  * A12 = -(x_r x_s + y_r y_s)/J from centred differences of the vertex
@@ -197,18 +197,19 @@ ew_status ew_filter_setup(const ew_grid* grid, const ew_filter_params* params,
  * order).  For N_p = 1, 2, 4, ..., max_periods, with the other fields of
  * params as given (omega, scheme, CFL or steps per period, adjust_omega), the
  * estimated cost N_p / (-ln CR) is evaluated from the exact discrete spectrum
- * of the box (tensor sine modes) and the cheapest N_p is written to
+ * of the box (tensor sine and cosine modes, by face kind) and the cheapest N_p is written to
  * *num_periods.  cr_host (may be NULL; capacity floor(log2(max_periods)) + 1)
  * receives CR for each candidate.  Host work only (no GPU, no stream).
- * EW_EUNSUPPORTED if no candidate gives CR < 1. */
+ * EW_EUNSUPPORTED if no candidate gives CR < 1, or for a curvilinear grid
+ * (its spectrum has no closed form). */
 ew_status ew_choose_num_periods(const ew_grid* grid, const ew_filter_params* params, int n_wanted,
                                 int krylov_dim, int max_periods, int* num_periods, double* cr_host);
 
 /* v_out = S v_in for each of `nvec` vectors: one wave-solve (Algorithm matVec
  * with the explicit or implicit scheme and the trapezoidal filter).  v_in and
- * v_out are device blocks of nvec vectors in the grid precision; they must not
- * overlap.  Scratch (a few fields per vector) is allocated on first use and
- * kept with the grid. */
+ * v_out are device blocks of nvec vectors in the grid precision (FP64 for
+ * EW_FP32X2 grids); they must not overlap.  Scratch (a few fields per vector)
+ * is allocated on first use and kept with the grid. */
 ew_status ew_filter_apply(const ew_grid* grid, const ew_filter_params* params, const void* v_in_dev,
                           void* v_out_dev, int nvec, cudaStream_t stream);
 

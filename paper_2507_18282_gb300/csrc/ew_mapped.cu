@@ -374,6 +374,7 @@ extern "C" ew_status ew_grid_create_mapped(const int64_t n_interior[2], const do
     clear_error();
     if (!out || !n_interior || !xy_host) return set_error(EW_EINVAL, "null argument");
     *out = nullptr;
+    if (prec == EW_FP32X2) return set_error(EW_EUNSUPPORTED, "mapped grids: FP32 or FP64 fields");
     if (prec != EW_FP32 && prec != EW_FP64) return set_error(EW_EINVAL, "bad precision");
     const int64_t n1 = n_interior[0], n2 = n_interior[1];
     if (n1 < 1 || n2 < 1) return set_error(EW_EINVAL, "n_interior must be >= 1");
