@@ -127,13 +127,16 @@ const std::vector<Tb2dVariant>& tb2d_variants<double, 1>() {
     return v;
 }
 
-// double-FP32 pairs: ALU-bound like FP64, so shallow depths (few recomputed halo points)
+// double-FP32 pairs: ALU-bound, yet on 2047 x 3071 depths 2-3 beat depth 1 (which moves 48 B per
+// point and step); the tuner picks among depths 1-5
 template <>
 const std::vector<Tb2dVariant>& tb2d_variants<dd, 2>() {
     static const std::vector<Tb2dVariant> v = {
         EW_TB2D_VARIANT(dd, 2, 2, 8, 8, 1, 1), EW_TB2D_VARIANT(dd, 2, 2, 8, 8, 2, 1),
         EW_TB2D_VARIANT(dd, 2, 2, 8, 8, 3, 1), EW_TB2D_VARIANT(dd, 2, 2, 4, 8, 1, 2),
-        EW_TB2D_VARIANT(dd, 2, 2, 4, 8, 2, 2),
+        EW_TB2D_VARIANT(dd, 2, 2, 4, 8, 2, 2), EW_TB2D_VARIANT(dd, 2, 2, 8, 8, 4, 1),
+        EW_TB2D_VARIANT(dd, 2, 2, 8, 8, 5, 1), EW_TB2D_VARIANT(dd, 2, 2, 4, 8, 3, 2),
+        EW_TB2D_VARIANT(dd, 2, 2, 4, 8, 4, 2),
     };
     return v;
 }
