@@ -303,7 +303,9 @@ typedef struct {
                                  per vector gives the exact relation S X = X Theta + E, span[X, E] is
                                  extended by p FP32 block expansions and Rayleigh-Ritz with S picks the
                                  new X.  p = 6 and g = n_wanted where they fit ((p + 2)(n_wanted + g)
-                                 <= 128 basis columns), fewer for large n_wanted (n_wanted <= 23).
+                                 <= 128 basis columns), fewer for large n_wanted (n_wanted <= 23); after
+                                 the first outer step p is sized by the contraction the last step
+                                 achieved (taken as geometric in p) for a 10x margin below refine_tol.
                               2: a second Krylov-Schur run with FP64 full-filter wave-solves started
                                  from the FP32 vectors (block n_wanted, basis 3 n_wanted)
                               3: as 1, with the images S X of each outer step computed in double-FP32

@@ -531,6 +531,7 @@ static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, ew_grid* gimg, in
     *outer_done = 0;
     if (!gimg) gimg = g64;
     double prev_worst = INFINITY;
+    int p_step = p;  // FP32 block expansions of the current outer step
     for (int outer = 0; outer < max_outer; ++outer) {
         double worst = 0.0;
         EW_TRY(lrr_check(&worst));
@@ -538,6 +539,12 @@ static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, ew_grid* gimg, in
         if (gimg != g64 && worst > 0.1 * prev_worst) {
             gimg = g64;
             if (getenv("EW_KS_LOG")) fprintf(stderr, "[ew refine] images in FP64 from here on\n");
+        }
+        // size the expansions by the contraction the last step achieved with p_step of
+        // them, taken as geometric in their number, for 10x below the target
+        if (prev_worst < INFINITY && worst < prev_worst) {
+            const double got = log(prev_worst / worst), need = log(10.0 * worst / res_tol);
+            if (need < got) p_step = std::max(2, std::min(p, (int)ceil(p_step * need / got)));
         }
         prev_worst = worst;
         // image of X at FP64 accuracy: S X = X Theta + E
@@ -586,7 +593,7 @@ static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, ew_grid* gimg, in
         for (int i = 0; i < r; ++i)
             for (int j = 0; j < nw; ++j) kr.h(nw + i, j) = R[(size_t)i * nw + j];
         kr.mcur = nw;
-        for (int e = 0; e < p; ++e) {
+        for (int e = 0; e < p_step; ++e) {
             const int col0 = kr.mcur;  // S is applied to V[:, col0 : col0 + nw] in this expansion
             EW_TRY(kr.expand());
             // S is symmetric, so X^T S Q_e = (S X)^T Q_e = (X Theta + Q_1 R)^T Q_e, known
