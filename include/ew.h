@@ -377,7 +377,7 @@ ew_status ew_smoother_backward(const ew_grid* grid, const float* weights_dev, co
  * first three V-cycles); each of `steps` Adam steps minimises
  *   1/2 ||M (e - N(r))||^2 = 1/2 ||r - M N(r)||^2    (M e = r)
  * over one sample, with the library's forward and backward kernels.  Plain
- * multigrid judges the result: the convergence factors of V(pre, post) cycles
+ * multigrid decides whether to accept the result: the convergence factors of V(pre, post) cycles
  * with the Jacobi smoother and with the learned one on the finest level are
  * measured on the same system, and the weights are kept only if the learned
  * factor is lower (else weights_dev is restored: plain-multigrid fallback).
@@ -386,10 +386,10 @@ typedef struct {
     int steps;             /* Adam steps */
     int samples;           /* residual samples kept on the device */
     double lr;             /* Adam learning rate */
-    int pre, post;         /* V-cycle shape of the sample generation and of the judgement */
+    int pre, post;         /* V-cycle shape of the sample generation and of the acceptance test */
     double jacobi_weight;  /* plain smoother weight (0: 0.8) */
     uint64_t seed;         /* right-hand sides: SplitMix64 streams seed, seed + 1, ... */
-    int judge_cycles;      /* V-cycles per convergence-factor measurement (0: 6) */
+    int accept_cycles;     /* V-cycles per convergence-factor measurement (0: 6) */
 } ew_train_params;
 typedef struct {
     double loss_first, loss_last;    /* training loss of the first and the last step */

@@ -268,12 +268,12 @@ def ew_smoother_backward(grid: Grid, weights, r, gy, grad, stream=None):
 
 
 def ew_smoother_train(grid: Grid, half_dt2, weights, steps=200, samples=6, lr=1e-3, pre=2, post=2,
-                      jacobi_weight=0.8, seed=1, judge_cycles=6, stream=None):
+                      jacobi_weight=0.8, seed=1, accept_cycles=6, stream=None):
     """Train the learned smoother in place (weights: 432 FP32 CUDA tensor).
     Returns the report as a dict."""
     import torch
     tp = _lib.ew_train_params(int(steps), int(samples), float(lr), int(pre), int(post), float(jacobi_weight),
-                              int(seed), int(judge_cycles))
+                              int(seed), int(accept_cycles))
     rep = _lib.ew_train_report()
     check(lib.ew_smoother_train(grid.handle, float(half_dt2), ctypes.byref(tp), _ptr(weights, torch.float32, 432),
                                 ctypes.byref(rep), _stream(stream)))

@@ -81,7 +81,7 @@ class ew_eigs_report(ctypes.Structure):
 class ew_train_params(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("samples", ctypes.c_int), ("lr", ctypes.c_double),
                 ("pre", ctypes.c_int), ("post", ctypes.c_int), ("jacobi_weight", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("judge_cycles", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("accept_cycles", ctypes.c_int)]
 
 
 class ew_train_report(ctypes.Structure):

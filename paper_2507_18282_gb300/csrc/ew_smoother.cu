@@ -606,10 +606,10 @@ ew_status ew_smoother_train(const ew_grid* grid, double half_dt2, const ew_train
         if (step < tp->samples) loss_first += 0.5 * l2 / rn2[ks] / std::min(tp->samples, tp->steps);
         if (step >= tp->steps - tp->samples) loss_last += 0.5 * l2 / rn2[ks] / std::min(tp->samples, tp->steps);
     }
-    // (3) judge: convergence factor of plain and learned V-cycles on the same
+    // (3) acceptance: convergence factor of plain and learned V-cycles on the same
     //     system.  The correction is linear in W2, so scaling W2 by s scales
-    //     N by s; a few scalings are judged and the best one is kept.
-    const int jc = tp->judge_cycles > 0 ? tp->judge_cycles : 6;
+    //     N by s; a few scalings are compared and the best one is kept.
+    const int jc = tp->accept_cycles > 0 ? tp->accept_cycles : 6;
     double rho_plain = 0.0, rho_learned = INFINITY;
     if (s == EW_OK) s = mg_convergence(g, a, &plain, jc, tp->seed + 99, &rho_plain, st);
     std::vector<float> hw(2 * kW), hbest(2 * kW);

@@ -165,7 +165,7 @@ def test_smoother_backward_parity(ew):
 def test_learned_smoother_beats_plain_multigrid(ew):
     """The learned smoother, trained on the GPU on residuals from plain-MG
     solves of the 255^3 order-4 implicit system, lowers the V(2,2) convergence
-    factor below plain damped-Jacobi multigrid on the same system (the judge
+    factor below plain damped-Jacobi multigrid on the same system (the acceptance test
     built into the trainer); otherwise the trainer keeps plain multigrid."""
     n = (255, 255, 255)
     g = ew.ew_grid_create(3, n, (1.0, 1.0, 1.0), order=4, prec="fp32")
