@@ -66,8 +66,10 @@ def parse():
                                            "mgtol", "mapped2d"],
                     default="rect2d",
                     help="rect2d is the headline line; the others print their own line")
-    ap.add_argument("--eigs-arm", choices=["both", "fp32_fp64", "fp32_pair", "plain"], default="both",
-                    help="eigs2d: every arm (default) or one")
+    ap.add_argument("--eigs-arm", choices=["pair_and_plain", "fp32_fp64", "fp32_pair", "plain"],
+                    default="pair_and_plain",
+                    help="eigs2d: the mixed arm with pair-arithmetic images and the plain FP64 arm (default), "
+                         "or one arm")
     ap.add_argument("--num-periods", type=int, default=0,
                     help="N_p of the eigs2d workload (0: the library's choice, ew_choose_num_periods)")
     return ap.parse_args()
@@ -635,10 +637,10 @@ def run_extra(args):
         # the plain arm stops on the Ritz residual of S: 2e-11 brings every eig-res below 1e-8
         arms = [("fp32_fp64_refine", "fp32", 1, 0.0), ("fp32_pair_refine", "fp32", 3, 0.0),
                 ("plain_fp64", "fp64", 0, 2e-11)]
-        if args.eigs_arm != "both":
-            arms = [a for a in arms if a[0].startswith(args.eigs_arm)]
-        else:  # the default run: the pair-arithmetic mixed arm against plain FP64
+        if args.eigs_arm == "pair_and_plain":
             arms = [a for a in arms if a[0] != "fp32_fp64_refine"]
+        else:
+            arms = [a for a in arms if a[0].startswith(args.eigs_arm)]
         for name, prec, refine, tol in arms:
             g = ew.ew_grid_create(2, n, L, order=4, prec=prec)
             p = ew.filter_params(150.0, num_periods=num_periods)

@@ -238,8 +238,8 @@ static ew_status filter_apply_dd(ew_grid* g, const ew_filter_params* p, const Fi
     const dd* cdev = nullptr;
     EW_TRY(upload_weights<dd>(g, plan, st, &cdev));
     EW_TRY(g->fields.reserve((size_t)4 * nvec * field_stride(g->geom.N) * sizeof(dd)));
-    EW_TRY(g->mg.reserve((size_t)2 * n * sizeof(dd)));
-    dd* din = (dd*)g->mg.ptr;
+    EW_TRY(g->pairs.reserve((size_t)2 * n * sizeof(dd)));
+    dd* din = (dd*)g->pairs.ptr;
     dd* dout = din + n;
     k_to_dd<<<kReduceBlocks * 4, 256, 0, st>>>(vin, din, n);
     EW_CUDA_TRY(cudaGetLastError());
@@ -362,6 +362,7 @@ void ew_grid_destroy(ew_grid* g) {
     g->reduce.release();
     g->misc.release();
     g->mg.release();
+    g->pairs.release();
     g->mgh.release();
     if (g->host_pinned) cudaFreeHost(g->host_pinned);
     delete g;

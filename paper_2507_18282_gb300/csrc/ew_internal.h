@@ -112,6 +112,7 @@ struct ew_grid {
     ew::Scratch misc;      // small device tables (filter weights)
     ew::Scratch mg;        // power-iteration iterate
     ew::Scratch mgh;       // multigrid hierarchy
+    ew::Scratch pairs;     // EW_FP32X2 grids: the input and output vectors as double-FP32 pairs
     void* host_pinned = nullptr;  // small pinned staging for reductions
     size_t host_pinned_bytes = 0;
 };
