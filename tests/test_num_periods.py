@@ -92,3 +92,15 @@ def test_rejects_bad_requests(ew):
         with pytest.raises(ew.EWError):
             ew.ew_choose_num_periods(g, p, *args, max_periods=8)
     g.close()
+
+
+def test_refuses_curvilinear_grids(ew):
+    """A mapped grid's spectrum has no closed form: the estimate is refused
+    (host work only, no GPU)."""
+    import ew_inputs
+    n = (20, 15)
+    g = ew.ew_grid_create_mapped(n, ew_inputs.mapped_vertices(*n, "square_warp"), prec="fp32")
+    with pytest.raises(ew.EWError) as e:
+        ew.ew_choose_num_periods(g, ew.filter_params(10.0), 4, 12, max_periods=8)
+    assert e.value.status == 7
+    g.close()
