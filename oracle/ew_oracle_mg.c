@@ -14,8 +14,12 @@
  *     even n; the coarsest system is solved by CG to 1e-14;
  *   - smoother: damped Jacobi x += wJ (b - M x) / D with the constant interior
  *     diagonal D = 1 + a sum_i d0 / h_i^2, d0 = 2 (order 2) or 5/2 (order 4);
- *     or, on the finest `nlev_learned` levels, the learned correction
- *     x += N(b - M x);
+ *     or, for the second-order stencil, red-black Gauss-Seidel (one of the
+ *     smoothers the paper names): each sweep updates first the points with
+ *     i + j + k even, then the others, each by x += (b - M x) / D with the
+ *     current values (the neighbours of a point are of the other colour, so
+ *     a colour's updates are independent); or, on the finest `nlev_learned`
+ *     levels, the learned correction x += N(b - M x);
  *   - restriction: full weighting, the tensor product of (1/4, 1/2, 1/4);
  *   - prolongation: (multi)linear interpolation, zero on the boundary.
  *
@@ -244,7 +248,7 @@ int og_conv_net_backward(const long* n, const double* w, const double* r, const 
 }
 
 typedef struct {
-    int dim, order, nlev, nu1, nu2, nlearn;
+    int dim, order, nlev, nu1, nu2, nlearn, red_black;
     double a, wJ;
     og_level lv[OG_MAX_LEVELS];
     const double* net; /* nlearn x (2 * OG_NET_W) */
@@ -256,9 +260,33 @@ static double og_jacobi_diag(const og_mg* m, const og_level* l) {
     return 1.0 + m->a * s;
 }
 
+/* (M x)_q = x_q - a sum_i (x(q - e_i) - 2 x_q + x(q + e_i)) / h_i^2 at point
+ * (i, j, k) of the second-order system, zero beyond the box */
+static double og_Mx_point2(const og_mg* m, const og_level* l, const double* x, long i, long j, long k) {
+    const long* n = l->n;
+    double xc = og_get(n, x, i, j, k), s = 0.0;
+    s += (og_get(n, x, i - 1, j, k) - 2.0 * xc + og_get(n, x, i + 1, j, k)) / (l->h[0] * l->h[0]);
+    s += (og_get(n, x, i, j - 1, k) - 2.0 * xc + og_get(n, x, i, j + 1, k)) / (l->h[1] * l->h[1]);
+    if (m->dim == 3) s += (og_get(n, x, i, j, k - 1) - 2.0 * xc + og_get(n, x, i, j, k + 1)) / (l->h[2] * l->h[2]);
+    return xc - m->a * s;
+}
+
 static void og_smooth(const og_mg* m, int L, const double* b, double* x, double* r, int nu) {
     const og_level* l = &m->lv[L];
     double D = og_jacobi_diag(m, l);
+    if (m->red_black && L >= m->nlearn) {
+        const long* n = l->n;
+        for (int s = 0; s < nu; ++s)
+            for (int colour = 0; colour < 2; ++colour)
+                for (long k = 0; k < n[2]; ++k)
+                    for (long j = 0; j < n[1]; ++j)
+                        for (long i = 0; i < n[0]; ++i) {
+                            if (((i + j + k) & 1) != colour) continue;
+                            long q = og_idx3(n, i, j, k);
+                            x[q] += (b[q] - og_Mx_point2(m, l, x, i, j, k)) / D;
+                        }
+        return;
+    }
     double* corr = NULL;
     if (L < m->nlearn) corr = (double*)malloc(sizeof(double) * (size_t)l->size);
     for (int s = 0; s < nu; ++s) {
@@ -302,15 +330,18 @@ static double og_norm2(long N, const double* v) {
     return sqrt(s);
 }
 
-/* `ncycles` V(nu1, nu2) cycles on M x = b starting from the x passed in.
+/* `ncycles` V(nu1, nu2) cycles on M x = b starting from the x passed in
+ * (red_black: the red-black Gauss-Seidel smoother instead of damped Jacobi).
  * res_hist (ncycles + 1 entries, may be NULL) receives ||b - M x||_2 before
  * the first and after every cycle.  Returns the number of levels, < 0 on bad
  * arguments. */
 int og_mg_solve(int dim, const long* n, const double* h, int order, double a, const double* b,
                 double* x, int nu1, int nu2, double wJ, int ncycles, const double* net_w,
-                int nlev_learned, double* res_hist) {
+                int nlev_learned, double* res_hist, int red_black) {
     og_mg m;
     if ((dim != 2 && dim != 3) || (order != 2 && order != 4) || ncycles < 0) return -1;
+    if (red_black && order != 2) return -1; /* the wide stencil couples points of one colour */
+    m.red_black = red_black;
     if (net_w && nlev_learned > 0 && dim != 3) return -1;
     m.dim = dim;
     m.order = order;

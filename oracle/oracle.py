@@ -60,7 +60,7 @@ def _load():
             lib.og_filter_explicit.argtypes = [i, lp, dp, i, ip, l, d, dp, dp, dp]
             lib.og_filter_implicit.argtypes = [i, lp, dp, i, l, d, dp, dp, dp, d]
             lib.og_cg_solve_M.argtypes = [i, lp, dp, i, d, dp, dp, d, i]
-            lib.og_mg_solve.argtypes = [i, lp, dp, i, d, dp, dp, i, i, d, i, dp, i, dp]
+            lib.og_mg_solve.argtypes = [i, lp, dp, i, d, dp, dp, i, i, d, i, dp, i, dp, i]
             lib.og_mapped_apply_L.argtypes = [l, l, dp, dp, dp]
             lib.og_mapped_jacobian.argtypes = [l, l, dp, dp]
             lib.og_mapped_filter_explicit.argtypes = [l, l, dp, l, d, dp, dp, dp]
@@ -514,11 +514,12 @@ def eigenspace_distance(v, basis):
 NET_WEIGHTS = 2 * 8 * 27   # [W1 (8 x 27) | W2 (8 x 27)], taps (dz, dy, dx), dz slowest
 
 
-def mg_solve(g: Grid, a, b, x0=None, nu1=2, nu2=2, wJ=0.8, ncycles=1, net=None):
+def mg_solve(g: Grid, a, b, x0=None, nu1=2, nu2=2, wJ=0.8, ncycles=1, net=None, red_black=False):
     """``ncycles`` multigrid V(nu1, nu2) cycles on (I - a L_h) x = b (eq. impMatrix).
 
-    The cycle (Jacobi or learned smoother, full weighting, linear
-    interpolation, CG on the coarsest level) is spelled out in ew_oracle_mg.c.
+    The cycle (Jacobi, red-black Gauss-Seidel (order 2) or learned smoother,
+    full weighting, linear interpolation, CG on the coarsest level) is spelled
+    out in ew_oracle_mg.c.
     ``net`` is None or an array (levels x NET_WEIGHTS) of learned-smoother
     weights for the finest levels.  Returns (x, residual 2-norm history)."""
     g.dirichlet_only()
@@ -532,7 +533,7 @@ def mg_solve(g: Grid, a, b, x0=None, nu1=2, nu2=2, wJ=0.8, ncycles=1, net=None):
         netp, nl = _dp(net), net.shape[0]
     nlev = _load().og_mg_solve(g.dim, g._n3, g._h3, g.order, float(a), _dp(b), _dp(x),
                                int(nu1), int(nu2), float(wJ), int(ncycles), netp, int(nl),
-                               _dp(hist))
+                               _dp(hist), int(bool(red_black)))
     assert nlev > 0
     return x, hist
 
