@@ -140,6 +140,10 @@ typedef struct {
     const float* weights_dev; /* learned weights, learned_levels x 432 FP32 values (device), each
                                  rounded to BF16 by the kernels; layout [W1 8x27 | W2 8x27],
                                  taps (dz,dy,dx) with dz slowest */
+    int red_black;            /* 1: red-black Gauss-Seidel smoothing instead of damped Jacobi on the
+                                 non-learned levels: each sweep updates the points with i + j + k
+                                 even, then the others, by x += (b - M x) / M_ii; second-order
+                                 grids only (EW_EINVAL otherwise) */
 } ew_mg_params;
 
 /* Filter parameters (Section "Discrete approximations").

@@ -120,9 +120,10 @@ def ew_grid_destroy(grid: Grid):
     grid.close()
 
 
-def mg_params(pre=2, post=2, max_cycles=1, rtol=0.0, jacobi_weight=0.8, learned_levels=0, weights=None):
+def mg_params(pre=2, post=2, max_cycles=1, rtol=0.0, jacobi_weight=0.8, learned_levels=0, weights=None,
+              red_black=False):
     m = ew_mg_params(pre, post, max_cycles, rtol, jacobi_weight, learned_levels,
-                     ctypes.c_void_p(weights.data_ptr()) if weights is not None else None)
+                     ctypes.c_void_p(weights.data_ptr()) if weights is not None else None, int(bool(red_black)))
     m._keep = weights
     return m
 

@@ -97,6 +97,21 @@ __global__ void k_mg_jacobi(int64_t nx, int64_t ny, int64_t nz, const T* __restr
     xo[q] = x[q] + wd * r;
 }
 
+// red-black Gauss-Seidel, second order, in place: the points of one colour
+// ((i + j + k) & 1 == colour) take x += (b - M x) * inv_d, M_ii = 1 / inv_d;
+// their neighbours are all of the other colour, so the colour's updates are
+// independent and the sweep is exact Gauss-Seidel in red-black order
+template <typename T, int DIM>
+__global__ void k_mg_rbgs(int64_t nx, int64_t ny, int64_t nz, T* __restrict__ x, const T* __restrict__ b,
+                          Stencil<T> sa, T inv_d, int colour) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    const int64_t j = blockIdx.y, k = blockIdx.z, q = (k * ny + j) * nx + i;
+    if (((i + j + k) & 1) != colour) return;
+    const T r = (b[q] - x[q]) + lap_global<T, DIM, 2>(x, sa, q, i, j, k, nx, ny, nz);
+    x[q] = x[q] + inv_d * r;
+}
+
 template <typename T>
 __device__ __forceinline__ T get0(const T* __restrict__ v, int64_t i, int64_t j, int64_t k, int64_t nx, int64_t ny,
                                   int64_t nz) {
@@ -263,6 +278,8 @@ struct MGSolver {
         if (g->geom.bc)
             return set_error(EW_EUNSUPPORTED, "multigrid: boxes with Neumann faces are not implemented");
         if (g->geom.map) return set_error(EW_EUNSUPPORTED, "multigrid: mapped grids are not implemented");
+        if (params->red_black && g->geom.order != 2)
+            return set_error(EW_EINVAL, "red-black smoothing needs the second-order stencil");
         if (g->prec == EW_FP32X2) return set_error(EW_EUNSUPPORTED, "multigrid: FP32 or FP64 grids only");
         nlev = mg_levels(g->geom, lv, 16);
         if (g->geom.n[1] > 65535 || g->geom.n[2] > 65535)
@@ -312,6 +329,20 @@ struct MGSolver {
             if (L < p->learned_levels) {
                 EW_MG_DISPATCH(k_mg_resid, lv[L], X[L], B[L], R[L], sa);
                 EW_TRY(smoother_apply<T>(lv[L], p->weights_dev + (size_t)L * 432, R[L], X[L], st));
+            } else if (p->red_black) {
+                // M_ii = 1 - c0 of the stored (consistent) stencil of a L_h
+                const T inv_d = (T)(1.0 / (1.0 - (double)sa.c0));
+                const GridGeom& g_ = lv[L];
+                const int nz_ = g_.dim == 3 ? (int)g_.n[2] : 1;
+                dim3 grid_ = pt_grid(g_.n[0], g_.n[1], nz_), blk_(pt_threads(g_.n[0]));
+                for (int colour = 0; colour < 2; ++colour) {
+                    if (g_.dim == 2)
+                        k_mg_rbgs<T, 2><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], 1, X[L], B[L], sa, inv_d, colour);
+                    else
+                        k_mg_rbgs<T, 3><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], g_.n[2], X[L], B[L], sa, inv_d,
+                                                               colour);
+                    count_launch();
+                }
             } else {
                 T wd = (T)(wJ / diag(L));
                 EW_MG_DISPATCH(k_mg_jacobi, lv[L], X[L], B[L], Tm[L], sa, wd);
@@ -426,6 +457,7 @@ static ew_status check_mg(const ew_mg_params* mg) {
     if (mg->pre < 0 || mg->post < 0 || mg->pre + mg->post < 1) return set_error(EW_EINVAL, "bad smoothing counts");
     if (mg->max_cycles < 1) return set_error(EW_EINVAL, "max_cycles must be >= 1");
     if (mg->learned_levels < 0) return set_error(EW_EINVAL, "learned_levels < 0");
+    if (mg->red_black != 0 && mg->red_black != 1) return set_error(EW_EINVAL, "red_black must be 0 or 1");
     return EW_OK;
 }
 
