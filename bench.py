@@ -84,6 +84,22 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks (the slowest replica's time); x itself at one rank."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, total_ms):
+    """Whole-job Gcell-steps/s: every replica's cell-steps over the slowest replica's time."""
+    return world * units_per_rank / (total_ms / 1e3) / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -281,11 +297,8 @@ def run_ours(args):
     clk = clocks.stop()
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
     barrier()
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * N * Nt * args.steps / (total_ms / 1e3) / 1e9
+    total_ms = max_over_ranks(total_ms, world, "cuda")
+    value = whole_job_rate(world, N * Nt * args.steps, total_ms)
 
     # ---- end to end through the C ABI from pinned host buffers ------------------
     h_in = torch.from_numpy(v_host).pin_memory()
@@ -309,10 +322,8 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = world * N * Nt * args.steps / (float(t.item()) / 1e3) / 1e9
+    e2e_ms = max_over_ranks(e2e_ms, world, "cuda")
+    e2e_value = whole_job_rate(world, N * Nt * args.steps, e2e_ms)
     # sanity: the result is finite and nonzero
     outn = float(h_out.abs().max())
     assert np.isfinite(outn) and outn > 0.0
