@@ -29,7 +29,8 @@
  *    Dirichlet faces; with a Neumann face they carry the trapezoid weights
  *    (the discrete L_2 inner product of eq. discreteRayleighQuotient).
  *  - Errors: every call returns an ew_status; on failure ew_last_error()
- *    returns a message for the calling thread.  No exception crosses the ABI.
+ *    returns a message for the calling thread.  No exception crosses the ABI:
+ *    a failed host allocation inside a call returns EW_ENOMEM.
  *    Device-side waits are bounded and report EW_ETIMEOUT.  A wave-solve
  *    returns before its kernels run, so a wait that gave up there is reported
  *    by the next call that synchronises (the autotuner, ew_rayleigh and the
@@ -149,7 +150,8 @@ typedef struct {
 /* Filter parameters (Section "Discrete approximations").
  *   omega             target frequency (> 0)
  *   num_periods       N_p >= 1; T_f = N_p 2 pi / omega
- *   steps_per_period  N_its; N_t = N_p * N_its, dt = T_f / N_t.  0 = derive
+ *   steps_per_period  N_its; N_t = N_p * N_its <= 2^31 - 2 (EW_EINVAL beyond),
+ *                     dt = T_f / N_t.  0 = derive
  *                     from `cfl` (explicit only): the smallest N_its with
  *                     dt <= cfl * 2 / sqrt(rho(-L_h)), rho the largest
  *                     eigenvalue of -L_h (4 sum 1/h^2, or 16/3 sum 1/h^2)
@@ -203,7 +205,10 @@ ew_status ew_filter_setup(const ew_grid* grid, const ew_filter_params* params,
  * estimated cost N_p / (-ln CR) is evaluated from the exact discrete spectrum
  * of the box (tensor sine and cosine modes, by face kind) and the cheapest N_p is written to
  * *num_periods.  cr_host (may be NULL; capacity floor(log2(max_periods)) + 1)
- * receives CR for each candidate.  Host work only (no GPU, no stream).
+ * receives CR for each candidate; a candidate is skipped (CR = 1), with all
+ * longer ones, once its N_t would pass 2^31 - 2 or (N_t + 1)(krylov_dim + 1)
+ * would pass 4e9 (the cost of the estimate: a sum over the N_t + 1 filter
+ * weights per eigenvalue).  Host work only (no GPU, no stream).
  * EW_EUNSUPPORTED if no candidate gives CR < 1, or for a curvilinear grid
  * (its spectrum has no closed form). */
 ew_status ew_choose_num_periods(const ew_grid* grid, const ew_filter_params* params, int n_wanted,

@@ -649,7 +649,7 @@ using namespace ew;
 
 extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params* params,
                                      const ew_eigs_params* ep, const double* start_dev, double* lambda_host,
-                                     double* vecs_dev, ew_eigs_report* rep, cudaStream_t st) {
+                                     double* vecs_dev, ew_eigs_report* rep, cudaStream_t st) try {
     clear_error();
     auto t0 = std::chrono::steady_clock::now();
     if (!grid || !params || !ep || !lambda_host) return set_error(EW_EINVAL, "null argument");
@@ -823,4 +823,6 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
     r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (rep) *rep = r;
     return status;
+} catch (...) {
+    return abi_exception();
 }

@@ -342,7 +342,7 @@ using namespace ew;
 
 extern "C" ew_status ew_filter_apply_batched(int nprob, const ew_grid* const* grids, const ew_filter_params* params,
                                              const void* const* v_in, void* const* v_out, const int* nvec,
-                                             cudaStream_t stream) {
+                                             cudaStream_t stream) try {
     clear_error();
     if (nprob < 1 || !grids || !params || !v_in || !v_out) return set_error(EW_EINVAL, "bad arguments");
     int dev = -1;
@@ -380,4 +380,6 @@ extern "C" ew_status ew_filter_apply_batched(int nprob, const ew_grid* const* gr
     }
     if (g0->prec == EW_FP32) return batched_t<float>(P, g0->geom.order, stream);
     return batched_t<double>(P, g0->geom.order, stream);
+} catch (...) {
+    return abi_exception();
 }

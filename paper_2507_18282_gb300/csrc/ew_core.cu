@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <mutex>
+#include <new>
+#include <stdexcept>
 #include <utility>
 #include <vector>
 #include <cstring>
@@ -94,6 +96,20 @@ ew_status cuda_error(cudaError_t e, const char* what) {
 }
 void clear_error() { g_last_error.clear(); }
 
+ew_status abi_exception() {
+    try {
+        throw;
+    } catch (const std::bad_alloc&) {
+        return set_error(EW_ENOMEM, "host allocation failed");
+    } catch (const std::length_error& e) {
+        return set_error(EW_ENOMEM, std::string("host container too large: ") + e.what());
+    } catch (const std::exception& e) {
+        return set_error(EW_EINVAL, std::string("host exception: ") + e.what());
+    } catch (...) {
+        return set_error(EW_EINVAL, "unknown host exception");
+    }
+}
+
 ew_status Scratch::reserve(size_t want) {
     if (want <= bytes) return EW_OK;
     if (ptr) cudaFree(ptr);
@@ -114,6 +130,9 @@ void Scratch::release() {
     ptr = nullptr;
     bytes = 0;
 }
+
+// Longest wave-solve: N_t (and with it the N_t + 1 filter weights) stays below 2^31 - 1.
+static constexpr int64_t kMaxSteps = INT32_MAX - 1;
 
 // Largest eigenvalue of -L_h: the 1D symbols 4 s (order 2) and 4 s + (4/3) s^2
 // (order 4) at s = sin^2 = 1, summed over the axes.
@@ -137,10 +156,14 @@ ew_status plan_filter(const GridGeom& g, const ew_filter_params* p, FilterPlan* 
         double cfl = p->cfl > 0.0 ? p->cfl : 0.8;
         double dtmax = 2.0 / sqrt(rho_bound(g));
         double period = 2.0 * M_PI / p->omega;
-        spp = (int)ceil(period / (cfl * dtmax) - 1e-12);
-        if (spp < 1) spp = 1;
+        double want = ceil(period / (cfl * dtmax) - 1e-12);
+        if (!(want <= (double)kMaxSteps))
+            return set_error(EW_EINVAL, "omega too small for this grid: more than 2^31 - 2 steps per period");
+        spp = want < 1.0 ? 1 : (int)want;
     }
     if (spp < 2) return set_error(EW_EINVAL, "need at least 2 steps per period");
+    if ((int64_t)p->num_periods * spp > kMaxSteps)
+        return set_error(EW_EINVAL, "N_t = num_periods * steps_per_period exceeds 2^31 - 2");
     double w = p->omega;
     if (p->adjust_omega) {
         // omega~ = (omega pi / N_its) sqrt((1 - 2 sin^2(pi/N_its)) / sin^2(pi/N_its))  (eq. adjustedOmega)
@@ -266,7 +289,7 @@ extern "C" {
 
 const char* ew_last_error(void) { return g_last_error.c_str(); }
 
-ew_status ew_profile_enable(int on) {
+ew_status ew_profile_enable(int on) try {
     clear_error();
     std::lock_guard<std::mutex> lk(g_prof_mu);
     for (auto& pr : g_fused_events) {
@@ -275,9 +298,11 @@ ew_status ew_profile_enable(int on) {
     profile_reset_locked();
     g_profile_on = on != 0;
     return EW_OK;
+} catch (...) {
+    return abi_exception();
 }
 
-ew_status ew_profile_read(ew_profile* out) {
+ew_status ew_profile_read(ew_profile* out) try {
     clear_error();
     if (!out) return set_error(EW_EINVAL, "null pointer");
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -297,10 +322,12 @@ ew_status ew_profile_read(ew_profile* out) {
     out->mg_solves = g_mg_solves;
     profile_reset_locked();
     return EW_OK;
+} catch (...) {
+    return abi_exception();
 }
 
 ew_status ew_grid_create(int dim, const int64_t n_interior[3], const double length[3], int order,
-                         const ew_bc bc[6], ew_prec prec, ew_grid** out) {
+                         const ew_bc bc[6], ew_prec prec, ew_grid** out) try {
     clear_error();
     if (!out || !n_interior || !length) return set_error(EW_EINVAL, "null argument");
     *out = nullptr;
@@ -349,6 +376,8 @@ ew_status ew_grid_create(int dim, const int64_t n_interior[3], const double leng
     g->device = dev;
     *out = g;
     return EW_OK;
+} catch (...) {
+    return abi_exception();
 }
 
 void ew_grid_destroy(ew_grid* g) {
@@ -369,7 +398,7 @@ void ew_grid_destroy(ew_grid* g) {
 }
 
 ew_status ew_filter_setup(const ew_grid* grid, const ew_filter_params* params, ew_filter_info* info,
-                          double* weights, int64_t cap) {
+                          double* weights, int64_t cap) try {
     clear_error();
     if (!grid) return set_error(EW_EINVAL, "grid is NULL");
     FilterPlan plan;
@@ -387,10 +416,12 @@ ew_status ew_filter_setup(const ew_grid* grid, const ew_filter_params* params, e
         std::memcpy(weights, plan.c.data(), sizeof(double) * plan.c.size());
     }
     return EW_OK;
+} catch (...) {
+    return abi_exception();
 }
 
 ew_status ew_filter_apply(const ew_grid* grid, const ew_filter_params* params, const void* v_in, void* v_out,
-                          int nvec, cudaStream_t stream) {
+                          int nvec, cudaStream_t stream) try {
     clear_error();
     EW_TRY(check_grid(grid));
     if (!v_in || !v_out) return set_error(EW_EINVAL, "null vector pointer");
@@ -403,9 +434,11 @@ ew_status ew_filter_apply(const ew_grid* grid, const ew_filter_params* params, c
     EW_TRY(plan_filter(grid->geom, params, &plan));
     ew_grid* g = const_cast<ew_grid*>(grid);
     return filter_apply_any(g, params, plan, v_in, v_out, nvec, stream);
+} catch (...) {
+    return abi_exception();
 }
 
-ew_status ew_apply_L(const ew_grid* grid, const void* u, void* Lu, int nvec, cudaStream_t stream) {
+ew_status ew_apply_L(const ew_grid* grid, const void* u, void* Lu, int nvec, cudaStream_t stream) try {
     clear_error();
     EW_TRY(check_grid(grid));
     if (!u || !Lu) return set_error(EW_EINVAL, "null vector pointer");
@@ -413,6 +446,8 @@ ew_status ew_apply_L(const ew_grid* grid, const void* u, void* Lu, int nvec, cud
     if (grid->prec == EW_FP32X2) return set_error(EW_EUNSUPPORTED, "double-FP32 grids: ew_filter_apply only");
     if (grid->prec == EW_FP32) return launch_apply_L<float>(grid->geom, (const float*)u, (float*)Lu, nvec, 1.0, stream);
     return launch_apply_L<double>(grid->geom, (const double*)u, (double*)Lu, nvec, 1.0, stream);
+} catch (...) {
+    return abi_exception();
 }
 
 }  // extern "C"
@@ -537,7 +572,7 @@ ew_status rayleigh_any(ew_grid* g, const void* phi, int nvec, double* lam, doubl
 extern "C" {
 
 ew_status ew_rayleigh(const ew_grid* grid, const void* phi, int nvec, double* lambda_host, double* eig_res_host,
-                      cudaStream_t stream) {
+                      cudaStream_t stream) try {
     clear_error();
     EW_TRY(check_grid(grid));
     if (!phi || !lambda_host) return set_error(EW_EINVAL, "null pointer");
@@ -546,10 +581,12 @@ ew_status ew_rayleigh(const ew_grid* grid, const void* phi, int nvec, double* la
     ew_grid* g = const_cast<ew_grid*>(grid);
     if (grid->prec == EW_FP32) return rayleigh_t<float>(g, (const float*)phi, nvec, lambda_host, eig_res_host, stream);
     return rayleigh_t<double>(g, (const double*)phi, nvec, lambda_host, eig_res_host, stream);
+} catch (...) {
+    return abi_exception();
 }
 
 ew_status ew_power_iteration(const ew_grid* grid, const ew_filter_params* params, void* v, int iters, double tol,
-                             double* beta_host, int* iters_done, double* lambda_host, cudaStream_t stream) {
+                             double* beta_host, int* iters_done, double* lambda_host, cudaStream_t stream) try {
     clear_error();
     EW_TRY(check_grid(grid));
     if (!v || !params) return set_error(EW_EINVAL, "null pointer");
@@ -559,6 +596,8 @@ ew_status ew_power_iteration(const ew_grid* grid, const ew_filter_params* params
     if (grid->prec == EW_FP32)
         return power_t<float>(g, params, (float*)v, iters, tol, beta_host, iters_done, lambda_host, stream);
     return power_t<double>(g, params, (double*)v, iters, tol, beta_host, iters_done, lambda_host, stream);
+} catch (...) {
+    return abi_exception();
 }
 
 }  // extern "C"

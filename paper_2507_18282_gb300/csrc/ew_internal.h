@@ -18,6 +18,10 @@ namespace ew {
 ew_status set_error(ew_status s, const std::string& msg);
 ew_status cuda_error(cudaError_t e, const char* what);
 void clear_error();
+// Called from the handler of an entry point's function-try-block (`catch (...)`):
+// turns the active C++ exception (a failed host allocation, a container size
+// beyond its limit) into a status and message, so that none crosses the ABI.
+ew_status abi_exception();
 
 #define EW_CUDA_TRY(call)                                   \
     do {                                                    \

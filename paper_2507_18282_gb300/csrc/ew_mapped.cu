@@ -36,6 +36,7 @@
 #include <algorithm>
 #include <cstring>
 #include <limits>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -370,7 +371,7 @@ template ew_status mapped_wsqrt<double>(const GridGeom&, const double*, double*,
 using namespace ew;
 
 extern "C" ew_status ew_grid_create_mapped(const int64_t n_interior[2], const double* xy_host, ew_prec prec,
-                                           ew_grid** out) {
+                                           ew_grid** out) try {
     clear_error();
     if (!out || !n_interior || !xy_host) return set_error(EW_EINVAL, "null argument");
     *out = nullptr;
@@ -380,22 +381,16 @@ extern "C" ew_status ew_grid_create_mapped(const int64_t n_interior[2], const do
     if (n1 < 1 || n2 < 1) return set_error(EW_EINVAL, "n_interior must be >= 1");
     if (n1 > (1 << 20) || n2 > (1 << 20) || (n1 + 2) * (n2 + 2) > ((int64_t)1 << 31))
         return set_error(EW_EINVAL, "mapped grid too large");
-    MappedData* m = new (std::nothrow) MappedData();
+    std::unique_ptr<MappedData> m(new (std::nothrow) MappedData());
     if (!m) return set_error(EW_ENOMEM, "host allocation failed");
-    ew_status s = mapped_build(n1, n2, xy_host, m);
-    if (s != EW_OK) {
-        delete m;
-        return s;
-    }
+    EW_TRY(mapped_build(n1, n2, xy_host, m.get()));
     int64_t n3[3] = {n1, n2, 1};
     double len[3] = {1.0, 1.0, 1.0};  // the unit square of the r coordinates
     ew_grid* g = nullptr;
-    s = ew_grid_create(2, n3, len, 2, nullptr, prec, &g);
-    if (s != EW_OK) {
-        delete m;
-        return s;
-    }
-    g->geom.map = m;
+    EW_TRY(ew_grid_create(2, n3, len, 2, nullptr, prec, &g));
+    g->geom.map = m.release();
     *out = g;
     return EW_OK;
+} catch (...) {
+    return abi_exception();
 }

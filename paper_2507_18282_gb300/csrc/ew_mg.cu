@@ -645,7 +645,7 @@ using namespace ew;
 
 extern "C" ew_status ew_implicit_step_mg(const ew_grid* grid, double half_dt2, const void* rhs, void* x,
                                          const ew_mg_params* mg, double* conv_factor, int* cycles_done,
-                                         cudaStream_t stream) {
+                                         cudaStream_t stream) try {
     clear_error();
     if (!grid || !rhs || !x || !mg) return set_error(EW_EINVAL, "null argument");
     if (!(half_dt2 >= 0.0)) return set_error(EW_EINVAL, "half_dt2 must be >= 0");
@@ -656,4 +656,6 @@ extern "C" ew_status ew_implicit_step_mg(const ew_grid* grid, double half_dt2, c
     if (g->prec == EW_FP32)
         return step_mg_t<float>(g, half_dt2, (const float*)rhs, (float*)x, mg, conv_factor, cycles_done, stream);
     return step_mg_t<double>(g, half_dt2, (const double*)rhs, (double*)x, mg, conv_factor, cycles_done, stream);
+} catch (...) {
+    return abi_exception();
 }

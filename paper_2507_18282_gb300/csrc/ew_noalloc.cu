@@ -87,7 +87,7 @@ static ew_status noalloc_t(const ew_grid* g, const ew_filter_params* p, const Fi
 using namespace ew;
 
 extern "C" ew_status ew_filter_apply_noalloc(const ew_grid* grid, const ew_filter_params* params, const void* v_in,
-                                             void* v_out, cudaStream_t stream) {
+                                             void* v_out, cudaStream_t stream) try {
     clear_error();
     if (!grid || !params || !v_in || !v_out) return set_error(EW_EINVAL, "null argument");
     int dev = -1;
@@ -105,4 +105,6 @@ extern "C" ew_status ew_filter_apply_noalloc(const ew_grid* grid, const ew_filte
     EW_TRY(plan_filter(grid->geom, params, &plan, /*with_weights=*/false));
     if (grid->prec == EW_FP32) return noalloc_t<float>(grid, params, plan, (const float*)v_in, (float*)v_out, stream);
     return noalloc_t<double>(grid, params, plan, (const double*)v_in, (double*)v_out, stream);
+} catch (...) {
+    return abi_exception();
 }

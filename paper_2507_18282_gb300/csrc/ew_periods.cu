@@ -100,7 +100,7 @@ using namespace ew;
 extern "C" {
 
 ew_status ew_choose_num_periods(const ew_grid* grid, const ew_filter_params* params, int n_wanted, int krylov_dim,
-                                int max_periods, int* num_periods, double* cr_host) {
+                                int max_periods, int* num_periods, double* cr_host) try {
     clear_error();
     if (!grid || !params || !num_periods) return set_error(EW_EINVAL, "null argument");
     if (n_wanted < 1 || krylov_dim <= n_wanted) return set_error(EW_EINVAL, "need 1 <= n_wanted < krylov_dim");
@@ -118,6 +118,18 @@ ew_status ew_choose_num_periods(const ew_grid* grid, const ew_filter_params* par
         ew_filter_params p = *params;
         p.num_periods = np;
         FilterPlan plan;
+        // The estimate sums the N_t + 1 weights for each of at least N_a + 1
+        // eigenvalues.  A candidate past that budget, or past the longest
+        // wave-solve, is not evaluated (CR = 1), nor are the longer ones; its
+        // weight table is never built.
+        const ew_status ps = plan_filter(g, &p, &plan, false);
+        if (np > 1 && (ps != EW_OK || (double)want * (double)(plan.Nt + 1) > 4e9)) {
+            clear_error();
+            if (cr_host)
+                for (int k = np; k <= max_periods; k *= 2) cr_host[idx++] = 1.0;
+            break;
+        }
+        EW_TRY(ps);
         EW_TRY(plan_filter(g, &p, &plan));
         // Widen a window [omega - w, omega + w] until the filter cannot put an
         // eigenvalue outside it among the top N_a + 1: beyond distance d of omega
@@ -170,6 +182,8 @@ ew_status ew_choose_num_periods(const ew_grid* grid, const ew_filter_params* par
         return set_error(EW_EUNSUPPORTED, "no N_p up to max_periods separates the wanted pairs (CR = 1)");
     *num_periods = best;
     return EW_OK;
+} catch (...) {
+    return abi_exception();
 }
 
 }  // extern "C"

@@ -496,26 +496,30 @@ using namespace ew;
 
 extern "C" {
 
-ew_status ew_smoother_forward(const ew_grid* grid, const float* w, const void* r, void* y, cudaStream_t st) {
+ew_status ew_smoother_forward(const ew_grid* grid, const float* w, const void* r, void* y, cudaStream_t st) try {
     clear_error();
     EW_TRY(check_smoother_grid(grid));
     if (!w || !r || !y) return set_error(EW_EINVAL, "null pointer");
     if (grid->prec == EW_FP32) return smoother_forward_t<float>(grid->geom, w, (const float*)r, (float*)y, st);
     return smoother_forward_t<double>(grid->geom, w, (const double*)r, (double*)y, st);
+} catch (...) {
+    return abi_exception();
 }
 
 ew_status ew_smoother_backward(const ew_grid* grid, const float* w, const void* r, const void* gy, float* grad,
-                               cudaStream_t st) {
+                               cudaStream_t st) try {
     clear_error();
     EW_TRY(check_smoother_grid(grid));
     if (!w || !r || !gy || !grad) return set_error(EW_EINVAL, "null pointer");
     ew_grid* g = const_cast<ew_grid*>(grid);
     if (grid->prec == EW_FP32) return smoother_backward_t<float>(g, w, (const float*)r, (const float*)gy, grad, st);
     return smoother_backward_t<double>(g, w, (const double*)r, (const double*)gy, grad, st);
+} catch (...) {
+    return abi_exception();
 }
 
 ew_status ew_smoother_train(const ew_grid* grid, double half_dt2, const ew_train_params* tp, float* weights,
-                            ew_train_report* rep, cudaStream_t st) {
+                            ew_train_report* rep, cudaStream_t st) try {
     clear_error();
     EW_TRY(check_smoother_grid(grid));
     if (!tp || !weights) return set_error(EW_EINVAL, "null pointer");
@@ -647,6 +651,8 @@ ew_status ew_smoother_train(const ew_grid* grid, double half_dt2, const ew_train
         rep->accepted = accepted;
     }
     return s;
+} catch (...) {
+    return abi_exception();
 }
 
 }  // extern "C"

@@ -92,6 +92,40 @@ def test_bad_arguments_are_refused(ew):
     g.close()
 
 
+def test_wave_solve_length_is_bounded(ew):
+    """N_t stays below 2^31 - 1: a tiny omega on a fine grid (CFL-derived steps
+    per period beyond int range) and N_p x N_its past the limit are refused with
+    EW_EINVAL instead of overflowing or allocating a weight table of that size."""
+    g = ew.ew_grid_create(2, (2047, 3071), (1.0, 1.5), order=4)
+    with pytest.raises(ew.EWError) as e:
+        ew.ew_filter_setup(g, ew.filter_params(1e-9))
+    assert e.value.status == 1 and "omega too small" in ew.ew_last_error()
+    with pytest.raises(ew.EWError) as e:
+        ew.ew_filter_setup(g, ew.filter_params(150.0, num_periods=(1 << 31) // 176 + 1))
+    assert e.value.status == 1 and "2^31" in ew.ew_last_error()
+    info, _ = ew.ew_filter_setup(g, ew.filter_params(150.0, num_periods=1024))
+    assert info["Nt"] == 1024 * 176
+    g.close()
+
+
+def test_every_entry_point_converts_host_exceptions(ew):
+    """No C++ exception crosses the ABI: every exported function that returns
+    an ew_status is a function-try-block whose handler maps the exception to a
+    status (abi_exception)."""
+    src = ""
+    csrc = os.path.join(ROOT, "paper_2507_18282_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith(".cu"):
+            src += open(os.path.join(csrc, f)).read()
+    hdr = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "ew.h")).read(), flags=re.S)
+    entry = re.findall(r"\bew_status\s+(ew_[a-z0-9_]+)\s*\(", hdr)
+    assert len(entry) >= 15
+    for name in entry:
+        m = re.search(r"ew_status\s+" + name + r"\s*\([^;{]*?\)\s*(try)?\s*\{", src, flags=re.S)
+        assert m, name
+        assert m.group(1) == "try", name
+
+
 def test_neumann_faces_add_active_wall_points(ew):
     """A Neumann face's wall points are active: one more point per Neumann
     face along its axis; h stays length / (n + 1), so the explicit step limit
