@@ -122,8 +122,11 @@ def ew_grid_destroy(grid: Grid):
 
 def mg_params(pre=2, post=2, max_cycles=1, rtol=0.0, jacobi_weight=0.8, learned_levels=0, weights=None,
               red_black=False):
-    m = ew_mg_params(pre, post, max_cycles, rtol, jacobi_weight, learned_levels,
-                     ctypes.c_void_p(weights.data_ptr()) if weights is not None else None, int(bool(red_black)))
+    wp = None
+    if weights is not None:
+        import torch
+        wp = _ptr(weights, torch.float32, 432 * max(int(learned_levels), 1))
+    m = ew_mg_params(pre, post, max_cycles, rtol, jacobi_weight, learned_levels, wp, int(bool(red_black)))
     m._keep = weights
     return m
 
@@ -174,9 +177,12 @@ def ew_filter_apply_batched(grids, params, v_in, v_out, nvec=None, stream=None):
     n = len(grids)
     G = (ctypes.c_void_p * n)(*[g.handle.value if hasattr(g.handle, "value") else g.handle for g in grids])
     P = (ew_filter_params * n)(*params)
-    vi = (ctypes.c_void_p * n)(*[_ptr(v_in[q], grids[q].dtype, grids[q].size).value for q in range(n)])
-    vo = (ctypes.c_void_p * n)(*[_ptr(v_out[q], grids[q].dtype, grids[q].size).value for q in range(n)])
-    nv = (ctypes.c_int * n)(*(nvec if nvec is not None else [1] * n))
+    nvec = list(nvec) if nvec is not None else [1] * n
+    if len(nvec) != n:
+        raise ValueError("nvec needs one entry per problem")
+    vi = (ctypes.c_void_p * n)(*[_ptr(v_in[q], grids[q].dtype, nvec[q] * grids[q].size).value for q in range(n)])
+    vo = (ctypes.c_void_p * n)(*[_ptr(v_out[q], grids[q].dtype, nvec[q] * grids[q].size).value for q in range(n)])
+    nv = (ctypes.c_int * n)(*[int(k) for k in nvec])
     check(lib.ew_filter_apply_batched(n, G, P, vi, vo, nv, _stream(stream)))
     return v_out
 

@@ -178,3 +178,18 @@ def test_pair_precision_is_two_dimensional(ew):
     with pytest.raises(ew.EWError) as e:
         ew.ew_grid_create(3, (8, 8, 8), (1.0, 1.0, 1.0), prec="fp32x2")
     assert e.value.status == 7
+
+
+def test_binding_checks_buffers_before_the_call(ew):
+    """The binding refuses what the library cannot check itself: host tensors
+    for device pointers, and a per-problem vector count list of the wrong length."""
+    import torch
+    with pytest.raises(TypeError):
+        ew.mg_params(learned_levels=1, weights=torch.zeros(432, dtype=torch.float32))
+    g = ew.ew_grid_create(2, (15, 15), (1.0, 1.0))
+    with pytest.raises(ValueError):
+        ew.ew_filter_apply_batched([g, g], [ew.filter_params(5.0)] * 2, [None, None], [None, None], nvec=[1])
+    with pytest.raises(TypeError):
+        x = torch.zeros(g.size, dtype=torch.float32)
+        ew.ew_filter_apply(g, ew.filter_params(5.0), x, torch.zeros_like(x))
+    g.close()
