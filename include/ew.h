@@ -224,7 +224,8 @@ ew_status ew_filter_apply(const ew_grid* grid, const ew_filter_params* params, c
 
 /* v_out[q] = S_q v_in[q] for nprob independent problems (each with its own
  * grid and filter parameters: uneven boxes, their own omega, time step and
- * N_t).  nvec (may be NULL = all 1) gives the vectors per problem.  2D
+ * N_t).  nvec (may be NULL = all 1) gives the vectors per problem; v_in[q]
+ * and v_out[q] must not overlap (EW_EINVAL).  2D
  * explicit problems of one precision and one order run together: the work of
  * every problem is cut into rounds of a few time steps, each round is one
  * persistent launch over all unfinished problems' tiles, and the whole

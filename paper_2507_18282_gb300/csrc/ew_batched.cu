@@ -363,6 +363,10 @@ extern "C" ew_status ew_filter_apply_batched(int nprob, const ew_grid* const* gr
             g->geom.order != g0->geom.order || g->geom.map || g->prec == EW_FP32X2)
             uniform = false;
         size_t es = g->prec == EW_FP32 ? 4 : 8;
+        const size_t bytes = (size_t)nv * g->geom.N * es;
+        const char* a = (const char*)v_in[q];
+        const char* b = (const char*)v_out[q];
+        if (a < b + bytes && b < a + bytes) return set_error(EW_EINVAL, "v_in and v_out of a problem overlap");
         for (int v = 0; v < nv; ++v) {
             BProblem b;
             b.g = g->geom;
