@@ -353,8 +353,9 @@ ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params* params, c
                           ew_eigs_report* report_host, cudaStream_t stream);
 
 /* Multigrid solve of one implicit time-step system (eqs. impMatrix,
- * implicitStep1):  (I - half_dt2 L_h) x = rhs.  x_dev holds the initial guess
- * on entry and the result on return (grid precision, device).  Runs up to
+ * implicitStep1):  (I - half_dt2 L_h) x = rhs, half_dt2 finite and >= 0.
+ * x_dev holds the initial guess on entry and the result on return (grid
+ * precision, device; must not overlap rhs_dev, EW_EINVAL).  Runs up to
  * mg->max_cycles V-cycles (fewer once ||rhs - M x||_2 <= rtol ||rhs||_2 when
  * rtol > 0).  conv_factor_host (may be NULL) receives the mean residual
  * reduction per cycle, cycles_done_host (may be NULL) the cycles run.  Axis

@@ -648,7 +648,13 @@ extern "C" ew_status ew_implicit_step_mg(const ew_grid* grid, double half_dt2, c
                                          cudaStream_t stream) try {
     clear_error();
     if (!grid || !rhs || !x || !mg) return set_error(EW_EINVAL, "null argument");
-    if (!(half_dt2 >= 0.0)) return set_error(EW_EINVAL, "half_dt2 must be >= 0");
+    if (!(half_dt2 >= 0.0) || !std::isfinite(half_dt2)) return set_error(EW_EINVAL, "half_dt2 must be finite and >= 0");
+    {
+        const size_t bytes = (size_t)grid->geom.N * (grid->prec == EW_FP32 ? 4 : 8);
+        const char* a = (const char*)rhs;
+        const char* b = (const char*)x;
+        if (a < b + bytes && b < a + bytes) return set_error(EW_EINVAL, "rhs and x overlap");
+    }
     int dev = -1;
     EW_CUDA_TRY(cudaGetDevice(&dev));
     if (grid->device >= 0 && grid->device != dev) return set_error(EW_EINVAL, "grid was created on another device");
