@@ -28,6 +28,7 @@
 #include <chrono>
 #include <cstring>
 #include <numeric>
+#include <memory>
 #include <vector>
 
 #include "ew_internal.h"
@@ -627,6 +628,11 @@ static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, ew_grid* gimg, in
     return EW_OK;
 }
 
+struct GridDeleter {
+    void operator()(ew_grid* g) const { ew_grid_destroy(g); }
+};
+using GridHandle = std::unique_ptr<ew_grid, GridDeleter>;
+
 static ew_status make_twin_fp64(const ew_grid* g, ew_grid** out) {
     if (g->geom.map) {
         const int64_t n[2] = {g->geom.map->n1, g->geom.map->n2};
@@ -706,26 +712,25 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
     };
     std::vector<double> lam1(nw), res1(nw);
     {
-        ew_grid* g64 = nullptr;
-        EW_TRY(make_twin_fp64(g, &g64));
-        ew_status s = rq(g64, ks.V, lam1.data(), res1.data());
-        ew_grid_destroy(g64);
-        EW_TRY(s);
+        ew_grid* raw = nullptr;
+        EW_TRY(make_twin_fp64(g, &raw));
+        GridHandle twin(raw);
+        EW_TRY(rq(twin.get(), ks.V, lam1.data(), res1.data()));
     }
     const double* final_vecs = ks.V;
     std::vector<double> lam(lam1), res(res1), beta(theta.begin(), theta.begin() + nw);
     KSRun ks2;
-    ew_grid* g64 = nullptr;
+    GridHandle g64;  // the FP64 twin of the refinement
     ew_status status = nconv >= nw ? EW_OK : EW_ENOCONV;
-    ew_grid* gdd = nullptr;  // refine_fp64 3: the images in double-FP32 pairs
     if ((ep->refine_fp64 == 1 || ep->refine_fp64 == 3) && g->prec == EW_FP32) {
-        EW_TRY(make_twin_fp64(g, &g64));
+        ew_grid* raw = nullptr;
+        EW_TRY(make_twin_fp64(g, &raw));
+        g64.reset(raw);
+        GridHandle gdd;  // refine_fp64 3: the images in double-FP32 pairs
         if (ep->refine_fp64 == 3 && g->geom.dim == 2 && !g->geom.map) {
-            ew_status st2 = make_twin_fp64(g, &gdd);
-            if (st2 != EW_OK) {
-                ew_grid_destroy(g64);
-                return st2;
-            }
+            raw = nullptr;
+            EW_TRY(make_twin_fp64(g, &raw));
+            gdd.reset(raw);
             gdd->prec = EW_FP32X2;
         }
         // guard vectors: a pair just outside the wanted set can share beta with
@@ -748,19 +753,16 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
         kr.st = st;
         int ws64 = 0, outer = 0;
         double res_tol = ep->refine_tol > 0 ? ep->refine_tol : 5e-9;
-        ew_status s = kr.setup();
-        if (s == EW_OK) s = refine_ir(ks, kr, g64, gdd, pexp, 6, res_tol, lam, beta, res, &ws64, &outer);
-        if (gdd) ew_grid_destroy(gdd);
-        if (s != EW_OK) {
-            ew_grid_destroy(g64);
-            return s;
-        }
+        EW_TRY(kr.setup());
+        EW_TRY(refine_ir(ks, kr, g64.get(), gdd.get(), pexp, 6, res_tol, lam, beta, res, &ws64, &outer));
         r.wave_solves += kr.wave_solves;
         r.wave_solves_fp64 = ws64;
         r.restarts += outer;
     } else if (ep->refine_fp64 == 2 && g->prec == EW_FP32) {
-        EW_TRY(make_twin_fp64(g, &g64));
-        ks2.g = g64;
+        ew_grid* raw = nullptr;
+        EW_TRY(make_twin_fp64(g, &raw));
+        g64.reset(raw);
+        ks2.g = g64.get();
         ks2.p = params;
         ks2.plan = ks.plan;
         ks2.N = ks.N;
@@ -770,16 +772,12 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
         ks2.tol = ep->refine_tol > 0 ? ep->refine_tol : 1e-10;
         ks2.max_ws = std::max(ks.max_ws / 2, 8 * nw);
         ks2.st = st;
-        ew_status s = ks2.setup();
-        if (s == EW_OK) s = ks2.start(ks.V, 0, true);
+        EW_TRY(ks2.setup());
+        EW_TRY(ks2.start(ks.V, 0, true));
         int nconv2 = 0;
         std::vector<double> theta2;
-        if (s == EW_OK) s = ks2.run(theta2, &nconv2);
-        if (s == EW_OK) s = rq(g64, ks2.V, lam.data(), res.data());
-        if (s != EW_OK) {
-            ew_grid_destroy(g64);
-            return s;
-        }
+        EW_TRY(ks2.run(theta2, &nconv2));
+        EW_TRY(rq(g64.get(), ks2.V, lam.data(), res.data()));
         final_vecs = ks2.V;
         beta.assign(theta2.begin(), theta2.begin() + nw);
         r.wave_solves_fp64 = ks2.wave_solves;
@@ -801,25 +799,11 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
         r.lambda_rel_change[j] = lam[j] > 0 ? best / lam[j] : 0.0;
     }
     r.n_converged = nconv;
-    if (vecs_dev && sym) {
-        ew_status s = launch_wsqrt<double>(g->geom, final_vecs, vecs_dev, nw, -1, st);
-        if (s != EW_OK) {
-            if (g64) ew_grid_destroy(g64);
-            return s;
-        }
-    }
-    if (vecs_dev) {
-        cudaError_t e = sym ? cudaSuccess
-                            : cudaMemcpyAsync(vecs_dev, final_vecs, sizeof(double) * (size_t)ks.N * nw,
-                                              cudaMemcpyDeviceToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            if (g64) ew_grid_destroy(g64);
-            return cuda_error(e, "copy of the eigenvectors");
-        }
-    }
+    if (vecs_dev && sym) EW_TRY(launch_wsqrt<double>(g->geom, final_vecs, vecs_dev, nw, -1, st));
+    if (vecs_dev && !sym)
+        EW_CUDA_TRY(cudaMemcpyAsync(vecs_dev, final_vecs, sizeof(double) * (size_t)ks.N * nw,
+                                    cudaMemcpyDeviceToDevice, st));
     EW_CUDA_TRY(cudaStreamSynchronize(st));
-    if (g64) ew_grid_destroy(g64);
     r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (rep) *rep = r;
     return status;
