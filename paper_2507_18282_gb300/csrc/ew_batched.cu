@@ -274,20 +274,21 @@ static ew_status batched_t(std::vector<BProblem>& P, int order, cudaStream_t st)
         EW_CUDA_TRY(cudaStreamWaitEvent(s, g_batch.ev_in, 0));
         EW_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         ew_status rs = EW_OK;
-        bool prof = g_profile_on;
-        g_profile_on = false;
-        for (auto& p : P) {
-            T* F = base + p.field_off;
-            if (rs == EW_OK) rs = first_step<T>(p.g, (const T*)p.vin, F, F + p.g.N, (T*)p.vout, p.plan, 1, p.g.N, s);
+        {
+            ProfilePause pause;  // the captured launches are counted once, below
+            for (auto& p : P) {
+                T* F = base + p.field_off;
+                if (rs == EW_OK)
+                    rs = first_step<T>(p.g, (const T*)p.vin, F, F + p.g.N, (T*)p.vout, p.plan, 1, p.g.N, s);
+            }
+            int grid_mult = g_batch.occ[vars[v].fn];
+            if (rs == EW_OK) {
+                std::vector<BatchDesc<T>> d2;
+                std::vector<BatchItem> i2;
+                std::vector<std::pair<size_t, size_t>> r2;
+                rs = run_rounds<T>(P, vars[v], base, nsm * grid_mult, s, d2, i2, r2, false, ddesc, ditem, gen);
+            }
         }
-        int grid_mult = g_batch.occ[vars[v].fn];
-        if (rs == EW_OK) {
-            std::vector<BatchDesc<T>> d2;
-            std::vector<BatchItem> i2;
-            std::vector<std::pair<size_t, size_t>> r2;
-            rs = run_rounds<T>(P, vars[v], base, nsm * grid_mult, s, d2, i2, r2, false, ddesc, ditem, gen);
-        }
-        g_profile_on = prof;
         cudaGraph_t graph = nullptr;
         cudaError_t ce = cudaStreamEndCapture(s, &graph);
         if (rs != EW_OK) {
@@ -310,9 +311,9 @@ static ew_status batched_t(std::vector<BProblem>& P, int order, cudaStream_t st)
     if (it != g_batch.tune.end()) {
         vi = it->second;
     } else if (vars.size() > 1) {
-        cudaEvent_t e0, e1;
-        EW_CUDA_TRY(cudaEventCreate(&e0));
-        EW_CUDA_TRY(cudaEventCreate(&e1));
+        EventPair ev;
+        EW_TRY(ev.create());
+        cudaEvent_t e0 = ev.a, e1 = ev.b;
         float best = 1e30f;
         for (size_t v = 0; v < vars.size(); ++v) {
             EW_CUDA_TRY(cudaEventRecord(e0, st));
@@ -329,8 +330,6 @@ static ew_status batched_t(std::vector<BProblem>& P, int order, cudaStream_t st)
                 vi = (int)v;
             }
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         g_batch.tune[key] = vi;
     }
     return upload_and_run((size_t)vi, g_batch.cap);

@@ -45,6 +45,31 @@ void count_mg_solve(int cycles);
 // brackets a fused-step launch: returns the start event (or null when off)
 cudaEvent_t fused_begin(cudaStream_t st);
 void fused_end(cudaEvent_t start, cudaStream_t st, int64_t points, int64_t cell_steps);
+// pauses the launch accounting for its lifetime (the autotuners' trial launches
+// are not counted)
+struct ProfilePause {
+    bool prev;
+    ProfilePause() : prev(g_profile_on) { g_profile_on = false; }
+    ~ProfilePause() { g_profile_on = prev; }
+    ProfilePause(const ProfilePause&) = delete;
+    ProfilePause& operator=(const ProfilePause&) = delete;
+};
+// two timing events, destroyed with the object
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    EventPair() = default;
+    EventPair(const EventPair&) = delete;
+    EventPair& operator=(const EventPair&) = delete;
+    ~EventPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+    ew_status create() {
+        EW_CUDA_TRY(cudaEventCreate(&a));
+        EW_CUDA_TRY(cudaEventCreate(&b));
+        return EW_OK;
+    }
+};
 
 // ---------------------------------------------------------------------------
 // stencil coefficients, already multiplied by a scale (dt^2, dt^2/2, -a, 1)

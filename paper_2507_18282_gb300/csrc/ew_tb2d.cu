@@ -234,11 +234,10 @@ static ew_status autotune(const GridGeom& g, T* const* F, T* acc, const T* cw, c
             return EW_OK;
         }
     }
-    bool prof = g_profile_on;
-    g_profile_on = false;  // tuning launches are not counted
-    cudaEvent_t e0, e1;
-    EW_CUDA_TRY(cudaEventCreate(&e0));
-    EW_CUDA_TRY(cudaEventCreate(&e1));
+    ProfilePause pause;  // tuning launches are not counted
+    EventPair ev;
+    EW_TRY(ev.create());
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     int best = 0;
     double best_rate = -1.0;
     ew_status status = EW_OK;
@@ -268,9 +267,6 @@ static ew_status autotune(const GridGeom& g, T* const* F, T* acc, const T* cw, c
             best = (int)i;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    g_profile_on = prof;
     EW_TRY(status);
     EW_CUDA_TRY(cudaGetLastError());
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -216,11 +216,10 @@ ew_status tb3d_tune(const GridGeom& g, const FilterPlan& plan, const T* cdev, T*
         if (g_tb3d_cache.count(key)) return EW_OK;
     }
     Stencil<T> s = make_stencil<T>(g, plan.dt * plan.dt);
-    bool prof = g_profile_on;
-    g_profile_on = false;  // tuning launches are not counted
-    cudaEvent_t e0, e1;
-    EW_CUDA_TRY(cudaEventCreate(&e0));
-    EW_CUDA_TRY(cudaEventCreate(&e1));
+    ProfilePause pause;  // tuning launches are not counted
+    EventPair ev;
+    EW_TRY(ev.create());
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     int best = 4;
     double best_rate = -1.0;
     ew_status status = EW_OK;
@@ -242,9 +241,6 @@ ew_status tb3d_tune(const GridGeom& g, const FilterPlan& plan, const T* cdev, T*
             best = B;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    g_profile_on = prof;
     EW_TRY(status);
     std::lock_guard<std::mutex> lk(g_tb3d_mu);
     g_tb3d_cache[key] = best;
