@@ -21,7 +21,7 @@ namespace ew {
 static thread_local std::string g_last_error;
 
 // ---- launch accounting -------------------------------------------------------
-bool g_profile_on = false;
+std::atomic<bool> g_profile_on{false};
 static std::mutex g_prof_mu;
 static int64_t g_launches = 0, g_fused_launches = 0, g_fused_cells = 0, g_fused_points = 0;
 static int64_t g_mg_cycles = 0, g_mg_solves = 0;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -38,7 +39,7 @@ ew_status abi_exception();
 // ---------------------------------------------------------------------------
 // launch accounting (ew_profile_*)
 // ---------------------------------------------------------------------------
-extern bool g_profile_on;
+extern std::atomic<bool> g_profile_on;  // read by every launch, set by ew_profile_enable
 void count_launch(int64_t k = 1);
 // one multigrid solve of an implicit time step that ran `cycles` V-cycles
 void count_mg_solve(int cycles);
@@ -49,7 +50,7 @@ void fused_end(cudaEvent_t start, cudaStream_t st, int64_t points, int64_t cell_
 // are not counted)
 struct ProfilePause {
     bool prev;
-    ProfilePause() : prev(g_profile_on) { g_profile_on = false; }
+    ProfilePause() : prev(g_profile_on.exchange(false)) {}
     ~ProfilePause() { g_profile_on = prev; }
     ProfilePause(const ProfilePause&) = delete;
     ProfilePause& operator=(const ProfilePause&) = delete;
