@@ -156,6 +156,32 @@ def test_continuous_filter_properties():
             assert abs(integral - O.beta_continuous(l, omega, Tf)) < 1e-8
 
 
+def test_simultaneous_iteration_worked_example():
+    """The worked example of the simultaneous-iteration rate (Section
+    "Estimating the EigenWave convergence rate based on simultaneous
+    iteration", eq. subSpaceIterationEigenWaveCR, with omega = 1 and N_p = 1):
+    a requested level beta_r of about 0.8 gives CR = beta(1 + 2 dw) /
+    beta(1 + dw) of about 0.4, dw defined by beta(1 + dw) = beta_r.  The
+    printed dw (about 0.375) is read as the width 2 dw of the interval
+    [1 - dw, 1 + dw]: the definition gives dw = 0.182.  The paper also states
+    that the rate is essentially independent of N_p while dw shrinks as
+    1 / N_p (so N_r(N_p) is about N_r(1) / N_p)."""
+    from scipy.optimize import brentq
+    crs, widths = [], []
+    for Np in (1, 2, 4, 8):
+        Tf = Np * 2 * math.pi
+
+        def beta(l):
+            return float(O.beta_continuous(l, 1.0, Tf))
+        dw = brentq(lambda d: beta(1.0 + d) - 0.8, 1e-9, 0.9 / Np)  # the first crossing past the peak
+        crs.append(beta(1.0 + 2 * dw) / beta(1.0 + dw))
+        widths.append(dw * Np)
+    assert abs(crs[0] - 0.4) < 0.05
+    assert abs(2 * widths[0] - 0.375) < 0.02
+    assert max(crs) - min(crs) < 0.02
+    assert max(widths) - min(widths) < 0.02 * widths[0]
+
+
 def test_discrete_filter_tends_to_continuous():
     """beta_d -> beta as N_t grows (the discrete-analysis remark)."""
     omega = 9.0
