@@ -72,7 +72,8 @@ typedef struct ew_grid ew_grid; /* opaque, library-owned */
  * eigBVPdiscrete, restricted to one Cartesian component grid).
  *   dim         2 or 3
  *   n_interior  interior points per axis (n_interior[2] ignored in 2D), each
- *               >= 1: the vertices strictly between the two walls
+ *               >= 1: the vertices strictly between the two walls; at most
+ *               2^40 active points in all (EW_EINVAL beyond)
  *   length      box side lengths; h_i = length_i / (n_i + 1)
  *   order       2: the 5/7-point Laplacian; 4: the fourth-order 9/13-point
  *               wide cross.  Both close at a wall by reflection (the paper's

@@ -357,6 +357,10 @@ ew_status ew_grid_create(int dim, const int64_t n_interior[3], const double leng
             geom.n[a] = 1;
             geom.h[a] = 1.0;
         }
+        // 2^40 active points (4 TB of FP32 per field) is far beyond any device;
+        // the bound keeps N and every byte count derived from it exact
+        if (geom.N > ((int64_t)1 << 40) / geom.n[a])
+            return set_error(EW_EINVAL, "grid too large: more than 2^40 active points");
         geom.N *= geom.n[a];
     }
     if (dim == 2 && (geom.n[0] > INT32_MAX / 2 || geom.n[1] > INT32_MAX / 2))

@@ -81,6 +81,11 @@ def test_bad_arguments_are_refused(ew):
         ew.ew_grid_create(2, (3, 3), (1, -1))
     with pytest.raises(ew.EWError):
         ew.ew_grid_create(2, (3, 3), (1, 1), order=3)
+    for n in [(1 << 30, 1 << 30, 1 << 30), (1 << 20, 1 << 20, 2)]:  # N would overflow / pass 2^40
+        with pytest.raises(ew.EWError) as e:
+            ew.ew_grid_create(3, n, (1, 1, 1))
+        assert e.value.status == 1 and "2^40" in ew.ew_last_error()
+    ew.ew_grid_create(3, (1 << 13, 1 << 13, 1 << 13), (1, 1, 1)).close()  # creation allocates nothing
     g = ew.ew_grid_create(2, (31, 31), (1, 1))
     for p in [ew.filter_params(-1.0), ew.filter_params(5.0, num_periods=0),
               ew.filter_params(5.0, steps_per_period=3),  # beyond the leapfrog stability limit
