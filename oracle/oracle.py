@@ -150,7 +150,8 @@ def cg_solve_M(g: Grid, a, b, tol=1e-14, maxit=100000):
 # ----------------------------------------------------------------------------
 
 def spectral_radius_bound(g: Grid):
-    """Largest eigenvalue of -L_h on the box: the mode symbol at sin^2 = 1.
+    """Largest eigenvalue of -L_h on the box: the mode symbol at sin^2 = 1
+    (the CFL limit of reading c2 takes dt_max = 2 / sqrt of it).
 
     Order 2: 4 sum 1/h_i^2.  Order 4: (4 + 4/3) sum 1/h_i^2 (1D symbol of the
     (-1, 16, -30, 16, -1)/12 stencil is 4 s + (4/3) s^2, s = sin^2(theta/2))."""
@@ -224,6 +225,7 @@ def filter_implicit(g: Grid, prm, v, tol=1e-14):
 
 
 def filter_apply(g: Grid, prm, v, scheme="explicit"):
+    """S v (Algorithm matVec) with the explicit or the implicit scheme."""
     return filter_explicit(g, prm, v) if scheme == "explicit" else filter_implicit(g, prm, v)
 
 
@@ -240,7 +242,9 @@ def mode_indices(g: Grid):
 
 
 def lambda2_closed_form(g: Grid, k):
-    """Discrete Dirichlet eigenvalue lambda_h^2 of -L_h for sine mode k.
+    """Discrete Dirichlet eigenvalue lambda_h^2 of -L_h for sine mode k: the
+    true discrete eigenvalues of eq. eigBVPdiscrete on a box (Section
+    "Accuracy of eigenpairs"), in closed form.
 
     With s_i = sin^2(k_i pi / (2 (n_i + 1))):  order 2: sum 4 s_i / h_i^2;
     order 4 (odd-reflection closure): sum 4 (s_i + s_i^2 / 3) / h_i^2."""
@@ -306,6 +310,7 @@ def dst(g: Grid, v):
 
 
 def idst(g: Grid, vhat):
+    """Inverse of ``dst``: the active vector with sine-mode coefficients vhat."""
     import scipy.fft
     return scipy.fft.idstn(np.asarray(vhat, dtype=np.float64).reshape(g.shape), type=1,
                            norm="ortho").reshape(-1)
@@ -400,8 +405,8 @@ def tensor_mode(g: Grid, k):
 
 
 def trapezoid_weights(g: Grid):
-    """Weights of the discrete L_2 inner product on the active points: the
-    trapezoid rule, 1/2 per Neumann wall coordinate (all 1 on Dirichlet
+    """Weights of the discrete L_2 inner product on the active points (eq.
+    discreteRayleighQuotient): the trapezoid rule, 1/2 per Neumann wall coordinate (all 1 on Dirichlet
     boxes, whose walls are not active).  L_h is symmetric in these weights."""
     w = np.ones(1)
     for a in range(g.dim):
@@ -498,8 +503,10 @@ def eig_res(g: Grid, lam, phi):
 
 
 def eigenspace_distance(v, basis):
-    """evect-err for a possibly multiple eigenvalue: max-norm distance from v
-    (scaled to ||v||_inf = 1) to its least-squares projection onto span(basis)."""
+    """evect-err for a possibly multiple eigenvalue (accuracy metrics of
+    Section "Numerical results": the distance to the closest vector of the
+    true discrete eigenspace): max-norm distance from v (scaled to
+    ||v||_inf = 1) to its least-squares projection onto span(basis)."""
     v = np.asarray(v, dtype=np.float64).reshape(-1)
     v = v / np.max(np.abs(v))
     B = np.asarray(basis, dtype=np.float64).reshape(len(v), -1)
