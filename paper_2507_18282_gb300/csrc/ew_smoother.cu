@@ -528,20 +528,22 @@ ew_status ew_smoother_train(const ew_grid* grid, double half_dt2, const ew_train
     ew_grid* g = const_cast<ew_grid*>(grid);
     const int64_t N = g->geom.N;
     const double a = half_dt2;
-    ew_mg_params plain{tp->pre, tp->post, 1, 0.0, tp->jacobi_weight > 0 ? tp->jacobi_weight : 0.8, 0, nullptr};
+    ew_mg_params plain{tp->pre, tp->post, 1, 0.0, tp->jacobi_weight > 0 ? tp->jacobi_weight : 0.8, 0, nullptr, 0};
     // device buffers: samples, N(r), M N(r), e = r - M N(r), gy, weight state
-    std::vector<void*> allocs;
+    struct DeviceBuffers {  // freed on every return path
+        std::vector<void*> p;
+        ~DeviceBuffers() {
+            for (void* q : p) cudaFree(q);
+        }
+    } allocs;
     auto alloc = [&](void** p, size_t bytes) -> ew_status {
         cudaError_t e = cudaMalloc(p, bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return set_error(EW_ENOMEM, "training workspace allocation failed");
         }
-        allocs.push_back(*p);
+        allocs.p.push_back(*p);
         return EW_OK;
-    };
-    auto release = [&]() {
-        for (void* p : allocs) cudaFree(p);
     };
     float *samples = nullptr, *y = nullptr, *My = nullptr, *res = nullptr, *gy = nullptr, *state = nullptr;
     ew_status s = EW_OK;
@@ -551,10 +553,7 @@ ew_status ew_smoother_train(const ew_grid* grid, double half_dt2, const ew_train
     if (s == EW_OK) s = alloc((void**)&res, sizeof(float) * (size_t)N);
     if (s == EW_OK) s = alloc((void**)&gy, sizeof(float) * (size_t)N);
     if (s == EW_OK) s = alloc((void**)&state, sizeof(float) * 4 * 2 * kW);  // grad, m, v, best
-    if (s != EW_OK) {
-        release();
-        return s;
-    }
+    if (s != EW_OK) return s;
     float* grad = state;
     float* m = state + 2 * kW;
     float* v = state + 4 * kW;
@@ -642,7 +641,6 @@ ew_status ew_smoother_train(const ew_grid* grid, double half_dt2, const ew_train
     if (s == EW_OK && !accepted)  // plain multigrid stays: hand back the initial weights
         cudaMemcpyAsync(weights, best, sizeof(float) * 2 * kW, cudaMemcpyDeviceToDevice, st);
     cudaStreamSynchronize(st);
-    release();
     if (rep) {
         rep->loss_first = loss_first;
         rep->loss_last = loss_last;
