@@ -36,6 +36,29 @@ ew_status abi_exception();
         if (s_ != EW_OK) return s_;           \
     } while (0)
 
+// a device allocation owned by a scope, freed on every return path
+struct DeviceBuffer {
+    void* p = nullptr;
+    DeviceBuffer() = default;
+    DeviceBuffer(const DeviceBuffer&) = delete;
+    DeviceBuffer& operator=(const DeviceBuffer&) = delete;
+    ~DeviceBuffer() {
+        if (p) cudaFree(p);
+    }
+    ew_status alloc(size_t bytes) {
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            return set_error(EW_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+        }
+        return EW_OK;
+    }
+    template <typename T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+};
+
 // ---------------------------------------------------------------------------
 // launch accounting (ew_profile_*)
 // ---------------------------------------------------------------------------

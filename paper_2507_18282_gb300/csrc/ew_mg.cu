@@ -579,8 +579,9 @@ ew_status mg_collect_residuals(ew_grid* g, double a, const ew_mg_params* mp, int
     const int64_t N = g->geom.N;
     MGSolver<float> mg;
     EW_TRY(mg.setup(g, a, mp, st));
-    double* tmp = nullptr;
-    EW_CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * (size_t)N));
+    DeviceBuffer tmp_buf;
+    EW_TRY(tmp_buf.alloc(sizeof(double) * (size_t)N));
+    double* tmp = tmp_buf.as<double>();
     Stencil<float> sa = make_stencil<float>(g->geom, a);
     ew_status s = EW_OK;
     int k = 0;
@@ -603,7 +604,6 @@ ew_status mg_collect_residuals(ew_grid* g, double a, const ew_mg_params* mp, int
         }
     }
     cudaStreamSynchronize(st);
-    cudaFree(tmp);
     return s;
 }
 
@@ -613,11 +613,13 @@ ew_status mg_collect_residuals(ew_grid* g, double a, const ew_mg_params* mp, int
 ew_status mg_convergence(ew_grid* g, double a, const ew_mg_params* mp, int ncycles, uint64_t seed, double* rho,
                          cudaStream_t st) {
     const int64_t N = g->geom.N;
-    float *b = nullptr, *x = nullptr;
-    double* tmp = nullptr;
-    EW_CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * (size_t)N));
-    EW_CUDA_TRY(cudaMalloc(&b, sizeof(float) * (size_t)N));
-    EW_CUDA_TRY(cudaMalloc(&x, sizeof(float) * (size_t)N));
+    DeviceBuffer tmp_buf, b_buf, x_buf;
+    EW_TRY(tmp_buf.alloc(sizeof(double) * (size_t)N));
+    EW_TRY(b_buf.alloc(sizeof(float) * (size_t)N));
+    EW_TRY(x_buf.alloc(sizeof(float) * (size_t)N));
+    double* tmp = tmp_buf.as<double>();
+    float* b = b_buf.as<float>();
+    float* x = x_buf.as<float>();
     ew_status s = splitmix_uniform(N, seed, tmp, st);
     if (s == EW_OK) s = convert<double, float>(N, tmp, b, st);
     cudaMemsetAsync(x, 0, sizeof(float) * N, st);
@@ -632,9 +634,6 @@ ew_status mg_convergence(ew_grid* g, double a, const ew_mg_params* mp, int ncycl
     double cr = 0.0;
     if (s == EW_OK) s = step_mg_t<float>(g, a, b, x, &rest, &cr, nullptr, st);
     cudaStreamSynchronize(st);
-    cudaFree(tmp);
-    cudaFree(b);
-    cudaFree(x);
     *rho = cr;
     return s;
 }
