@@ -222,6 +222,7 @@ static ew_status batched_t(std::vector<BProblem>& P, int order, cudaStream_t st)
         g_batch.dev_bytes = 0;
         cudaError_t e = cudaMalloc(&g_batch.dev, need);
         if (e != cudaSuccess) {
+            g_batch.dev = nullptr;
             cudaGetLastError();
             return set_error(EW_ENOMEM, "batched workspace allocation failed");
         }
@@ -230,14 +231,18 @@ static ew_status batched_t(std::vector<BProblem>& P, int order, cudaStream_t st)
     if (g_batch.host_bytes < need) {
         if (g_batch.host) cudaFreeHost(g_batch.host);
         g_batch.host = nullptr;
-        EW_CUDA_TRY(cudaMallocHost(&g_batch.host, need));
+        g_batch.host_bytes = 0;
+        cudaError_t e = cudaMallocHost(&g_batch.host, need);
+        if (e != cudaSuccess) {
+            g_batch.host = nullptr;
+            cudaGetLastError();
+            return set_error(EW_ENOMEM, "batched pinned staging allocation failed");
+        }
         g_batch.host_bytes = need;
     }
-    if (!g_batch.cap) {
-        EW_CUDA_TRY(cudaStreamCreateWithFlags(&g_batch.cap, cudaStreamNonBlocking));
-        EW_CUDA_TRY(cudaEventCreateWithFlags(&g_batch.ev_in, cudaEventDisableTiming));
-        EW_CUDA_TRY(cudaEventCreateWithFlags(&g_batch.ev_out, cudaEventDisableTiming));
-    }
+    if (!g_batch.cap) EW_CUDA_TRY(cudaStreamCreateWithFlags(&g_batch.cap, cudaStreamNonBlocking));
+    if (!g_batch.ev_in) EW_CUDA_TRY(cudaEventCreateWithFlags(&g_batch.ev_in, cudaEventDisableTiming));
+    if (!g_batch.ev_out) EW_CUDA_TRY(cudaEventCreateWithFlags(&g_batch.ev_out, cudaEventDisableTiming));
     T* base = (T*)g_batch.dev;
     char* tdev = (char*)g_batch.dev + field_bytes;
     // weights (host staging -> device)
