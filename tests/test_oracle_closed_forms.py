@@ -50,6 +50,24 @@ def test_closed_form_matches_paper_tables(fixture, n, length, lo, hi):
         assert gm == wm
 
 
+def test_closed_form_counts_the_eigenvalues_below_each_level():
+    """The paper's index k of the closest true eigenvalue (same table, the true
+    eigenvalues sorted from k = 0) fixes how many eigenvalues of the whole
+    discrete spectrum lie below each printed level: a closed form that dropped
+    or doubled a mode family anywhere below 20 fails it."""
+    g = O.Grid((127, 127), (1.0, 1.0), 2)
+    lam = np.sort(np.sqrt(O.spectrum(g)[0]))
+    with open(os.path.join(GOLDEN, "square128_order2_index.txt")) as f:
+        rows = [line.split() for line in f if line.strip() and not line.startswith("#")]
+    assert len(rows) == 27
+    for j, lv, k, m in rows:
+        lv, k, m = float(lv), int(k), int(m)
+        below = int(np.sum(lam < lv - 5e-7))
+        at = int(np.sum(np.abs(lam - lv) <= 5e-7 + 1e-9 * lv))
+        assert at == m, (j, lv, at, m)
+        assert below <= k <= below + m - 1, (j, lv, below, k)
+
+
 def _dense(g, op):
     N = g.size
     A = np.empty((N, N))
