@@ -50,14 +50,18 @@ def test_closed_form_matches_paper_tables(fixture, n, length, lo, hi):
         assert gm == wm
 
 
-def test_closed_form_counts_the_eigenvalues_below_each_level():
-    """The paper's index k of the closest true eigenvalue (same table, the true
-    eigenvalues sorted from k = 0) fixes how many eigenvalues of the whole
+@pytest.mark.parametrize("fixture,n", [
+    ("square128_order2_index.txt", (127, 127)),
+    ("box2_order2_index.txt", (19, 19, 19)),
+])
+def test_closed_form_counts_the_eigenvalues_below_each_level(fixture, n):
+    """The paper's index k of the closest true eigenvalue (same tables, the
+    true eigenvalues sorted from k = 0) fixes how many eigenvalues of the whole
     discrete spectrum lie below each printed level: a closed form that dropped
-    or doubled a mode family anywhere below 20 fails it."""
-    g = O.Grid((127, 127), (1.0, 1.0), 2)
+    or doubled a mode family anywhere below the printed levels fails it."""
+    g = O.Grid(n, (1.0,) * len(n), 2)
     lam = np.sort(np.sqrt(O.spectrum(g)[0]))
-    with open(os.path.join(GOLDEN, "square128_order2_index.txt")) as f:
+    with open(os.path.join(GOLDEN, fixture)) as f:
         rows = [line.split() for line in f if line.strip() and not line.startswith("#")]
     assert len(rows) == 27
     for j, lv, k, m in rows:
