@@ -198,3 +198,43 @@ def test_binding_checks_buffers_before_the_call(ew):
         x = torch.zeros(g.size, dtype=torch.float32)
         ew.ew_filter_apply(g, ew.filter_params(5.0), x, torch.zeros_like(x))
     g.close()
+
+
+def test_every_entry_point_refuses_null_arguments(ew):
+    """Each exported function, called with null pointers and zero sizes, returns
+    an error status and a message instead of dereferencing them (run in a
+    child process, so that a crash would fail this test rather than the run)."""
+    script = r'''
+import ctypes
+from paper_2507_18282_gb300 import _lib as L
+lib = L.lib
+calls = {
+    "ew_grid_create": (2, None, None, 2, None, 0, None),
+    "ew_grid_create_mapped": (None, None, 0, None),
+    "ew_filter_setup": (None, None, None, None, 0),
+    "ew_filter_apply": (None, None, None, None, 1, None),
+    "ew_filter_apply_batched": (0, None, None, None, None, None, None),
+    "ew_filter_apply_noalloc": (None, None, None, None, None),
+    "ew_choose_num_periods": (None, None, 1, 2, 1, None, None),
+    "ew_apply_L": (None, None, None, 1, None),
+    "ew_rayleigh": (None, None, 1, None, None, None),
+    "ew_power_iteration": (None, None, None, 1, 0.0, None, None, None, None),
+    "ew_arnoldi_eigs": (None, None, None, None, None, None, None, None),
+    "ew_implicit_step_mg": (None, 0.0, None, None, None, None, None, None),
+    "ew_smoother_forward": (None, None, None, None, None),
+    "ew_smoother_backward": (None, None, None, None, None, None),
+    "ew_smoother_train": (None, 0.0, None, None, None, None),
+    "ew_profile_read": (None,),
+}
+for name, args in calls.items():
+    st = getattr(lib, name)(*args)
+    assert st in (L.EW_EINVAL, L.EW_ECUDA), (name, st)
+    assert lib.ew_last_error(), name
+lib.ew_grid_destroy(None)
+print("ok", len(calls))
+'''
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "-c", script], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == "ok 16"
