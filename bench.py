@@ -30,6 +30,7 @@ each rank runs the same workload and `value` counts all ranks' work.
 from __future__ import annotations
 
 import argparse
+import atexit
 import hashlib
 import json
 import os
@@ -118,8 +119,13 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            atexit.register(self._end)  # no sampler outlives the bench, whatever ends it
         except Exception:
             self.proc = None
+
+    def _end(self):
+        if self.proc is not None and self.proc.poll() is None:
+            self.proc.kill()
 
     def stop(self):
         if self.proc is None:
@@ -459,6 +465,8 @@ def run_extra(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     pk, pk_kind = peaks()
     w = args.workload
+    clocks = ClockSampler(0)  # over the whole workload (tuning and warm-up included)
+    clocks.start()
     if w == "cube3d":
         n, L = (511, 511, 511), (1.0, 1.0, 1.0)
         g = ew.ew_grid_create(3, n, L, order=2, prec="fp32")
@@ -680,7 +688,7 @@ def run_extra(args):
     else:
         raise SystemExit("unknown workload %s" % w)
     line.update(dict(n_gpus=1, steps=args.steps, warmup=args.warmup, dtype="f32", data="synthetic",
-                     l2="flushed between timed steps (512 MB write)"))
+                     l2="flushed between timed steps (512 MB write)", clocks=clocks.stop()))
     print(json.dumps(line), flush=True)
     return 0
 
