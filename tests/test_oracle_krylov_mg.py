@@ -38,6 +38,26 @@ def test_krylov_schur_finds_closed_form_eigenpairs(order, scheme):
         assert O.eig_res(g, l, X[:, j]) < 1e-7
 
 
+def test_cgs2_orthogonalises_to_rounding_on_nearly_dependent_vectors():
+    """Gram-Schmidt twice ("twice is enough", Kahan-Parlett): against an
+    orthonormal basis the projected vector is orthogonal to rounding even when
+    w lies almost in span(V), where one classical pass leaves an error of
+    about eps ||w|| / ||w_perp||; and w = w_perp + V h exactly up to rounding."""
+    rng = np.random.default_rng(3)
+    N, m = 4000, 24
+    V, _ = np.linalg.qr(rng.standard_normal((N, m)))
+    for gap in (1e-2, 1e-6, 1e-9):
+        w = V @ rng.standard_normal(m) + gap * rng.standard_normal(N)
+        wp, h = O._cgs2(V, w)
+        eps = np.finfo(float).eps
+        assert np.max(np.abs(V.T @ wp)) <= 50 * eps * np.linalg.norm(wp)
+        assert np.linalg.norm(w - wp - V @ h) <= 50 * eps * np.linalg.norm(w)
+        # one pass is not enough once the gap is small (what the second pass is for)
+        one = w - V @ (V.T @ w)
+        if gap <= 1e-6:
+            assert np.max(np.abs(V.T @ one)) > 50 * eps * np.linalg.norm(one)
+
+
 def test_eigenspace_distance_of_multiple_eigenvalue():
     """evect-err by projection onto a multiple eigenspace: any combination of
     the (3,1) and (1,3) square modes is at distance 0, another mode is not."""
