@@ -238,3 +238,35 @@ print("ok", len(calls))
     r = subprocess.run([sys.executable, "-c", script], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == "ok 16"
+
+
+def test_header_is_plain_c(ew, tmp_path):
+    """include/ew.h compiles as C99 (the ABI is a C interface, usable without
+    C++) and a C program links against the library's exported names."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc")
+    inc = next((os.path.join(d, "include") for d in (os.environ.get("CUDA_HOME", ""), "/usr/local/cuda")
+                if d and os.path.exists(os.path.join(d, "include", "cuda_runtime_api.h"))), None)
+    if not cc or not inc:
+        pytest.skip("needs gcc and the CUDA headers")
+    src = tmp_path / "use_ew.c"
+    src.write_text(
+        '#include "ew.h"\n'
+        "int main(void) {\n"
+        "    ew_grid* g = 0;\n"
+        "    int64_t n[3] = {15, 15, 1};\n"
+        "    double len[3] = {1.0, 1.0, 1.0};\n"
+        "    ew_status s = ew_grid_create(2, n, len, 2, 0, EW_FP32, &g);\n"
+        "    ew_filter_params p = {0};\n"
+        "    ew_filter_info info;\n"
+        "    p.omega = 5.0; p.num_periods = 1;\n"
+        "    if (s == EW_OK) s = ew_filter_setup(g, &p, &info, 0, 0);\n"
+        "    ew_grid_destroy(g);\n"
+        "    return (s == EW_OK && info.num_steps > 0) ? 0 : 1;\n"
+        "}\n")
+    exe = tmp_path / "use_ew"
+    libdir = os.path.dirname(ew.LIB_PATH)
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-I", inc,
+                           str(src), "-L", libdir, "-lew", "-Wl,-rpath," + libdir, "-o", str(exe)])
+    assert subprocess.run([str(exe)], timeout=120).returncode == 0
