@@ -6,7 +6,11 @@ Tolerances:
   FP32: a leapfrog step makes about four roundings of size eps32 |u| and the
   scheme is neutrally stable, so the error of W^n grows at most linearly in
   n; the filter weights sum to O(1), so ||S v - S_32 v|| / ||v|| stays below
-  C * N_t * eps32.  C = 4 is used for the 2-norm bound.
+  C * N_t * eps32.  C = 4 is used for the 2-norm bound.  Element by element
+  the same argument applies to one point's roundings (each at most a few
+  eps32 max |W^n| <= eps32 max |v| per step, carried by a propagator that is
+  bounded in the max norm over one period), so every point is also checked
+  against 4 N_t eps32 max |v|; the measured worst point sits about 10x inside.
 """
 import math
 
@@ -162,6 +166,8 @@ def test_fp32_parity(ew, n, length, order, tb):
     ref = _oracle(n, length, order, omega, 1, info["steps_per_period"], v.astype(np.float32).astype(np.float64))
     rel2 = np.linalg.norm(out - ref) / np.linalg.norm(v)
     assert rel2 < 4 * info["Nt"] * EPS32, (rel2, info["Nt"])
+    relmax = np.max(np.abs(out - ref)) / np.max(np.abs(v))
+    assert relmax < 4 * info["Nt"] * EPS32, (relmax, info["Nt"])
 
 
 def _mode_test(ew, n, length, order, omega, k, prec="fp32"):
@@ -208,9 +214,9 @@ def test_full_size_random_parity_rectangle(ew):
     ref = _oracle(n, L, 4, omega, 1, info["steps_per_period"], v.astype(np.float32).astype(np.float64))
     rel2 = np.linalg.norm(out - ref) / np.linalg.norm(v)
     assert rel2 < 4 * info["Nt"] * EPS32, rel2
-    # sampled points one by one
-    idx = np.array([0, 2046, 2047, 1234567, n[0] * n[1] - 1])
-    assert np.max(np.abs(out[idx] - ref[idx])) < 4 * info["Nt"] * EPS32
+    # every point (max norm), the corners and seams of the tiling included
+    relmax = np.max(np.abs(out - ref)) / np.max(np.abs(v))
+    assert relmax < 4 * info["Nt"] * EPS32, relmax
 
 
 @pytest.mark.parametrize("order", [2, 4])

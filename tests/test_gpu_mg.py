@@ -4,8 +4,9 @@ the oracle.
 Tolerances: FP64 V-cycles and implicit wave-solves repeat the oracle's cycle
 operation for operation (only rounding order differs), so 1e-12 relative.
 The learned smoother rounds its input and hidden activations to BF16
-(relative half-ulp 2^-9), so forward outputs agree with the FP64 oracle to a
-few 2^-9 in the 2-norm (4e-3 used); gradients to 1e-2.
+(8 significant bits: at most 2^-8 relative per rounding), so forward outputs
+agree with the FP64 oracle to about 2^-8 in the 2-norm (4e-3 used); gradients
+to 1e-2.  Element-wise bounds at larger sizes: test_gpu_learned.py.
 """
 import math
 
