@@ -238,10 +238,10 @@ ew_status ew_filter_apply_batched(int nprob, const ew_grid* const* grids, const 
                                   cudaStream_t stream);
 
 /* ew_filter_apply for callers that cannot allocate device memory (no
- * counterpart in the paper).  Code that runs while a stream is being captured
- * into a CUDA graph, plugins whose host application owns every device
- * allocation, and real-time loops that must not enter the allocator cannot
- * let the library cudaMalloc scratch on first use, as ew_filter_apply does.
+ * counterpart in the paper).  Plugins whose host application owns every
+ * device allocation, and real-time loops that must not enter the allocator
+ * (its latency is unbounded), cannot let the library cudaMalloc scratch on
+ * first use, as ew_filter_apply does.
  * This entry point calls no cudaMalloc, cudaFree or other allocating routine:
  * its scratch is one file-scope device array of 16.5 MiB (four time-level
  * fields of up to 16 MiB and up to 512 KiB of filter weights) that every GPU
@@ -253,10 +253,12 @@ ew_status ew_filter_apply_batched(int nprob, const ew_grid* const* grids, const 
  *     KiB; larger requests return EW_EINVAL with the limit in ew_last_error.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) for that device; make that first call before any
- *     stream capture.
+ *     stream capture.  The address is kept for the life of the process: do
+ *     not call this entry point on a device after cudaDeviceReset of it.
  *   - Every call shares the array (each rewrites all of it that it reads, so
  *     nothing is carried over); calls whose GPU work overlaps race on it.
- *   - temporal_block 0 means a fixed depth of 4 (no autotuning). */
+ *   - temporal_block 0 means a fixed depth of 4 (no autotuning); a negative
+ *     one returns EW_EINVAL, as in ew_filter_apply. */
 ew_status ew_filter_apply_noalloc(const ew_grid* grid, const ew_filter_params* params, const void* v_in_dev,
                                   void* v_out_dev, cudaStream_t stream);
 

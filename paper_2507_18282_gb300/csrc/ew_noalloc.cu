@@ -1,9 +1,10 @@
 // ew_noalloc.cu -- the explicit wave-solve for callers that cannot allocate
 // device memory.
 //
-// Some callers cannot call cudaMalloc: code running while a stream is being
-// captured into a CUDA graph, plugins whose host application owns every
-// device allocation, or real-time loops that must not touch the allocator.
+// Some callers cannot call cudaMalloc: plugins whose host application owns
+// every device allocation (the library may not take memory behind its back),
+// or real-time loops that must not enter the allocator, whose latency is
+// unbounded.
 // ew_filter_apply keeps its time levels in scratch it allocates on first use;
 // this variant takes them from one file-scope device array instead, of a
 // fixed size, which every GPU that loads the library holds until the process
@@ -78,6 +79,7 @@ static ew_status noalloc_t(const ew_grid* g, const ew_filter_params* p, const Fi
     count_launch();
     // a fixed temporal depth: the autotuner (which times candidates with CUDA
     // events) is not used on this path
+    if (p->temporal_block < 0) return set_error(EW_EINVAL, "temporal_block < 0");
     int tb = p->temporal_block > 0 ? p->temporal_block : 4;
     return explicit_wave_solve<T>(g->geom, plan, cdev, vin, vout, 1, fields, tb, st);
 }
