@@ -207,9 +207,10 @@ ew_status ew_filter_setup(const ew_grid* grid, const ew_filter_params* params,
  * of the box (tensor sine and cosine modes, by face kind) and the cheapest N_p is written to
  * *num_periods.  cr_host (may be NULL; capacity floor(log2(max_periods)) + 1)
  * receives CR for each candidate; a candidate is skipped (CR = 1), with all
- * longer ones, once its N_t would pass 2^31 - 2 or (N_t + 1)(krylov_dim + 1)
- * would pass 4e9 (the cost of the estimate: a sum over the N_t + 1 filter
- * weights per eigenvalue).  Host work only (no GPU, no stream).
+ * longer ones, once its N_t would pass 2^31 - 2.  Each beta_d takes O(1)
+ * operations (the trapezoid sum in closed form), over the eigenvalues of a
+ * window around omega that is widened until no eigenvalue outside it can
+ * enter the top N_a + 1.  Host work only (no GPU, no stream).
  * EW_EUNSUPPORTED if no candidate gives CR < 1, or for a curvilinear grid
  * (its spectrum has no closed form). */
 ew_status ew_choose_num_periods(const ew_grid* grid, const ew_filter_params* params, int n_wanted,
@@ -248,9 +249,11 @@ ew_status ew_filter_apply_batched(int nprob, const ew_grid* const* grids, const 
  * loading the library holds until the process exits.
  *   - One vector (v_in, v_out device, grid precision, not overlapping), the
  *     explicit scheme only (EW_EUNSUPPORTED otherwise).
- *   - Limits: 4 N sizeof(element) <= 16 MiB, i.e. N <= 1048576 active points
- *     in FP32 and N <= 524288 in FP64, and (N_t + 1) sizeof(element) <= 512
- *     KiB; larger requests return EW_EINVAL with the limit in ew_last_error.
+ *   - Limits: 4 M sizeof(element) <= 16 MiB, with M the points of one
+ *     time level: N on 3D grids and (n_x rounded up to 4) n_y on 2D grids,
+ *     rounded up to 64; i.e. about 1048576 active points in FP32 and 524288
+ *     in FP64.  Also (N_t + 1) sizeof(element) <= 512 KiB.  Larger requests
+ *     return EW_EINVAL with the limit in ew_last_error.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) for that device; make that first call before any
  *     stream capture.  The address is kept for the life of the process: do
@@ -355,6 +358,31 @@ ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params* params, c
                           const double* start_dev, double* lambda_host, double* vecs_dev,
                           ew_eigs_report* report_host, cudaStream_t stream);
 
+/* Eigen-solves of nprob independent problems with their filter applications
+ * batched (the paper's method per problem; the batching has no counterpart in
+ * the paper).  Problem q runs the solver of ew_arnoldi_eigs with grids[q],
+ * params[q] and eigs[q] (random start block from eigs[q].seed) on a host
+ * thread and a stream of its own.  Whenever every unfinished solver has asked
+ * for a filter application S X, all of them run together as one
+ * ew_filter_apply_batched call (its CUDA graph kept per batch and replayed;
+ * the tile variant tuned on the first round and then kept); the rest of each
+ * solver (orthogonalisation, small eigenproblems, Rayleigh quotients,
+ * refinement) runs per problem between those rounds.
+ *   lambda_host[q]  receives problem q's n_wanted eigenvalues (host)
+ *   vecs_dev        may be NULL, else vecs_dev[q] (may be NULL) receives
+ *                   problem q's eigenvectors as in ew_arnoldi_eigs (device)
+ *   reports, statuses  may be NULL, else nprob entries (host)
+ *   rounds_host     may be NULL, else the number of batched calls made
+ * The problems' work starts after the work already queued on `stream`, and
+ * the call returns when all of it is done.  Returns EW_OK when every problem
+ * did, else the first other status in problem order, with that problem's
+ * message in ew_last_error.  Uses the process-wide batched workspace: calls
+ * must not overlap with each other or with ew_filter_apply_batched. */
+ew_status ew_arnoldi_eigs_batched(int nprob, const ew_grid* const* grids, const ew_filter_params* params,
+                                  const ew_eigs_params* eigs, double* const* lambda_host, double* const* vecs_dev,
+                                  ew_eigs_report* reports, ew_status* statuses, int* rounds_host,
+                                  cudaStream_t stream);
+
 /* Multigrid solve of one implicit time-step system (eqs. impMatrix,
  * implicitStep1):  (I - half_dt2 L_h) x = rhs, half_dt2 finite and >= 0.
  * x_dev holds the initial guess on entry and the result on return (grid
@@ -412,6 +440,16 @@ typedef struct {
 } ew_train_report;
 ew_status ew_smoother_train(const ew_grid* grid, double half_dt2, const ew_train_params* params,
                             float* weights_dev, ew_train_report* report_host, cudaStream_t stream);
+
+/* The variant the autotuner chose for the 2D blocked time step on this grid
+ * and a block of nvec vectors (no counterpart in the paper; for reports and
+ * benchmarks): the kernel's name with its template shape, NUL-terminated in
+ * name_host (cap bytes), the time steps per launch (*depth) and the owned
+ * tile of a CTA (*tile_x x *tile_y points); depth and tiles may be NULL.
+ * EW_EINVAL when no wave-solve of this shape has been tuned in this process,
+ * or for a grid other than a 2D box.  Host only. */
+ew_status ew_tuned_variant(const ew_grid* grid, int nvec, char* name_host, int cap, int* depth, int* tile_x,
+                           int* tile_y);
 
 /* Launch accounting, for benchmarks.  While enabled (process-wide), the
  * library counts every kernel it launches and brackets each launch of its

@@ -248,6 +248,51 @@ def ew_arnoldi_eigs(grid: Grid, params, eigs, start=None, vecs=None, stream=None
     return lam, report, st
 
 
+def tb2d_choice(grid: Grid, nvec=1):
+    """The tuned 2D blocked-step variant for this grid and nvec: dict(kernel,
+    depth, tile) or None if none has been tuned yet."""
+    buf = ctypes.create_string_buffer(256)
+    b, tx, ty = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    st = lib.ew_tuned_variant(grid.handle, int(nvec), buf, 256, ctypes.byref(b), ctypes.byref(tx), ctypes.byref(ty))
+    if st != _lib.EW_OK:
+        return None
+    return dict(kernel=buf.value.decode(), depth=b.value, tile=[tx.value, ty.value])
+
+
+def _report_dict(rep, nw):
+    return dict(n_converged=rep.n_converged, wave_solves=rep.wave_solves,
+                wave_solves_fp64=rep.wave_solves_fp64, restarts=rep.restarts, seconds=rep.seconds,
+                beta=np.array(rep.beta[:nw]), eig_res=np.array(rep.eig_res[:nw]),
+                lambda_stage1=np.array(rep.lambda_stage1[:nw]),
+                eig_res_stage1=np.array(rep.eig_res_stage1[:nw]),
+                lambda_rel_change=np.array(rep.lambda_rel_change[:nw]))
+
+
+def ew_arnoldi_eigs_batched(grids, params, eigs, vecs=None, stream=None, allow_noconv=False):
+    """Eigen-solves of len(grids) problems with batched filter applications.
+    `params` and `eigs` hold one entry per problem; `vecs` (optional) one FP64
+    CUDA tensor (N_q x n_wanted_q) or None per problem.  Returns (list of
+    lambda arrays, list of report dicts, list of statuses, batched rounds)."""
+    import torch
+    n = len(grids)
+    G = (ctypes.c_void_p * n)(*[g.handle.value if hasattr(g.handle, "value") else g.handle for g in grids])
+    P = (ew_filter_params * n)(*params)
+    E = (_lib.ew_eigs_params * n)(*eigs)
+    lams = [np.zeros(e.n_wanted) for e in eigs]
+    L = (ctypes.POINTER(ctypes.c_double) * n)(*[x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for x in lams])
+    V = None
+    if vecs is not None:
+        V = (ctypes.c_void_p * n)(*[(_ptr(vecs[q], torch.float64, grids[q].size * eigs[q].n_wanted).value
+                                     if vecs[q] is not None else None) for q in range(n)])
+    R = (_lib.ew_eigs_report * n)()
+    S = (ctypes.c_int * n)()
+    rounds = ctypes.c_int(0)
+    st = lib.ew_arnoldi_eigs_batched(n, G, P, E, L, V, R, S, ctypes.byref(rounds), _stream(stream))
+    if st != _lib.EW_OK and not (allow_noconv and all(x in (_lib.EW_OK, _lib.EW_ENOCONV) for x in S)):
+        check(st)
+    return lams, [_report_dict(R[q], eigs[q].n_wanted) for q in range(n)], list(S), rounds.value
+
+
 def ew_implicit_step_mg(grid: Grid, half_dt2, rhs, x, mg, stream=None):
     """Multigrid solve of (I - half_dt2 L_h) x = rhs; x holds the initial guess
     and receives the result.  Returns (convergence factor, cycles run)."""

@@ -118,6 +118,12 @@ lib.ew_arnoldi_eigs.argtypes = [_vp, ctypes.POINTER(ew_filter_params), ctypes.PO
 lib.ew_filter_apply_batched.argtypes = [_i, ctypes.POINTER(_vp), ctypes.POINTER(ew_filter_params),
                                         ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip, _vp]
 lib.ew_filter_apply_batched.restype = ctypes.c_int
+lib.ew_arnoldi_eigs_batched.argtypes = [_i, ctypes.POINTER(_vp), ctypes.POINTER(ew_filter_params),
+                                        ctypes.POINTER(ew_eigs_params), ctypes.POINTER(_dp), ctypes.POINTER(_vp),
+                                        ctypes.POINTER(ew_eigs_report), _ip, _ip, _vp]
+lib.ew_arnoldi_eigs_batched.restype = ctypes.c_int
+lib.ew_tuned_variant.argtypes = [_vp, _i, ctypes.c_char_p, _i, _ip, _ip, _ip]
+lib.ew_tuned_variant.restype = ctypes.c_int
 lib.ew_filter_apply_noalloc.argtypes = [_vp, ctypes.POINTER(ew_filter_params), _vp, _vp, _vp]
 lib.ew_filter_apply_noalloc.restype = ctypes.c_int
 lib.ew_implicit_step_mg.argtypes =[_vp, _d, _vp, _vp, ctypes.POINTER(ew_mg_params), _dp, _ip, _vp]

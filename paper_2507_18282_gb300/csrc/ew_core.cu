@@ -239,7 +239,7 @@ static ew_status filter_apply_t(ew_grid* g, const ew_filter_params* p, const Fil
     if (p->scheme == EW_IMPLICIT) return implicit_wave_solve_any(g, plan, p, vin, vout, nvec, st);
     const T* cdev = nullptr;
     EW_TRY(upload_weights<T>(g, plan, st, &cdev));
-    EW_TRY(g->fields.reserve((size_t)4 * nvec * field_stride(g->geom.N) * sizeof(T)));
+    EW_TRY(g->fields.reserve((size_t)4 * nvec * wave_field_stride(g->geom) * sizeof(T)));
     return explicit_wave_solve<T>(g->geom, plan, cdev, vin, vout, nvec, (T*)g->fields.ptr, p->temporal_block, st);
 }
 
@@ -260,7 +260,7 @@ static ew_status filter_apply_dd(ew_grid* g, const ew_filter_params* p, const Fi
     const int64_t n = g->geom.N * (int64_t)nvec;
     const dd* cdev = nullptr;
     EW_TRY(upload_weights<dd>(g, plan, st, &cdev));
-    EW_TRY(g->fields.reserve((size_t)4 * nvec * field_stride(g->geom.N) * sizeof(dd)));
+    EW_TRY(g->fields.reserve((size_t)4 * nvec * wave_field_stride(g->geom) * sizeof(dd)));
     EW_TRY(g->pairs.reserve((size_t)2 * n * sizeof(dd)));
     dd* din = (dd*)g->pairs.ptr;
     dd* dout = din + n;
@@ -494,6 +494,7 @@ static ew_status rayleigh_t(ew_grid* g, const T* phi, int nvec, double* lam_host
     EW_CUDA_TRY(cudaMemcpyAsync(h, dnum, sizeof(double) * 2 * nvec, cudaMemcpyDeviceToHost, st));
     EW_CUDA_TRY(cudaStreamSynchronize(st));
     EW_TRY(rb2d_check_timeout());  // a register-blocked wave-solve before this point gave up a wait
+    EW_TRY(tma2d_check_timeout());  // the same for a TMA-staged one
     std::vector<double> lam2(nvec);
     for (int j = 0; j < nvec; ++j) {
         double den = h[nvec + j];

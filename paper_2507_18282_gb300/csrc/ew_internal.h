@@ -218,10 +218,34 @@ ew_status rb2d_launch(const Rb2dDesc& d, const GridGeom& g, const float* Ain, co
 // reads (and clears) the flag a staging wait sets when it gives up: EW_ETIMEOUT if set
 ew_status rb2d_check_timeout();
 
+// TMA-staged persistent form of the 2D FP32 blocked step (ew_tma2d.cu)
+struct Tma2dDesc {
+    void* fn;      // boxes with Dirichlet faces only
+    void* fn_gen;  // any faces
+    int nwx, nty, ky, B, TX, TY, threads;
+    size_t smem;
+    int boxw, boxh;  // tensor-map box of one staged field
+};
+const std::vector<Tma2dDesc>& tma2d_variants(int R);
+// fields of padded row pitch pitch2d(nx) (Ain, Bin, Aout, Bout), acc dense
+ew_status tma2d_launch(const Tma2dDesc& d, const GridGeom& g, const float* Ain, const float* Bin, float* Aout,
+                       float* Bout, float* acc, const float* cw, int b, const Stencil<float>& s, int nvec,
+                       int64_t fstride, cudaStream_t st);
+// reads (and clears) the flag a staging wait of the TMA-staged step sets when it gives up
+ew_status tma2d_check_timeout();
+
 // distance between consecutive vectors of a wave-solve's time-level fields:
 // N rounded up to 64 points, so every vector starts on a 256-byte boundary
 // (bulk copies need 16-byte aligned rows)
 inline int64_t field_stride(int64_t N) { return (N + 63) & ~(int64_t)63; }
+// row pitch of the 2D time-level fields in the layout of the TMA-staged step:
+// nx rounded up to 4 points (tensor maps need 16-byte row strides)
+inline int64_t pitch2d(int64_t nx) { return (nx + 3) & ~(int64_t)3; }
+// vector stride of a wave-solve's time-level fields: room for either row
+// pitch on 2D grids
+inline int64_t wave_field_stride(const GridGeom& g) {
+    return g.dim == 2 ? field_stride(pitch2d(g.n[0]) * g.n[1]) : field_stride(g.N);
+}
 
 template <typename T>
 ew_status explicit_wave_solve(const GridGeom& g, const FilterPlan& plan, const T* cdev,
@@ -253,6 +277,33 @@ ew_status tb2d_advance(const GridGeom& g, const FilterPlan& plan, const T* cdev,
                        int64_t L, T* acc, int nvec, int64_t fstride, int tb, cudaStream_t st);
 template <typename T>
 int tb2d_choice(const GridGeom& g, int nvec, int* B, int* TX, int* TY);
+// row pitch of the time-level fields for the variant tb2d_advance will run
+// (pitch2d(nx) for a TMA-staged one, else nx); call after tb2d_tune
+template <typename T>
+int64_t tb2d_field_pitch(const GridGeom& g, const FilterPlan& plan, const T* cdev, T* const* F, T* acc, int nvec,
+                         int64_t fstride, int tb, cudaStream_t st);
+
+// --- eigen-solver (ew_arnoldi.cu) ------------------------------------------
+// S v for nvec vectors, routed by the caller: the batched eigen-solver gathers
+// the filter applications of several solvers into one batched call
+struct FilterHook {
+    virtual ew_status apply(ew_grid* g, const ew_filter_params* p, const FilterPlan& plan, const void* vin, void* vout,
+                            int nvec, cudaStream_t st) = 0;
+
+   protected:
+    ~FilterHook() = default;
+};
+ew_status filter_apply_any(ew_grid* g, const ew_filter_params* p, const FilterPlan& plan, const void* vin, void* vout,
+                           int nvec, cudaStream_t st);
+// ew_arnoldi_eigs without the ABI wrapper; hook (may be NULL) takes every filter application
+ew_status arnoldi_eigs_impl(const ew_grid* grid, const ew_filter_params* params, const ew_eigs_params* ep,
+                            const double* start_dev, double* lambda_host, double* vecs_dev, ew_eigs_report* rep,
+                            cudaStream_t st, FilterHook* hook);
+// ew_filter_apply_batched without the ABI wrapper; *variant (may be NULL; < 0: tune
+// and store the choice) pins the tile variant across calls of different batch shapes
+ew_status filter_apply_batched_impl(int nprob, const ew_grid* const* grids, const ew_filter_params* params,
+                                    const void* const* v_in, void* const* v_out, const int* nvec, cudaStream_t stream,
+                                    int* variant);
 
 // --- reductions (ew_reduce.cu) ---------------------------------------------
 // out[j] = sum_i x_j[i] * y_j[i] for nvec pairs of vectors (FP64 accumulate),

@@ -63,9 +63,10 @@ template <typename T>
 static ew_status noalloc_t(const ew_grid* g, const ew_filter_params* p, const FilterPlan& plan, const T* vin, T* vout,
                            cudaStream_t st) {
     const int64_t N = g->geom.N;
-    if ((size_t)4 * field_stride(N) * sizeof(T) > kFieldBytes)
+    if ((size_t)4 * wave_field_stride(g->geom) * sizeof(T) > kFieldBytes)
         return set_error(EW_EINVAL, "grid too large for ew_filter_apply_noalloc: at most " +
-                                        std::to_string(kFieldBytes / (4 * sizeof(T))) + " active points in this precision");
+                                        std::to_string(kFieldBytes / (4 * sizeof(T))) +
+                                        " points per time level in this precision (2D rows padded to 4 points)");
     if ((size_t)(plan.Nt + 1) * sizeof(T) > kWeightBytes)
         return set_error(EW_EINVAL, "too many time steps for ew_filter_apply_noalloc: at most " +
                                         std::to_string(kWeightBytes / sizeof(T) - 1));

@@ -117,14 +117,17 @@ __global__ void k_apply_L(int64_t nx, int64_t ny, int64_t nz, const T* __restric
 
 // a3: D^1 = (dt^2/2) L V, W^1 = V + D^1, V_out = c0 W^0 + c1 W^1.  `s`
 // carries the dt^2/2 scale.
+// D1 and W1 have row pitch fpitch (>= nx: the padded layout of the
+// TMA-staged 2D step, or nx)
 template <typename T, int DIM, int ORDER>
 __global__ void k_first_step(int64_t nx, int64_t ny, int64_t nz, const T* __restrict__ vin,
                              T* __restrict__ D1, T* __restrict__ W1, T* __restrict__ vout,
-                             Stencil<T> s, T c0, T c1, int64_t fstride) {
+                             Stencil<T> s, T c0, T c1, int64_t fstride, int64_t fpitch) {
     const int64_t N = nx * ny * nz;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nx) return;
     const int64_t v = blockIdx.z / nz, k = blockIdx.z - v * nz, j = blockIdx.y, q = (k * ny + j) * nx + i;
+    const int64_t qf = (k * ny + j) * fpitch + i;
     vin += v * N;
     vout += v * N;
     D1 += v * fstride;
@@ -132,8 +135,8 @@ __global__ void k_first_step(int64_t nx, int64_t ny, int64_t nz, const T* __rest
     T x = vin[q];
     T d = lap_global<T, DIM, ORDER>(vin, s, q, i, j, k, nx, ny, nz);
     T w1 = x + d;
-    D1[q] = d;
-    W1[q] = w1;
+    D1[qf] = d;
+    W1[qf] = w1;
     vout[q] = c0 * x + c1 * w1;
 }
 
@@ -320,19 +323,20 @@ ew_status step3d(const GridGeom& g, const T* W, T* D, T* Wout, T* acc, T c, cons
 
 template <typename T>
 ew_status first_step(const GridGeom& g, const T* vin, T* D1, T* W1, T* vout,
-                            const FilterPlan& plan, int nvec, int64_t fstride, cudaStream_t st) {
+                            const FilterPlan& plan, int nvec, int64_t fstride, cudaStream_t st, int64_t fpitch) {
+    if (fpitch < g.n[0] || (g.dim == 3 && fpitch != g.n[0])) return set_error(EW_EINVAL, "first step: bad field pitch");
     Stencil<T> s = make_stencil<T>(g, 0.5 * plan.dt * plan.dt);
     EW_TRY(pt_check(g, nvec));
     dim3 grid = pt_grid(g, nvec), blk(pt_threads(g.n[0]));
     T c0 = T(plan.cn(0)), c1 = T(plan.cn(1));
     if (g.dim == 2 && g.order == 2)
-        k_first_step<T, 2, 2><<<grid, blk, 0, st>>>(g.n[0], g.n[1], 1, vin, D1, W1, vout, s, c0, c1, fstride);
+        k_first_step<T, 2, 2><<<grid, blk, 0, st>>>(g.n[0], g.n[1], 1, vin, D1, W1, vout, s, c0, c1, fstride, fpitch);
     else if (g.dim == 2)
-        k_first_step<T, 2, 4><<<grid, blk, 0, st>>>(g.n[0], g.n[1], 1, vin, D1, W1, vout, s, c0, c1, fstride);
+        k_first_step<T, 2, 4><<<grid, blk, 0, st>>>(g.n[0], g.n[1], 1, vin, D1, W1, vout, s, c0, c1, fstride, fpitch);
     else if (g.order == 2)
-        k_first_step<T, 3, 2><<<grid, blk, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, D1, W1, vout, s, c0, c1, fstride);
+        k_first_step<T, 3, 2><<<grid, blk, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, D1, W1, vout, s, c0, c1, fstride, fpitch);
     else
-        k_first_step<T, 3, 4><<<grid, blk, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, D1, W1, vout, s, c0, c1, fstride);
+        k_first_step<T, 3, 4><<<grid, blk, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, D1, W1, vout, s, c0, c1, fstride, fpitch);
     EW_CUDA_TRY(cudaGetLastError());
     count_launch();
     return EW_OK;
@@ -396,9 +400,12 @@ ew_status explicit_wave_solve(const GridGeom& g, const FilterPlan& plan, const T
     } else {
         if (g.map) return mapped_wave_solve<T>(g, plan, vin, vout, nvec, fields, st);  // one step per launch
     }
-    if (use_resident<T>(g, nvec) && temporal_block == 0) return resident<T>(g, vin, vout, cdev, plan, nvec, st);
-    // fields are laid out [field][vector][point]
-    const int64_t fstride = field_stride(g.N);
+    // the variant override EW_TB2D_VARIANT (a tuning and testing hook) selects a
+    // blocked kernel, so it also bypasses the one-CTA path of small grids
+    if (use_resident<T>(g, nvec) && temporal_block == 0 && !getenv("EW_TB2D_VARIANT"))
+        return resident<T>(g, vin, vout, cdev, plan, nvec, st);
+    // fields are laid out [field][vector][point]; 2D rows may be padded (pitch2d)
+    const int64_t fstride = wave_field_stride(g);
     T* F[4];
     for (int q = 0; q < 4; ++q) F[q] = fields + (int64_t)q * nvec * fstride;
     const bool blocked = g.dim == 2 && temporal_block != 1;
@@ -408,7 +415,9 @@ ew_status explicit_wave_solve(const GridGeom& g, const FilterPlan& plan, const T
         if (g.dim == 3 && g.order == 2 && temporal_block == 0)
             EW_TRY(tb3d_tune<T>(g, plan, cdev, F, vout, nvec, fstride, st));
     // F[0] = D^n, F[1] = W^n; the unblocked steps write W^{n+1} to F[2] and swap
-    EW_TRY(first_step<T>(g, vin, F[0], F[1], vout, plan, nvec, fstride, st));
+    const int64_t fpitch =
+        blocked ? tb2d_field_pitch<T>(g, plan, cdev, F, vout, nvec, fstride, temporal_block, st) : g.n[0];
+    EW_TRY(first_step<T>(g, vin, F[0], F[1], vout, plan, nvec, fstride, st, fpitch));
     if (blocked) {
         int prv = 0, cur = 1;
         return tb2d_advance<T>(g, plan, cdev, F, &prv, &cur, 1, vout, nvec, fstride, temporal_block, st);
@@ -444,7 +453,7 @@ template ew_status explicit_wave_solve<dd>(const GridGeom&, const FilterPlan&, c
 
 namespace ew {
 template ew_status first_step<float>(const GridGeom&, const float*, float*, float*, float*, const FilterPlan&, int,
-                                     int64_t, cudaStream_t);
+                                     int64_t, cudaStream_t, int64_t);
 template ew_status first_step<double>(const GridGeom&, const double*, double*, double*, double*, const FilterPlan&,
-                                      int, int64_t, cudaStream_t);
+                                      int, int64_t, cudaStream_t, int64_t);
 }  // namespace ew

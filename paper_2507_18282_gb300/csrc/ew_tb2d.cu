@@ -34,6 +34,8 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <cstring>
+#include <string>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -54,8 +56,9 @@ struct Tb2dVariant {
     void* fn;  // kernel pointer, boxes with Dirichlet faces only
     void* fn_gen;  // the same kernel for any faces (see ext2 in ew_tb2d_dev.cuh)
     int minb, fence;
-    int kind = 0;  // 0: shared-memory form (k_step_tb2d), 1: register-blocked persistent form (k_step_rb2d)
-    int rb = -1;   // index into rb2d_variants(R) for kind 1
+    int kind = 0;  // 0: shared-memory form (k_step_tb2d), 1: register-blocked persistent form (k_step_rb2d),
+                   // 2: TMA-staged persistent form (k_step_tma2d, padded field pitch)
+    int rb = -1;   // index into rb2d_variants(R) for kind 1, into tma2d_variants(R) for kind 2
 };
 
 // FP32 lists also carry the register-blocked forms; the autotuner picks among all
@@ -65,6 +68,19 @@ static std::vector<Tb2dVariant> with_rb2d(std::vector<Tb2dVariant> v, int R) {
         Tb2dVariant x{1, rb[i].nty, rb[i].ky, rb[i].B, rb[i].TX, rb[i].TY, rb[i].threads, rb[i].smem, rb[i].fn,
                       rb[i].fn_gen, 1, 0};
         x.kind = 1;
+        x.rb = (int)i;
+        v.push_back(x);
+    }
+    return v;
+}
+
+// FP32 lists also carry the TMA-staged forms
+static std::vector<Tb2dVariant> with_tma2d(std::vector<Tb2dVariant> v, int R) {
+    const auto& tm = tma2d_variants(R);
+    for (size_t i = 0; i < tm.size(); ++i) {
+        Tb2dVariant x{tm[i].nwx, tm[i].nty, tm[i].ky, tm[i].B, tm[i].TX, tm[i].TY, tm[i].threads, tm[i].smem, tm[i].fn,
+                      tm[i].fn_gen, 1, 0};
+        x.kind = 2;
         x.rb = (int)i;
         v.push_back(x);
     }
@@ -85,7 +101,7 @@ static const std::vector<Tb2dVariant>& tb2d_variants();
 // Index 0 of each list is the default used when the caller fixes the depth.
 template <>
 const std::vector<Tb2dVariant>& tb2d_variants<float, 2>() {
-    static const std::vector<Tb2dVariant> v = with_rb2d({
+    static const std::vector<Tb2dVariant> v = with_tma2d(with_rb2d({
         EW_TB2D_VARIANT(float, 2, 2, 8, 8, 4, 2),  EW_TB2D_VARIANT(float, 2, 2, 8, 8, 2, 2),
         EW_TB2D_VARIANT(float, 2, 2, 8, 8, 3, 2),  EW_TB2D_VARIANT(float, 2, 2, 16, 8, 4, 1),
         EW_TB2D_VARIANT(float, 2, 2, 16, 8, 6, 1), EW_TB2D_VARIANT(float, 2, 2, 4, 16, 4, 2),
@@ -93,17 +109,17 @@ const std::vector<Tb2dVariant>& tb2d_variants<float, 2>() {
         EW_TB2D_VARIANT(float, 2, 2, 16, 8, 8, 1), EW_TB2D_VARIANT(float, 2, 1, 16, 8, 4, 2),
         // depths whose tile count fills whole waves of 152 SMs on common grids
         EW_TB2D_VARIANT(float, 2, 2, 16, 8, 7, 1), EW_TB2D_VARIANT(float, 2, 2, 16, 8, 5, 1),
-    }, 2);
+    }, 2), 2);
     return v;
 }
 template <>
 const std::vector<Tb2dVariant>& tb2d_variants<float, 1>() {
-    static const std::vector<Tb2dVariant> v = with_rb2d({
+    static const std::vector<Tb2dVariant> v = with_tma2d(with_rb2d({
         EW_TB2D_VARIANT(float, 1, 2, 8, 8, 4, 2),  EW_TB2D_VARIANT(float, 1, 2, 8, 8, 8, 2),
         EW_TB2D_VARIANT(float, 1, 2, 8, 8, 2, 2),  EW_TB2D_VARIANT(float, 1, 2, 16, 8, 8, 1),
         EW_TB2D_VARIANT(float, 1, 2, 16, 8, 12, 1), EW_TB2D_VARIANT(float, 1, 2, 4, 16, 8, 2),
         EW_TB2D_VARIANT(float, 1, 4, 4, 8, 8, 2),
-    }, 1);
+    }, 1), 1);
     return v;
 }
 template <>
@@ -172,6 +188,12 @@ static ew_status launch_variant(const Tb2dVariant& var, const GridGeom& g, const
                                s, nvec, fstride, st);
         return set_error(EW_EUNSUPPORTED, "register-blocked step is FP32 only");
     }
+    if (var.kind == 2) {
+        if constexpr (sizeof(T) == 4)
+            return tma2d_launch(tma2d_variants(g.order == 2 ? 1 : 2)[(size_t)var.rb], g, Ain, Bin, Aout, Bout, acc, cw,
+                                b, s, nvec, fstride, st);
+        return set_error(EW_EUNSUPPORTED, "TMA-staged step is FP32 only");
+    }
     void* fn = g.bc ? var.fn_gen : var.fn;
     {
         // raise the dynamic shared-memory limit once per kernel and device
@@ -207,14 +229,28 @@ template <typename T>
 static ew_status autotune(const GridGeom& g, T* const* F, T* acc, const T* cw, const Stencil<T>& s, int nvec,
                           int64_t fstride, cudaStream_t st, int* out, bool lookup_only) {
     const auto& vars = variants_for<T>(g.order);
-    // the register-blocked forms stage rows with 16-byte bulk copies
+    // the register-blocked forms stage rows with 16-byte bulk copies; the
+    // TMA-staged forms also need room for the padded row pitch
     const bool rb_ok = sizeof(T) == 4 && fstride % 4 == 0 &&
                        (((uintptr_t)F[0] | (uintptr_t)F[1] | (uintptr_t)F[2] | (uintptr_t)F[3]) & 15) == 0;
+    const bool tma_ok = rb_ok && g.dim == 2 && fstride >= pitch2d(g.n[0]) * g.n[1];
+    auto usable = [&](const Tb2dVariant& v) { return v.kind == 0 || (v.kind == 1 && rb_ok) || (v.kind == 2 && tma_ok); };
     // EW_TB2D_VARIANT=i fixes the variant (index into this precision's and
-    // order's list) instead of timing them: a tuning and testing override
+    // order's list) instead of timing them, "rb:i" / "tma:i" the i-th
+    // register-blocked / TMA-staged one: a tuning and testing override
     if (const char* fv = getenv("EW_TB2D_VARIANT")) {
-        const int i = atoi(fv);
-        if (i < 0 || i >= (int)vars.size() || (vars[(size_t)i].kind == 1 && !rb_ok))
+        int kind = 0;
+        const char* num = fv;
+        if (!strncmp(fv, "rb:", 3)) kind = 1, num = fv + 3;
+        if (!strncmp(fv, "tma:", 4)) kind = 2, num = fv + 4;
+        int i = atoi(num);
+        if (kind) {  // the i-th entry of that kind
+            int k = -1;
+            for (size_t j = 0; j < vars.size() && k < 0; ++j)
+                if (vars[j].kind == kind && i-- == 0) k = (int)j;
+            i = k;
+        }
+        if (i < 0 || i >= (int)vars.size() || !usable(vars[(size_t)i]))
             return set_error(EW_EINVAL, "EW_TB2D_VARIANT: no such variant for this grid");
         *out = i;
         return EW_OK;
@@ -243,7 +279,7 @@ static ew_status autotune(const GridGeom& g, T* const* F, T* acc, const T* cw, c
     ew_status status = EW_OK;
     for (size_t i = 0; i < vars.size() && status == EW_OK; ++i) {
         const auto& var = vars[i];
-        if (var.kind == 1 && !rb_ok) continue;
+        if (!usable(var)) continue;
         int b = var.B;
         // one warm launch, then three timed ones
         for (int rep = 0; rep < 4 && status == EW_OK; ++rep) {
@@ -253,6 +289,7 @@ static ew_status autotune(const GridGeom& g, T* const* F, T* acc, const T* cw, c
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         if (status == EW_OK && var.kind == 1) status = rb2d_check_timeout();
+        if (status == EW_OK && var.kind == 2) status = tma2d_check_timeout();
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         double rate = (double)b * 3.0 / std::max(ms, 1e-6f);  // time steps per ms
@@ -260,7 +297,7 @@ static ew_status autotune(const GridGeom& g, T* const* F, T* acc, const T* cw, c
             fprintf(stderr, "[ew tune] %lldx%lld order %d %s: variant %zu (warps %dx%d, rows %d, depth %d, "
                             "minb %d, fence %d, tile %dx%d)%s: %.4f ms/step\n",
                     (long long)g.n[0], (long long)g.n[1], g.order, type_name<T>(), i, var.nwx,
-                    var.nty, var.ky, var.B, var.minb, var.fence, var.TX, var.TY, var.kind ? " register-blocked" : "",
+                    var.nty, var.ky, var.B, var.minb, var.fence, var.TX, var.TY, var.kind == 1 ? " register-blocked" : var.kind == 2 ? " TMA-staged" : "",
                     1.0 / rate);
         if (rate > best_rate) {
             best_rate = rate;
@@ -327,6 +364,27 @@ template ew_status tb2d_advance<double>(const GridGeom&, const FilterPlan&, cons
 template ew_status tb2d_advance<dd>(const GridGeom&, const FilterPlan&, const dd*, dd* const*, int*,
                                         int*, int64_t, dd*, int, int64_t, int, cudaStream_t);
 
+// row pitch of the time-level fields the advance will use: the padded pitch
+// when the variant it runs is a TMA-staged one, nx otherwise (call after the
+// tuner)
+template <typename T>
+int64_t tb2d_field_pitch(const GridGeom& g, const FilterPlan& plan, const T* cdev, T* const* F, T* acc, int nvec,
+                         int64_t fstride, int tb, cudaStream_t st) {
+    if (g.dim != 2 || sizeof(T) != 4) return g.n[0];
+    int vi = 0;
+    if (tb == 0) {
+        Stencil<T> s = make_stencil<T>(g, plan.dt * plan.dt);
+        if (autotune<T>(g, F, acc, cdev, s, nvec, fstride, st, &vi, true) != EW_OK) return g.n[0];
+    }
+    return variants_for<T>(g.order)[(size_t)vi].kind == 2 ? pitch2d(g.n[0]) : g.n[0];
+}
+template int64_t tb2d_field_pitch<float>(const GridGeom&, const FilterPlan&, const float*, float* const*, float*, int,
+                                         int64_t, int, cudaStream_t);
+template int64_t tb2d_field_pitch<double>(const GridGeom&, const FilterPlan&, const double*, double* const*, double*,
+                                          int, int64_t, int, cudaStream_t);
+template int64_t tb2d_field_pitch<dd>(const GridGeom&, const FilterPlan&, const dd*, dd* const*, dd*, int, int64_t,
+                                      int, cudaStream_t);
+
 // description of the tuned choice (for reports)
 template <typename T>
 int tb2d_choice(const GridGeom& g, int nvec, int* B, int* TX, int* TY) {
@@ -346,4 +404,52 @@ template int tb2d_choice<float>(const GridGeom&, int, int*, int*, int*);
 template int tb2d_choice<double>(const GridGeom&, int, int*, int*, int*);
 template int tb2d_choice<dd>(const GridGeom&, int, int*, int*, int*);
 
+// the tuned variant's kernel with its template shape, e.g. "k_step_tma2d<2, 2, 12, 8, 4, false>"
+template <typename T>
+static std::string tb2d_choice_name(const GridGeom& g, int vi) {
+    const auto& v = variants_for<T>(g.order)[(size_t)vi];
+    const int R = g.order == 2 ? 1 : 2;
+    const char* gen = g.bc ? "true" : "false";
+    char buf[160];
+    if (v.kind == 2)
+        snprintf(buf, sizeof buf, "k_step_tma2d<%d, %d, %d, %d, %d, %s>", R, v.nwx, v.nty, v.ky, v.B, gen);
+    else if (v.kind == 1)
+        snprintf(buf, sizeof buf, "k_step_rb2d<%d, %d, %d, %d, %s>", R, v.nty, v.ky, v.B, gen);
+    else
+        snprintf(buf, sizeof buf, "k_step_tb2d<%s, %d, %d, %d, %d, %d, %d, %s>",
+                 sizeof(T) == 4 ? "float" : std::is_same<T, dd>::value ? "dd" : "double", R, v.nwx, v.nty, v.ky,
+                 v.B, v.minb, gen);
+    return buf;
+}
+
 }  // namespace ew
+
+using namespace ew;
+
+extern "C" ew_status ew_tuned_variant(const ew_grid* grid, int nvec, char* name_host, int cap, int* depth,
+                                      int* tile_x, int* tile_y) try {
+    clear_error();
+    if (!grid || !name_host || cap < 1) return set_error(EW_EINVAL, "null argument");
+    const GridGeom& g = grid->geom;
+    if (g.dim != 2 || g.map) return set_error(EW_EINVAL, "not a 2D box grid");
+    int B = 0, TX = 0, TY = 0, vi = -1;
+    std::string name;
+    if (grid->prec == EW_FP32) {
+        vi = tb2d_choice<float>(g, nvec, &B, &TX, &TY);
+        if (vi >= 0) name = tb2d_choice_name<float>(g, vi);
+    } else if (grid->prec == EW_FP64) {
+        vi = tb2d_choice<double>(g, nvec, &B, &TX, &TY);
+        if (vi >= 0) name = tb2d_choice_name<double>(g, vi);
+    } else {
+        vi = tb2d_choice<dd>(g, nvec, &B, &TX, &TY);
+        if (vi >= 0) name = tb2d_choice_name<dd>(g, vi);
+    }
+    if (vi < 0) return set_error(EW_EINVAL, "no wave-solve of this grid shape and nvec has been tuned");
+    snprintf(name_host, (size_t)cap, "%s", name.c_str());
+    if (depth) *depth = B;
+    if (tile_x) *tile_x = TX;
+    if (tile_y) *tile_y = TY;
+    return EW_OK;
+} catch (...) {
+    return abi_exception();
+}

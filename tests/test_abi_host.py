@@ -220,6 +220,8 @@ calls = {
     "ew_rayleigh": (None, None, 1, None, None, None),
     "ew_power_iteration": (None, None, None, 1, 0.0, None, None, None, None),
     "ew_arnoldi_eigs": (None, None, None, None, None, None, None, None),
+    "ew_arnoldi_eigs_batched": (0, None, None, None, None, None, None, None, None, None),
+    "ew_tuned_variant": (None, 1, None, 0, None, None, None),
     "ew_implicit_step_mg": (None, 0.0, None, None, None, None, None, None),
     "ew_smoother_forward": (None, None, None, None, None),
     "ew_smoother_backward": (None, None, None, None, None, None),
@@ -237,7 +239,7 @@ print("ok", len(calls))
     import sys
     r = subprocess.run([sys.executable, "-c", script], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
-    assert r.stdout.strip() == "ok 16"
+    assert r.stdout.strip() == "ok 18"
 
 
 def test_header_is_plain_c(ew, tmp_path):

@@ -307,28 +307,21 @@ def test_invalid_calls(ew):
     g.close()
 
 
-def test_register_blocked_staging_wait_gives_up_cleanly(ew, monkeypatch):
-    """Failure handling without a fault: the register-blocked kernel's waits on
-    its bulk copies are bounded (about 2 s).  A test hook makes every CTA expect
-    16 bytes that never arrive, so its first wait runs out; the kernel records
-    that and returns, the next synchronising call reports EW_ETIMEOUT, and the
-    device stays usable: the same wave-solve without the hook then matches the
+@pytest.mark.parametrize("form", ["rb:0", "tma:0"])
+def test_staging_wait_gives_up_cleanly(ew, form, monkeypatch):
+    """Failure handling without a fault: the waits of the register-blocked
+    (rb) and TMA-staged (tma) forms on their asynchronous copies are bounded
+    (about 2 s).  A test hook makes every CTA expect 16 bytes that never
+    arrive, so its first wait runs out; the kernel records that and returns,
+    the next synchronising call reports EW_ETIMEOUT, and the device stays
+    usable: the same wave-solve without the hook then matches the
     shared-memory kernel bit for bit."""
     n, L = (300, 140), (1.0, 0.5)
-    count = 0
-    for i in range(64):  # the register-blocked forms are the last entries of the variant list
-        monkeypatch.setenv("EW_TB2D_VARIANT", str(i))
-        try:
-            _run(ew, n, L, 4, "fp32", 400.0)
-        except ew.EWError:
-            break
-        count += 1
-    last = count - 1
     g = ew.ew_grid_create(2, n, L, order=4, prec="fp32")
-    p = ew.filter_params(400.0, num_periods=1)  # about 10 steps: two launches, each wait runs out once
+    p = ew.filter_params(400.0, num_periods=1)  # about 10 steps: a few launches, each wait runs out once
     vin = torch.tensor(ew_inputs.uniform_pm1(77, g.size), dtype=torch.float32, device="cuda")
     out = torch.empty_like(vin)
-    monkeypatch.setenv("EW_TB2D_VARIANT", str(last))
+    monkeypatch.setenv("EW_TB2D_VARIANT", form)
     monkeypatch.setenv("EW_TEST_RB2D_STALL", "1")
     ew.ew_filter_apply(g, p, vin, out)  # returns before the kernels run
     with pytest.raises(ew.EWError) as e:
@@ -343,6 +336,30 @@ def test_register_blocked_staging_wait_gives_up_cleanly(ew, monkeypatch):
     assert torch.equal(out, ref)
     ew.ew_rayleigh(g, out, nvec=1)  # no stale report left behind
     g.close()
+
+
+@pytest.mark.parametrize("n,order", [((2047, 3071), 4), ((5, 3), 4), ((3, 200), 2), ((129, 7), 4), ((301, 97), 2),
+                                     ((116, 84), 4), ((117, 85), 4)])
+def test_tma_staged_forms_bit_identical(ew, n, order, monkeypatch):
+    """Every TMA-staged variant against the shared-memory form (variant 0), bit
+    for bit: the full-size rectangle, boxes narrower than the halo (the
+    reflection wraps across the whole axis), one-tile and ragged grids, two
+    vectors (one tensor-map plane each)."""
+    L = tuple(0.01 * x for x in n)
+    omega = 120.0 if n[0] > 1000 else 30.0
+    monkeypatch.setenv("EW_TB2D_VARIANT", "0")
+    _, ref, _ = _run(ew, n, L, order, "fp32", omega, nvec=2, seed=31)
+    count = 0
+    for i in range(16):
+        monkeypatch.setenv("EW_TB2D_VARIANT", "tma:%d" % i)
+        try:
+            _, out, _ = _run(ew, n, L, order, "fp32", omega, nvec=2, seed=31)
+        except ew.EWError as e:
+            assert "EW_TB2D_VARIANT" in str(e)
+            break
+        assert np.array_equal(out, ref), "TMA variant %d differs" % i
+        count += 1
+    assert count >= 4
 
 
 @pytest.mark.parametrize("k", [(2, 3, 4), (19, 17, 21)])
