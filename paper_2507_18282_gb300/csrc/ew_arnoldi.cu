@@ -126,9 +126,19 @@ static void inv_upper(int n, const std::vector<double>& R, std::vector<double>& 
 // ---------------------------------------------------------------------------
 // one Krylov-Schur run
 // ---------------------------------------------------------------------------
+// S applied to nvec vectors: filter_apply_any, or through the hook of a
+// caller that gathers the applications of several solvers (the batched
+// eigen-solver, ew_eigs_batched.cu)
+static ew_status apply_filter(FilterHook* hook, ew_grid* g, const ew_filter_params* p, const FilterPlan& plan,
+                              const void* vin, void* vout, int nvec, cudaStream_t st) {
+    if (hook) return hook->apply(g, p, plan, vin, vout, nvec, st);
+    return filter_apply_any(g, p, plan, vin, vout, nvec, st);
+}
+
 struct KSRun {
     ew_grid* g;
     const ew_filter_params* p;
+    FilterHook* hook = nullptr;
     FilterPlan plan;
     int64_t N;
     int b, m, nw;
@@ -216,13 +226,13 @@ struct KSRun {
                 Xs = W;
             }
             EW_TRY((convert<double, float>(N * b, Xs, (float*)fin, st)));
-            EW_TRY(filter_apply_any(g, p, plan, fin, fout, b, st));
+            EW_TRY(apply_filter(hook, g, p, plan, fin, fout, b, st));
             EW_TRY((convert<float, double>(N * b, (const float*)fout, W, st)));
         } else if (sym) {
             EW_TRY(launch_wsqrt<double>(g->geom, X, symtmp, b, -1, st));
-            EW_TRY(filter_apply_any(g, p, plan, symtmp, W, b, st));
+            EW_TRY(apply_filter(hook, g, p, plan, symtmp, W, b, st));
         } else {
-            EW_TRY(filter_apply_any(g, p, plan, X, W, b, st));
+            EW_TRY(apply_filter(hook, g, p, plan, X, W, b, st));
         }
         if (sym) EW_TRY(launch_wsqrt<double>(g->geom, W, W, b, 1, st));
         wave_solves += b;
@@ -422,9 +432,22 @@ struct KSRun {
     }
 };
 
+// Trapezoid sum S(mu) = sum_{n=0}^{N_t} sigma_n cos(mu t^n) (sigma_0 = sigma_{N_t}
+// = dt/2, else dt) in closed form: with theta = mu dt the cosine sum is the
+// Dirichlet kernel, sum_{n=0}^{N} cos(n theta) = sin((N + 1/2) theta) / (2 sin(theta/2))
+// + 1/2, so S = dt [sin((N + 1/2) theta) / (2 sin(theta/2)) - cos(N theta) / 2]
+// (S(0) = T_f).  O(1) per value instead of N_t + 1 terms.
+static double trapezoid_cos_sum(double mu, double dt, int64_t N) {
+    const double th = mu * dt, sh = sin(0.5 * th);
+    if (fabs(sh) < 1e-300) return dt * (double)N;
+    return dt * (sin(((double)N + 0.5) * th) / (2.0 * sh) - 0.5 * cos((double)N * th));
+}
+
 // beta_d of the discrete filter at a spatial eigenvalue lambda: eq. betad with
 // the time-corrected frequency of eq. discreteExplicitLambdaTilde (explicit)
 // or eq. discreteCorr (implicit).  Modes beyond the leapfrog limit get -1.
+// With c_n = (2/T_f) sigma_n (cos(omega t^n) - alpha_d/2) (eq. filterQuadrature),
+// sum_n c_n cos(lambda~ t^n) = [S(omega - lambda~) + S(omega + lambda~) - alpha_d S(lambda~)] / T_f.
 double filter_beta(const FilterPlan& plan, ew_scheme scheme, double lam) {
     const double dt = plan.dt;
     double x;
@@ -435,9 +458,10 @@ double filter_beta(const FilterPlan& plan, ew_scheme scheme, double lam) {
     }
     if (x >= 1.0) return -1.0;
     const double lt = 2.0 / dt * asin(x);
-    double s = 0.0;
-    for (size_t n = 0; n < plan.c.size(); ++n) s += plan.c[n] * cos(lt * (double)n * dt);
-    return s;
+    const int64_t N = plan.Nt;
+    return (trapezoid_cos_sum(plan.omega - lt, dt, N) + trapezoid_cos_sum(plan.omega + lt, dt, N) -
+            plan.alpha_d * trapezoid_cos_sum(lt, dt, N)) /
+           plan.Tf;
 }
 
 // Mixed-precision iterative refinement of the invariant subspace found by the
@@ -553,11 +577,11 @@ static ew_status refine_ir(KSRun& ks, KSRun& kr, ew_grid* g64, ew_grid* gimg, in
             int nb = std::min(16, nw - c0);
             if (sym) {
                 EW_TRY(launch_wsqrt<double>(g64->geom, kr.V + (size_t)c0 * N, Qfree, nb, -1, kr.st));
-                EW_TRY(filter_apply_any(gimg, ks.p, ks.plan, Qfree, W64 + (size_t)c0 * N, nb, kr.st));
+                EW_TRY(apply_filter(ks.hook, gimg, ks.p, ks.plan, Qfree, W64 + (size_t)c0 * N, nb, kr.st));
                 EW_TRY(launch_wsqrt<double>(g64->geom, W64 + (size_t)c0 * N, W64 + (size_t)c0 * N, nb, 1, kr.st));
             } else {
-                EW_TRY(filter_apply_any(gimg, ks.p, ks.plan, kr.V + (size_t)c0 * N, W64 + (size_t)c0 * N, nb,
-                                        kr.st));
+                EW_TRY(apply_filter(ks.hook, gimg, ks.p, ks.plan, kr.V + (size_t)c0 * N, W64 + (size_t)c0 * N, nb,
+                                    kr.st));
             }
         }
         *ws64 += nw;
@@ -653,10 +677,11 @@ static ew_status make_twin_fp64(const ew_grid* g, ew_grid** out) {
 
 using namespace ew;
 
-extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params* params,
-                                     const ew_eigs_params* ep, const double* start_dev, double* lambda_host,
-                                     double* vecs_dev, ew_eigs_report* rep, cudaStream_t st) try {
-    clear_error();
+namespace ew {
+
+ew_status arnoldi_eigs_impl(const ew_grid* grid, const ew_filter_params* params, const ew_eigs_params* ep,
+                            const double* start_dev, double* lambda_host, double* vecs_dev, ew_eigs_report* rep,
+                            cudaStream_t st, FilterHook* hook) {
     auto t0 = std::chrono::steady_clock::now();
     if (!grid || !params || !ep || !lambda_host) return set_error(EW_EINVAL, "null argument");
     int dev = -1;
@@ -681,6 +706,7 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
     KSRun ks;
     ks.g = g;
     ks.p = params;
+    ks.hook = hook;
     EW_TRY(plan_filter(g->geom, params, &ks.plan));
     ks.N = g->geom.N;
     ks.b = b;
@@ -743,6 +769,7 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
         KSRun kr;
         kr.g = g;
         kr.p = params;
+        kr.hook = hook;
         kr.plan = ks.plan;
         kr.N = ks.N;
         kr.b = nr;
@@ -764,6 +791,7 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
         g64.reset(raw);
         ks2.g = g64.get();
         ks2.p = params;
+        ks2.hook = hook;
         ks2.plan = ks.plan;
         ks2.N = ks.N;
         ks2.b = nw;
@@ -807,6 +835,15 @@ extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params
     r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (rep) *rep = r;
     return status;
+}
+
+}  // namespace ew
+
+extern "C" ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params* params,
+                                     const ew_eigs_params* ep, const double* start_dev, double* lambda_host,
+                                     double* vecs_dev, ew_eigs_report* rep, cudaStream_t st) try {
+    clear_error();
+    return arnoldi_eigs_impl(grid, params, ep, start_dev, lambda_host, vecs_dev, rep, st, nullptr);
 } catch (...) {
     return abi_exception();
 }

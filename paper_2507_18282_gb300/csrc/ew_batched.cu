@@ -8,9 +8,12 @@
 // step of ew_tb2d_dev.cuh, same arithmetic per point as the single-grid path,
 // so results are bit-identical to it).  A problem's descriptor for round r
 // holds its ping-pong buffers, its weights c_{L+1..L+b} and its own b.  The
-// first steps and every round are captured in one CUDA graph and replayed on
-// the caller's stream; the tile shape and depth are chosen by timing one
-// round of each candidate (autotuner), cached per batch shape.
+// first steps and every round are captured in one CUDA graph, instantiated
+// once per batch (problems, buffers, parameters, variant) and kept, with its
+// tables, in a small cache: a repeated call (an eigen-solver's expansion
+// rounds over the same boxes) only replays the graph on the caller's stream.
+// The tile shape and depth are chosen by timing one full batch of each
+// candidate (autotuner), cached per batch shape, or pinned by the caller.
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -27,7 +30,7 @@ namespace ew {
 
 template <typename T>
 ew_status first_step(const GridGeom& g, const T* vin, T* D1, T* W1, T* vout, const FilterPlan& plan, int nvec,
-                     int64_t fstride, cudaStream_t st);
+                     int64_t fstride, cudaStream_t st, int64_t fpitch);
 
 template <typename T>
 struct BatchDesc {
@@ -98,31 +101,54 @@ const std::vector<BVariant>& bvariants<double, 2>() {
     return v;
 }
 
-// process-wide batched workspace (device), one per call at a time
+// One built batch: its descriptor / item tables and weight tables in a device
+// buffer of its own, and the instantiated graph (first steps + rounds).  A call
+// whose problems, buffers, parameters and variant match an entry replays the
+// graph: no table upload, no capture, no instantiation, no host sync.
+struct BatchEntry {
+    std::vector<int64_t> key;
+    uint64_t ws_gen = 0;          // workspace generation the graph's field pointers belong to
+    void* tables = nullptr;       // device: descriptors, items, weights
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;         // kernels in the graph (launch accounting)
+    uint64_t last_use = 0;
+};
+
+// process-wide batched workspace (device fields), one call at a time
 struct BatchCache {
     std::mutex mu;
     void* dev = nullptr;
     size_t dev_bytes = 0;
-    void* host = nullptr;
-    size_t host_bytes = 0;
+    uint64_t ws_gen = 0;
     cudaStream_t cap = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_in = nullptr;
     std::map<std::vector<int64_t>, int> tune;
     std::map<void*, int> occ;
+    std::vector<BatchEntry> entries;
+    uint64_t use_clock = 0;
 };
 static BatchCache g_batch;
+constexpr size_t kMaxBatchEntries = 8;
+
+static void drop_entry(BatchEntry& e) {
+    if (e.exec) cudaGraphExecDestroy(e.exec);  // an in-flight replay completes first
+    if (e.tables) cudaFree(e.tables);
+    e.exec = nullptr;
+    e.tables = nullptr;
+}
 
 struct BProblem {
     GridGeom g;
     FilterPlan plan;
     const void* vin;
     void* vout;
-    size_t field_off, c_off;  // element offsets in the workspace
+    size_t field_off;  // element offset of the problem's four fields in the workspace
+    size_t c_off;      // element offset of its weights in the entry's table buffer
 };
 
 template <typename T>
-static ew_status run_rounds(const std::vector<BProblem>& P, const BVariant& var, T* base, int nsm, cudaStream_t cs,
-                            std::vector<BatchDesc<T>>& hd, std::vector<BatchItem>& hi,
+static ew_status run_rounds(const std::vector<BProblem>& P, const BVariant& var, T* base, const T* cbase, int nsm,
+                            cudaStream_t cs, std::vector<BatchDesc<T>>& hd, std::vector<BatchItem>& hi,
                             std::vector<std::pair<size_t, size_t>>& ranges, bool build_only, BatchDesc<T>* ddesc,
                             BatchItem* ditem, bool gen) {
     // ping-pong state per problem: fields 0..3, level L
@@ -141,7 +167,7 @@ static ew_status run_rounds(const std::vector<BProblem>& P, const BVariant& var,
             d.Aout = F + (size_t)spa[p] * g.N;
             d.Bout = F + (size_t)spb[p] * g.N;
             d.acc = (T*)P[p].vout;
-            d.cw = base + P[p].c_off + L[p] + 1;
+            d.cw = cbase + P[p].c_off + L[p] + 1;
             d.b = (int)std::min<int64_t>(var.B, P[p].plan.Nt - L[p]);
             d.nx = (int)g.n[0];
             d.ny = (int)g.n[1];
@@ -170,13 +196,85 @@ static ew_status run_rounds(const std::vector<BProblem>& P, const BVariant& var,
         int grid = std::min(nitems, nsm);
         void* args[] = {(void*)&dd, (void*)&di, (void*)&nitems};
         EW_CUDA_TRY(cudaLaunchKernel(gen ? var.fn_gen : var.fn, dim3(grid), dim3(var.threads), args, var.smem, cs));
-        count_launch();
     }
     return EW_OK;
 }
 
+// Build one batch for variant v: tables (descriptors, items, weights) in a new
+// device buffer, the first steps and rounds captured on the capture stream and
+// instantiated.  The caller owns the returned entry.
 template <typename T>
-static ew_status batched_t(std::vector<BProblem>& P, int order, cudaStream_t st) {
+static ew_status build_entry(const std::vector<BProblem>& P, const BVariant& var, int nsm, int grid_mult, bool gen,
+                             BatchEntry* e) {
+    T* base = (T*)g_batch.dev;
+    // weights of every problem
+    size_t nc = 0;
+    for (const auto& p : P) nc += p.plan.c.size();
+    std::vector<BatchDesc<T>> hd;
+    std::vector<BatchItem> hi;
+    std::vector<std::pair<size_t, size_t>> rg;
+    EW_TRY(run_rounds<T>(P, var, base, nullptr, nsm, nullptr, hd, hi, rg, true, nullptr, nullptr, gen));
+    const size_t desc_bytes = ((hd.size() * sizeof(BatchDesc<T>) + 255) / 256) * 256;
+    const size_t item_bytes = ((hi.size() * sizeof(BatchItem) + 255) / 256) * 256;
+    const size_t c_bytes = nc * sizeof(T);
+    if (cudaMalloc(&e->tables, desc_bytes + item_bytes + c_bytes) != cudaSuccess) {
+        e->tables = nullptr;
+        cudaGetLastError();
+        return set_error(EW_ENOMEM, "batched table allocation failed");
+    }
+    char* tdev = (char*)e->tables;
+    BatchDesc<T>* ddesc = (BatchDesc<T>*)tdev;
+    BatchItem* ditem = (BatchItem*)(tdev + desc_bytes);
+    T* cdev = (T*)(tdev + desc_bytes + item_bytes);
+    // descriptors again with the real weight addresses
+    hd.clear();
+    hi.clear();
+    rg.clear();
+    EW_TRY(run_rounds<T>(P, var, base, cdev, nsm, nullptr, hd, hi, rg, true, nullptr, nullptr, gen));
+    std::vector<char> host(desc_bytes + item_bytes + c_bytes, 0);
+    std::memcpy(host.data(), hd.data(), hd.size() * sizeof(BatchDesc<T>));
+    std::memcpy(host.data() + desc_bytes, hi.data(), hi.size() * sizeof(BatchItem));
+    T* hc = (T*)(host.data() + desc_bytes + item_bytes);
+    for (const auto& p : P)
+        for (size_t i = 0; i < p.plan.c.size(); ++i) hc[p.c_off + i] = (T)p.plan.c[i];
+    // a synchronous copy: the tables are complete before any replay is queued
+    EW_CUDA_TRY(cudaMemcpy(e->tables, host.data(), host.size(), cudaMemcpyHostToDevice));
+    cudaStream_t s = g_batch.cap;
+    EW_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    ew_status rs = EW_OK;
+    {
+        ProfilePause pause;  // the captured launches are counted at each replay
+        for (const auto& p : P) {
+            T* F = base + p.field_off;
+            if (rs == EW_OK)
+                rs = first_step<T>(p.g, (const T*)p.vin, F, F + p.g.N, (T*)p.vout, p.plan, 1, p.g.N, s, p.g.n[0]);
+        }
+        if (rs == EW_OK) {
+            std::vector<BatchDesc<T>> d2;
+            std::vector<BatchItem> i2;
+            std::vector<std::pair<size_t, size_t>> r2;
+            rs = run_rounds<T>(P, var, base, cdev, nsm * grid_mult, s, d2, i2, r2, false, ddesc, ditem, gen);
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    if (rs != EW_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rs;
+    }
+    if (ce != cudaSuccess) return cuda_error(ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&e->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+        e->exec = nullptr;
+        return cuda_error(ce, "cudaGraphInstantiate");
+    }
+    e->launches = (int64_t)P.size() + (int64_t)rg.size() - 1;  // first steps + rounds
+    return EW_OK;
+}
+
+template <typename T>
+static ew_status batched_t(std::vector<BProblem>& P, int order, cudaStream_t st, int* variant_pin) {
     std::lock_guard<std::mutex> lk(g_batch.mu);
     const auto& vars = order == 2 ? bvariants<T, 1>() : bvariants<T, 2>();
     int dev = 0;
@@ -195,28 +293,19 @@ static ew_status batched_t(std::vector<BProblem>& P, int order, cudaStream_t st)
             g_batch.occ[v.fn] = std::max(occ, 1);
         }
     }
-    // workspace: 4 fields per problem + weight tables
-    size_t off = 0;
+    // workspace: 4 fields per problem; weights live in each entry's tables
+    size_t off = 0, coff = 0;
     for (auto& p : P) {
         p.field_off = off;
         off += 4 * (size_t)p.g.N;
+        p.c_off = coff;
+        coff += p.plan.c.size();
     }
-    for (auto& p : P) {
-        p.c_off = off;
-        off += p.plan.c.size();
-    }
-    size_t field_bytes = ((off * sizeof(T) + 255) / 256) * 256;
-    // tables: worst case over the variants (deepest tiles: the most rounds x tiles)
-    std::vector<std::vector<BatchDesc<T>>> hds(vars.size());
-    std::vector<std::vector<BatchItem>> his(vars.size());
-    std::vector<std::vector<std::pair<size_t, size_t>>> rgs(vars.size());
-    size_t tbl = 0;
-    for (size_t v = 0; v < vars.size(); ++v) {
-        EW_TRY(run_rounds<T>(P, vars[v], nullptr, nsm, nullptr, hds[v], his[v], rgs[v], true, nullptr, nullptr, gen));
-        tbl = std::max(tbl, hds[v].size() * sizeof(BatchDesc<T>) + 256 + his[v].size() * sizeof(BatchItem));
-    }
-    size_t need = field_bytes + tbl + 256;
+    const size_t need = ((off * sizeof(T) + 255) / 256) * 256;
     if (g_batch.dev_bytes < need) {
+        // every cached graph points into the old workspace
+        for (auto& e : g_batch.entries) drop_entry(e);
+        g_batch.entries.clear();
         if (g_batch.dev) cudaFree(g_batch.dev);
         g_batch.dev = nullptr;
         g_batch.dev_bytes = 0;
@@ -227,106 +316,43 @@ static ew_status batched_t(std::vector<BProblem>& P, int order, cudaStream_t st)
             return set_error(EW_ENOMEM, "batched workspace allocation failed");
         }
         g_batch.dev_bytes = need;
-    }
-    if (g_batch.host_bytes < need) {
-        if (g_batch.host) cudaFreeHost(g_batch.host);
-        g_batch.host = nullptr;
-        g_batch.host_bytes = 0;
-        cudaError_t e = cudaMallocHost(&g_batch.host, need);
-        if (e != cudaSuccess) {
-            g_batch.host = nullptr;
-            cudaGetLastError();
-            return set_error(EW_ENOMEM, "batched pinned staging allocation failed");
-        }
-        g_batch.host_bytes = need;
+        ++g_batch.ws_gen;
     }
     if (!g_batch.cap) EW_CUDA_TRY(cudaStreamCreateWithFlags(&g_batch.cap, cudaStreamNonBlocking));
     if (!g_batch.ev_in) EW_CUDA_TRY(cudaEventCreateWithFlags(&g_batch.ev_in, cudaEventDisableTiming));
-    if (!g_batch.ev_out) EW_CUDA_TRY(cudaEventCreateWithFlags(&g_batch.ev_out, cudaEventDisableTiming));
-    T* base = (T*)g_batch.dev;
-    char* tdev = (char*)g_batch.dev + field_bytes;
-    // weights (host staging -> device)
-    EW_CUDA_TRY(cudaStreamSynchronize(st));  // the pinned staging may still feed a previous copy
-    T* hw = (T*)g_batch.host;
-    for (auto& p : P)
-        for (size_t i = 0; i < p.plan.c.size(); ++i) hw[p.c_off - P[0].c_off + i] = (T)p.plan.c[i];
-    size_t cbytes = (off - P[0].c_off) * sizeof(T);
-    EW_CUDA_TRY(cudaMemcpyAsync(base + P[0].c_off, hw, cbytes, cudaMemcpyHostToDevice, st));
-    EW_CUDA_TRY(cudaStreamSynchronize(st));
 
-    // choose the variant for this batch shape (time one full batched solve per candidate)
-    std::vector<int64_t> key = {(int64_t)sizeof(T), order, dev};
+    // the variant: pinned by the caller, tuned for this batch shape before, or tuned now
+    std::vector<int64_t> tkey = {(int64_t)sizeof(T), order, dev};
     for (auto& p : P) {
-        key.push_back(p.g.n[0]);
-        key.push_back(p.g.n[1]);
-        key.push_back(p.plan.Nt);
+        tkey.push_back(p.g.n[0]);
+        tkey.push_back(p.g.n[1]);
+        tkey.push_back(p.plan.Nt);
     }
-    auto upload_and_run = [&](size_t v, cudaStream_t s) -> ew_status {
-        // descriptors with their real device addresses, then items
-        std::vector<BatchDesc<T>> hd;
-        std::vector<BatchItem> hi;
-        std::vector<std::pair<size_t, size_t>> rg;
-        EW_TRY(run_rounds<T>(P, vars[v], base, nsm, nullptr, hd, hi, rg, true, nullptr, nullptr, gen));
-        BatchDesc<T>* ddesc = (BatchDesc<T>*)tdev;
-        BatchItem* ditem = (BatchItem*)(tdev + ((hd.size() * sizeof(BatchDesc<T>) + 255) / 256) * 256);
-        char* hstage = (char*)g_batch.host + field_bytes;
-        std::memcpy(hstage, hd.data(), hd.size() * sizeof(BatchDesc<T>));
-        std::memcpy(hstage + ((char*)ditem - tdev), hi.data(), hi.size() * sizeof(BatchItem));
-        size_t tb = ((char*)ditem - tdev) + hi.size() * sizeof(BatchItem);
-        EW_CUDA_TRY(cudaMemcpyAsync(tdev, hstage, tb, cudaMemcpyHostToDevice, st));
-        // the first step of every problem, then the rounds, captured in one graph
-        EW_CUDA_TRY(cudaEventRecord(g_batch.ev_in, st));
-        EW_CUDA_TRY(cudaStreamWaitEvent(s, g_batch.ev_in, 0));
-        EW_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        ew_status rs = EW_OK;
-        {
-            ProfilePause pause;  // the captured launches are counted once, below
-            for (auto& p : P) {
-                T* F = base + p.field_off;
-                if (rs == EW_OK)
-                    rs = first_step<T>(p.g, (const T*)p.vin, F, F + p.g.N, (T*)p.vout, p.plan, 1, p.g.N, s);
-            }
-            int grid_mult = g_batch.occ[vars[v].fn];
-            if (rs == EW_OK) {
-                std::vector<BatchDesc<T>> d2;
-                std::vector<BatchItem> i2;
-                std::vector<std::pair<size_t, size_t>> r2;
-                rs = run_rounds<T>(P, vars[v], base, nsm * grid_mult, s, d2, i2, r2, false, ddesc, ditem, gen);
-            }
-        }
-        cudaGraph_t graph = nullptr;
-        cudaError_t ce = cudaStreamEndCapture(s, &graph);
-        if (rs != EW_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return rs;
-        }
-        if (ce != cudaSuccess) return cuda_error(ce, "cudaStreamEndCapture");
-        cudaGraphExec_t exec = nullptr;
-        ce = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) return cuda_error(ce, "cudaGraphInstantiate");
-        ce = cudaGraphLaunch(exec, st);
-        cudaGraphExecDestroy(exec);
-        if (ce != cudaSuccess) return cuda_error(ce, "cudaGraphLaunch");
-        count_launch((int64_t)P.size() + (int64_t)rg.size() - 1);  // first steps + rounds in the graph
-        return EW_OK;
-    };
     int vi = 0;
-    auto it = g_batch.tune.find(key);
-    if (it != g_batch.tune.end()) {
+    auto it = g_batch.tune.find(tkey);
+    if (variant_pin && *variant_pin >= 0 && *variant_pin < (int)vars.size()) {
+        vi = *variant_pin;
+    } else if (it != g_batch.tune.end()) {
         vi = it->second;
     } else if (vars.size() > 1) {
+        // time one full batched solve per candidate (entries built for timing only)
         EventPair ev;
         EW_TRY(ev.create());
-        cudaEvent_t e0 = ev.a, e1 = ev.b;
         float best = 1e30f;
         for (size_t v = 0; v < vars.size(); ++v) {
-            EW_CUDA_TRY(cudaEventRecord(e0, st));
-            EW_TRY(upload_and_run(v, g_batch.cap));
-            EW_CUDA_TRY(cudaEventRecord(e1, st));
-            EW_CUDA_TRY(cudaEventSynchronize(e1));
+            BatchEntry e;
+            ew_status bs = build_entry<T>(P, vars[v], nsm, g_batch.occ[vars[v].fn], gen, &e);
+            if (bs == EW_OK) {
+                cudaEventRecord(ev.a, st);
+                cudaError_t ce = cudaGraphLaunch(e.exec, st);
+                cudaEventRecord(ev.b, st);
+                cudaEventSynchronize(ev.b);
+                if (ce != cudaSuccess) bs = cuda_error(ce, "cudaGraphLaunch");
+            }
+            drop_entry(e);
+            EW_TRY(bs);
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventElapsedTime(&ms, ev.a, ev.b);
             if (getenv("EW_TUNE_LOG"))
                 fprintf(stderr, "[ew tune] batched %zu problems: variant %zu (depth %d, tile %dx%d): %.3f ms\n",
                         P.size(), v, vars[v].B, vars[v].TX, vars[v].TY, ms);
@@ -335,19 +361,61 @@ static ew_status batched_t(std::vector<BProblem>& P, int order, cudaStream_t st)
                 vi = (int)v;
             }
         }
-        g_batch.tune[key] = vi;
+        g_batch.tune[tkey] = vi;
     }
-    return upload_and_run((size_t)vi, g_batch.cap);
+    if (variant_pin) *variant_pin = vi;
+
+    // the full key of this call: variant, faces, and per problem its shape, steps,
+    // weights' parameters and buffers (the graph bakes them all in)
+    std::vector<int64_t> key = {(int64_t)sizeof(T), order, dev, vi, gen};
+    for (const auto& p : P) {
+        int64_t ob, db;
+        std::memcpy(&ob, &p.plan.omega, 8);
+        std::memcpy(&db, &p.plan.dt, 8);
+        key.insert(key.end(), {p.g.n[0], p.g.n[1], (int64_t)p.g.bc, p.plan.Nt, ob, db, (int64_t)(uintptr_t)p.vin,
+                               (int64_t)(uintptr_t)p.vout});
+        std::memcpy(&db, &p.g.h[0], 8);
+        key.push_back(db);
+        std::memcpy(&db, &p.g.h[1], 8);
+        key.push_back(db);
+    }
+    BatchEntry* hit = nullptr;
+    for (auto& e : g_batch.entries)
+        if (e.ws_gen == g_batch.ws_gen && e.key == key) hit = &e;
+    if (!hit) {
+        if (g_batch.entries.size() >= kMaxBatchEntries) {  // evict the least recently used
+            size_t old = 0;
+            for (size_t i = 1; i < g_batch.entries.size(); ++i)
+                if (g_batch.entries[i].last_use < g_batch.entries[old].last_use) old = i;
+            drop_entry(g_batch.entries[old]);
+            g_batch.entries.erase(g_batch.entries.begin() + (long)old);
+        }
+        BatchEntry e;
+        ew_status bs = build_entry<T>(P, vars[(size_t)vi], nsm, g_batch.occ[vars[(size_t)vi].fn], gen, &e);
+        if (bs != EW_OK) {
+            drop_entry(e);
+            return bs;
+        }
+        e.key = key;
+        e.ws_gen = g_batch.ws_gen;
+        g_batch.entries.push_back(e);
+        hit = &g_batch.entries.back();
+    }
+    hit->last_use = ++g_batch.use_clock;
+    EW_CUDA_TRY(cudaGraphLaunch(hit->exec, st));
+    count_launch(hit->launches);
+    return EW_OK;
 }
 
 }  // namespace ew
 
 using namespace ew;
 
-extern "C" ew_status ew_filter_apply_batched(int nprob, const ew_grid* const* grids, const ew_filter_params* params,
-                                             const void* const* v_in, void* const* v_out, const int* nvec,
-                                             cudaStream_t stream) try {
-    clear_error();
+namespace ew {
+
+ew_status filter_apply_batched_impl(int nprob, const ew_grid* const* grids, const ew_filter_params* params,
+                                    const void* const* v_in, void* const* v_out, const int* nvec, cudaStream_t stream,
+                                    int* variant) {
     if (nprob < 1 || !grids || !params || !v_in || !v_out) return set_error(EW_EINVAL, "bad arguments");
     int dev = -1;
     EW_CUDA_TRY(cudaGetDevice(&dev));
@@ -386,8 +454,17 @@ extern "C" ew_status ew_filter_apply_batched(int nprob, const ew_grid* const* gr
             EW_TRY(ew_filter_apply(grids[q], &params[q], v_in[q], v_out[q], nvec ? nvec[q] : 1, stream));
         return EW_OK;
     }
-    if (g0->prec == EW_FP32) return batched_t<float>(P, g0->geom.order, stream);
-    return batched_t<double>(P, g0->geom.order, stream);
+    if (g0->prec == EW_FP32) return batched_t<float>(P, g0->geom.order, stream, variant);
+    return batched_t<double>(P, g0->geom.order, stream, variant);
+}
+
+}  // namespace ew
+
+extern "C" ew_status ew_filter_apply_batched(int nprob, const ew_grid* const* grids, const ew_filter_params* params,
+                                             const void* const* v_in, void* const* v_out, const int* nvec,
+                                             cudaStream_t stream) try {
+    clear_error();
+    return filter_apply_batched_impl(nprob, grids, params, v_in, v_out, nvec, stream, nullptr);
 } catch (...) {
     return abi_exception();
 }

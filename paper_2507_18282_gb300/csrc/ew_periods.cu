@@ -118,19 +118,17 @@ ew_status ew_choose_num_periods(const ew_grid* grid, const ew_filter_params* par
         ew_filter_params p = *params;
         p.num_periods = np;
         FilterPlan plan;
-        // The estimate sums the N_t + 1 weights for each of at least N_a + 1
-        // eigenvalues.  A candidate past that budget, or past the longest
-        // wave-solve, is not evaluated (CR = 1), nor are the longer ones; its
-        // weight table is never built.
+        // A candidate past the longest wave-solve is not evaluated (CR = 1), nor
+        // are the longer ones.  (beta_d costs O(1) per eigenvalue: filter_beta
+        // sums the trapezoid rule in closed form.)
         const ew_status ps = plan_filter(g, &p, &plan, false);
-        if (np > 1 && (ps != EW_OK || (double)want * (double)(plan.Nt + 1) > 4e9)) {
+        if (np > 1 && ps != EW_OK) {
             clear_error();
             if (cr_host)
                 for (int k = np; k <= max_periods; k *= 2) cr_host[idx++] = 1.0;
             break;
         }
         EW_TRY(ps);
-        EW_TRY(plan_filter(g, &p, &plan));
         // Widen a window [omega - w, omega + w] until the filter cannot put an
         // eigenvalue outside it among the top N_a + 1: beyond distance d of omega
         // (in time-corrected frequency) the filter's sum of cosines is bounded by
@@ -158,7 +156,6 @@ ew_status ew_choose_num_periods(const ew_grid* grid, const ew_filter_params* par
                 continue;
             }
             if (lam.size() < want) break;
-            if ((double)lam.size() * (double)plan.c.size() > 4e9) break;  // too costly: keep the last estimate
             beta.resize(lam.size());
             for (size_t i = 0; i < lam.size(); ++i) beta[i] = filter_beta(plan, sch, lam[i]);
             std::sort(beta.begin(), beta.end(), std::greater<double>());

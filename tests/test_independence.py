@@ -74,7 +74,8 @@ def test_bench_uses_the_oracle_only_in_its_cpu_legs():
     sites = _oracle_import_sites(os.path.join(ROOT, "bench.py"))
     assert sites
     for fn, tests in sites:
-        assert fn in ("cpu_baseline_sample", "run_reference", "run_ours"), fn
+        # _oracle_sample_worker: one process of the all-cores CPU baseline
+        assert fn in ("cpu_baseline_sample", "_oracle_sample_worker", "run_reference", "run_ours"), fn
         if fn == "run_ours":
             assert any("no_cpu_baseline" in t for t in tests), tests
 
