@@ -43,15 +43,26 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# one bench step: S applied to a block of NVEC vectors (the block a Krylov expansion hands the
+# filter), which also makes the timed region long enough for the clock sampler
+NVEC = 16
 WORKLOAD = dict(workload="rect2d_2047x3071_order4_fp32_explicit", n=(2047, 3071), length=(1.0, 1.5),
-                order=4, omega=150.0, num_periods=1, cfl=0.8, precision="fp32", nvec=1)
+                order=4, omega=150.0, num_periods=1, cfl=0.8, precision="fp32", nvec=NVEC)
 METRIC = "Gcell-steps/s of fused filter step"
 UNIT = "Gcell-steps/s"
 BYTES_PER_POINT_PER_LAUNCH = 24  # 6 x FP32: D^n, W^n, acc in; D^{n+b}, W^{n+b}, acc out
 DOMINANT_KERNEL = "k_step_tb2d"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
-# the device code of the dominant kernel (the tuner and variant table in ew_tb2d.cu are host code)
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_2507_18282_gb300", "csrc", "ew_tb2d_dev.cuh")]
+
+
+def workload_config(nt, world, temporal_block=0):
+    """The config object of both arms' JSON lines (the same workload)."""
+    w = WORKLOAD
+    return {"workload": w["workload"], "grid": list(w["n"]), "length": list(w["length"]),
+            "order": w["order"], "omega": w["omega"], "num_periods": w["num_periods"],
+            "time_steps_per_step": nt, "temporal_block": temporal_block or "default",
+            "nvec": w["nvec"], "l2": "flushed between timed steps (512 MB write)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
 def parse():
@@ -63,6 +74,9 @@ def parse():
     ap.add_argument("--temporal-block", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline line only: skip the 3D roofline and the time-to-eigenpairs runs")
+    ap.add_argument("--no-tts", action="store_true", help="skip the time-to-eigenpairs runs")
     ap.add_argument("--workload", choices=["rect2d", "cube3d", "batched", "implicit3d", "mg3d", "eigs2d", "scaling2d",
                                            "mgtol", "mapped2d"],
                     default="rect2d",
@@ -102,7 +116,7 @@ def whole_job_rate(world, units_per_rank, total_ms):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -117,7 +131,7 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
             atexit.register(self._end)  # no sampler outlives the bench, whatever ends it
         except Exception:
@@ -164,20 +178,23 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(sources):
+    """sha256 of the device-code files (paths relative to the package's csrc)."""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        h.update(open(f, "rb").read())
+    for f in sources:
+        h.update(open(os.path.join(ROOT, "paper_2507_18282_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
 
-def traffic_for_kernel():
+def traffic_for_kernel(choice):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, or None when the kernel source changed since it was taken."""
+    summary, or None when it was taken on another kernel, or when the kernel's
+    source changed since."""
     try:
         t = json.load(open(TRAFFIC_FILE))
-        src = kernel_source_hash()
-        if t.get("kernel_source_sha256") != src:
+        if choice is None or t.get("kernel") != choice.get("kernel"):
+            return None
+        if t.get("kernel_source_sha256") != kernel_source_hash(t.get("sources", [])):
             return None
         return t.get("dram_bytes_per_launch")
     except Exception:
@@ -213,6 +230,45 @@ def cpu_baseline_sample(target_s):
                       "2047x3071 order-4 wave-solve, %.1f s" % (steps, prm["Nt"], t)}, steps, t
 
 
+def _oracle_sample_worker(args):
+    """One process of the all-cores baseline: the oracle on the first `steps`
+    time steps of the workload's wave-solve (its own start vector)."""
+    steps, seed = args
+    import ew_inputs
+    from oracle import oracle as O
+    w = WORKLOAD
+    og = O.Grid(w["n"], w["length"], w["order"])
+    spp = O.steps_per_period_cfl(og, w["omega"], w["cfl"])
+    prm = O.filter_params(w["omega"], w["num_periods"], spp)
+    sub = dict(prm)
+    sub["Nt"] = steps
+    sub["c"] = prm["c"][:steps + 1]
+    v = ew_inputs.uniform_pm1(seed, og.size)
+    O.filter_explicit(og, sub, v)  # warm (page-in)
+    t0 = time.perf_counter()
+    O.filter_explicit(og, sub, v)
+    return og.size * steps, time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(steps):
+    """The oracle as it stands (one thread each) in one process per host core,
+    all at once, each on its own vector: the host's aggregate FP64 rate."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")  # never fork a process that may hold a CUDA context
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_sample_worker, [(steps, 9000 + i) for i in range(cores)])
+    wall = time.perf_counter() - t0
+    cells = sum(r[0] for r in res)
+    slowest = max(r[1] for r in res)
+    return {"value": cells / slowest / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "FP64 oracle (plain C, one thread per process), %d processes at once, each the first %d time "
+                      "steps of the same 2047x3071 order-4 wave-solve on its own vector; value = all processes' "
+                      "cell-steps over the slowest one's time (%.1f s; %.1f s with start-up)" %
+                      (cores, steps, slowest, wall)}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -223,8 +279,6 @@ def run_reference(args):
     # each step: a bounded sample (first `s` time steps) of the wave-solve on the full grid
     info, s_steps, t = cpu_baseline_sample(min(args.cpu_seconds, 8.0))
     per_step = max(2, min(s_steps, 8))
-    import numpy as np
-
     import ew_inputs as I
     w = WORKLOAD
     og = O.Grid(w["n"], w["length"], w["order"])
@@ -245,10 +299,11 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": w["workload"], "sample_time_steps_per_step": per_step,
-                       "l2": "not applicable (CPU)"},
+            "config": workload_config(prm["Nt"], world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "first %d of %d time steps of the wave-solve per step" % (per_step, prm["Nt"])},
+                             "sample": "FP64 oracle on one host core: each step the first %d of the %d time steps "
+                                       "of the wave-solve of one vector (the rate, not the step, is the workload's)"
+                                       % (per_step, prm["Nt"])},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -266,12 +321,13 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2507_18282_gb300 as ew
     w = WORKLOAD
+    nvec = w["nvec"]
     g = ew.ew_grid_create(2, w["n"], w["length"], order=w["order"], prec=w["precision"])
     p = ew.filter_params(w["omega"], num_periods=w["num_periods"], cfl=w["cfl"],
                          temporal_block=args.temporal_block)
     info, _ = ew.ew_filter_setup(g, p)
     N, Nt = g.size, info["Nt"]
-    v_host = ew_inputs.uniform_pm1(ew_inputs.BASE_SEED + 1, N).astype(np.float32)
+    v_host = ew_inputs.uniform_pm1(ew_inputs.BASE_SEED + 1, N * nvec).astype(np.float32)
     vin = torch.from_numpy(v_host).cuda()
     vout = torch.empty_like(vin)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -282,7 +338,7 @@ def run_ours(args):
             torch.distributed.barrier()
 
     for _ in range(args.warmup):
-        ew.ew_filter_apply(g, p, vin, vout)
+        ew.ew_filter_apply(g, p, vin, vout, nvec=nvec)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -295,7 +351,7 @@ def run_ours(args):
     for k in range(args.steps):
         flush.fill_(float(k))            # L2 flush between timed steps (not timed)
         ev[k][0].record(stream)
-        ew.ew_filter_apply(g, p, vin, vout)
+        ew.ew_filter_apply(g, p, vin, vout, nvec=nvec)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     prof = ew.ew_profile_read()
@@ -304,7 +360,7 @@ def run_ours(args):
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
     barrier()
     total_ms = max_over_ranks(total_ms, world, "cuda")
-    value = whole_job_rate(world, N * Nt * args.steps, total_ms)
+    value = whole_job_rate(world, N * Nt * nvec * args.steps, total_ms)
 
     # ---- end to end through the C ABI from pinned host buffers ------------------
     h_in = torch.from_numpy(v_host).pin_memory()
@@ -313,7 +369,7 @@ def run_ours(args):
     d_out = torch.empty_like(vin)
     for _ in range(2):
         d_in.copy_(h_in, non_blocking=True)
-        ew.ew_filter_apply(g, p, d_in, d_out)
+        ew.ew_filter_apply(g, p, d_in, d_out, nvec=nvec)
         h_out.copy_(d_out, non_blocking=True)
     torch.cuda.synchronize()
     barrier()
@@ -323,13 +379,13 @@ def run_ours(args):
         flush.fill_(float(k))
         e0.record(stream)
         d_in.copy_(h_in, non_blocking=True)
-        ew.ew_filter_apply(g, p, d_in, d_out)
+        ew.ew_filter_apply(g, p, d_in, d_out, nvec=nvec)
         h_out.copy_(d_out, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
     e2e_ms = max_over_ranks(e2e_ms, world, "cuda")
-    e2e_value = whole_job_rate(world, N * Nt * args.steps, e2e_ms)
+    e2e_value = whole_job_rate(world, N * Nt * nvec * args.steps, e2e_ms)
     # sanity: the result is finite and nonzero
     outn = float(h_out.abs().max())
     assert np.isfinite(outn) and outn > 0.0
@@ -342,37 +398,123 @@ def run_ours(args):
     bytes_per_launch = BYTES_PER_POINT_PER_LAUNCH * points_per_launch
     achieved = bytes_per_launch / (mean_launch_ms / 1e3) / 1e9
     peak = float(pk["hbm_gbs"])
-    roofline = {"bound": "hbm", "kernel": DOMINANT_KERNEL, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for_kernel(),
+    choice = ew.tb2d_choice(g, nvec)
+    roofline = {"bound": "hbm", "kernel": choice["kernel"] if choice else DOMINANT_KERNEL, "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for_kernel(choice),
                 "peak_source": pk_kind, "bytes_per_launch": bytes_per_launch,
                 "mean_launch_ms": mean_launch_ms,
                 "cell_steps_per_launch": prof["fused_cell_steps"] / max(launches, 1),
-                "share_of_step_time": prof["fused_ms"] / max(total_ms, 1e-9)}
+                "share_of_step_time": prof["fused_ms"] / max(total_ms, 1e-9),
+                "variant": choice}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w["workload"], "grid": list(w["n"]), "length": list(w["length"]),
-                       "order": w["order"], "omega": w["omega"], "num_periods": w["num_periods"],
-                       "time_steps_per_step": Nt, "temporal_block": args.temporal_block or "default",
-                       "nvec": 1, "l2": "flushed between timed steps (512 MB write)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * 4),
-                    "d2h_bytes_per_step": int(N * 4)},
+            "config": workload_config(Nt, world, args.temporal_block),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * nvec * 4),
+                    "d2h_bytes_per_step": int(N * nvec * 4)},
             "gpu_launches": int(prof["launches"]),
             "roofline": roofline,
             "clocks": clk}
+    g.close()
+    del vin, vout, d_in, d_out, h_in, h_out
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_extras:
+        # secondary measurements on the same GPU, after the headline's timed region
+        clocks = ClockSampler(local)
+        clocks.start()
+        line["roofline_3d"] = measure_cube3d(ew, flush, pk, pk_kind, 3, 1)
+        if not args.no_tts:
+            line["time_to_solution"] = measure_eigs2d(ew, "pair_and_plain", 0)
+        line["clocks_extras"] = clocks.stop()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
         O.build()
-        cb, _, _ = cpu_baseline_sample(args.cpu_seconds)
+        cb, steps, _ = cpu_baseline_sample(args.cpu_seconds)
         line["cpu_baseline"] = cb
-    g.close()
+        try:
+            line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(max(2, steps // 2))
+        except Exception as e:  # reported, not fatal: the one-core baseline stands
+            line["cpu_baseline_all_cores"] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def measure_cube3d(ew, flush, pk, pk_kind, steps, warmup):
+    """One wave-solve (117 steps) of the 511^3 order-2 FP32 cube workload: the
+    clean HBM case (534 MB per field), throughput and the roofline of its
+    temporally blocked kernel."""
+    import torch
+
+    import ew_inputs
+    n, L = (511, 511, 511), (1.0, 1.0, 1.0)
+    g = ew.ew_grid_create(3, n, L, order=2, prec="fp32")
+    p = ew.filter_params(60.0, num_periods=1)
+    info, _ = ew.ew_filter_setup(g, p)
+    v = torch.tensor(ew_inputs.uniform_pm1(ew_inputs.BASE_SEED + 2, g.size), dtype=torch.float32, device="cuda")
+    o = torch.empty_like(v)
+    ew.ew_profile_enable(True)
+    ms = _timed(lambda: ew.ew_filter_apply(g, p, v, o), steps, warmup, flush)
+    prof = ew.ew_profile_read()
+    ew.ew_profile_enable(False)
+    g.close()
+    cells = g.size * info["Nt"] * steps
+    launches = max(prof["fused_launches"], 1)
+    mean = prof["fused_ms"] / launches
+    bytes_launch = 24 * prof["fused_points"] / launches  # per launch: W^n, D^n, acc in; W^{n+b}, D^{n+b}, acc out
+    achieved = bytes_launch / (mean / 1e3) / 1e9
+    return dict(workload="cube3d_511_order2_fp32_explicit", metric=METRIC, unit=UNIT,
+                value=cells / (ms / 1e3) / 1e9, ms_per_step=ms / steps, steps=steps, warmup=warmup,
+                time_steps_per_step=info["Nt"], l2="flushed between timed steps (512 MB write)",
+                bound="hbm", kernel="k_step_tb3d<float, tuned depth>", bytes_per_launch=bytes_launch,
+                mean_launch_ms=mean, achieved=achieved, peak=float(pk["hbm_gbs"]), frac=achieved / float(pk["hbm_gbs"]),
+                peak_source=pk_kind, share_of_step_time=prof["fused_ms"] / max(ms, 1e-9))
+
+
+def measure_eigs2d(ew, which, num_periods):
+    """Time to the 8 eigenpairs nearest omega = 150 on the 2047 x 3071 order-4
+    rectangle at eig-res <= 1e-8: FP32 wave-solves + refinement against FP64
+    wave-solves throughout, each pair's error against the closed form."""
+    import numpy as np
+    import torch
+    n, L = (2047, 3071), (1.0, 1.5)
+    runs = {}
+    cr_est = None
+    if num_periods <= 0:  # the convergence estimate of simultaneous iteration over the box's spectrum
+        g = ew.ew_grid_create(2, n, L, order=4, prec="fp32")
+        num_periods, cr = ew.ew_choose_num_periods(g, ew.filter_params(150.0), 8, 32, max_periods=1024)
+        cr_est = float(cr[num_periods.bit_length() - 1])
+        g.close()
+    # the plain arm stops on the Ritz residual of S: 2e-11 brings every eig-res below 1e-8
+    arms = [("fp32_fp64_refine", "fp32", 1, 0.0), ("fp32_pair_refine", "fp32", 3, 0.0),
+            ("plain_fp64", "fp64", 0, 2e-11)]
+    if which == "pair_and_plain":
+        arms = [a for a in arms if a[0] != "fp32_fp64_refine"]
+    else:
+        arms = [a for a in arms if a[0].startswith(which)]
+    exact = closed_form_lambdas(n, L, 4, 150.0, 40)
+    for name, prec, refine, tol in arms:
+        g = ew.ew_grid_create(2, n, L, order=4, prec=prec)
+        p = ew.filter_params(150.0, num_periods=num_periods)
+        e = ew.eigs_params(8, krylov_dim=32, block=4, tol=tol, seed=7, refine_fp64=refine, max_wave_solves=600)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        lam, rep, st = ew.ew_arnoldi_eigs(g, p, e, allow_noconv=True)
+        torch.cuda.synchronize()
+        sec = time.time() - t0
+        err = [float(np.min(np.abs(exact - x)) / x) for x in lam]
+        runs[name] = dict(seconds=sec, status=int(st), wave_solves=int(rep["wave_solves"]),
+                          wave_solves_fp64=int(rep["wave_solves_fp64"]), max_eig_res=float(rep["eig_res"].max()),
+                          lambda_=[float(x) for x in lam], rel_err_vs_closed_form=err, max_rel_err=max(err))
+        g.close()
+    return dict(workload="eigs_rect2d_2047x3071_order4_8_nearest_omega150", unit="s",
+                metric="s to 8 eigenpairs at 1e-8 resid vs plain", num_periods=num_periods, cr_estimate=cr_est,
+                krylov_dim=32, block=4, runs=runs,
+                speedup={k: runs["plain_fp64"]["seconds"] / r["seconds"] for k, r in runs.items()
+                         if k != "plain_fp64"} if "plain_fp64" in runs else None)
 
 
 def _timed(fn, steps, warmup, flush):
@@ -468,25 +610,7 @@ def run_extra(args):
     clocks = ClockSampler(0)  # over the whole workload (tuning and warm-up included)
     clocks.start()
     if w == "cube3d":
-        n, L = (511, 511, 511), (1.0, 1.0, 1.0)
-        g = ew.ew_grid_create(3, n, L, order=2, prec="fp32")
-        p = ew.filter_params(60.0, num_periods=1)
-        info, _ = ew.ew_filter_setup(g, p)
-        v = torch.tensor(ew_inputs.uniform_pm1(ew_inputs.BASE_SEED + 2, g.size), dtype=torch.float32, device="cuda")
-        o = torch.empty_like(v)
-        ew.ew_profile_enable(True)
-        ms = _timed(lambda: ew.ew_filter_apply(g, p, v, o), args.steps, args.warmup, flush)
-        prof = ew.ew_profile_read()
-        ew.ew_profile_enable(False)
-        cells = g.size * info["Nt"] * args.steps
-        launches = max(prof["fused_launches"], 1)
-        mean = prof["fused_ms"] / launches
-        bytes_launch = 24 * prof["fused_points"] / launches  # per launch: W^n, D^n, acc in; W^{n+b}, D^{n+b}, acc out
-        line = dict(workload="cube3d_511_order2_fp32_explicit", metric=METRIC, unit=UNIT,
-                    value=cells / (ms / 1e3) / 1e9, ms_per_step=ms / args.steps, time_steps_per_step=info["Nt"],
-                    roofline=dict(bound="hbm", kernel="k_step_tb3d<float, tuned depth>", bytes_per_launch=bytes_launch,
-                                  achieved=bytes_launch / (mean / 1e3) / 1e9, peak=pk["hbm_gbs"], unit="GB/s",
-                                  frac=bytes_launch / (mean / 1e3) / 1e9 / pk["hbm_gbs"], peak_source=pk_kind))
+        line = measure_cube3d(ew, flush, pk, pk_kind, args.steps, args.warmup)
     elif w == "batched":
         boxes = ew_inputs.batched_boxes(ew_inputs.BASE_SEED + 3)
         grids, params, vin, vout = [], [], [], []
@@ -647,44 +771,7 @@ def run_extra(args):
                 max_eig_res=float(rep["eig_res"][:16].max())))
         line = dict(workload="mgtol_square128_order2_implicit_omega12_16pairs", unit="relative error", rows=rows)
     elif w == "eigs2d":
-        # time to the 8 eigenpairs nearest omega = 150 on the 2047 x 3071 order-4 rectangle:
-        # FP32 wave-solves + FP64 refinement against FP64 wave-solves throughout
-        n, L = (2047, 3071), (1.0, 1.5)
-        runs = {}
-        num_periods, cr_est = args.num_periods, None
-        if num_periods <= 0:  # the convergence estimate of simultaneous iteration over the box's spectrum
-            g = ew.ew_grid_create(2, n, L, order=4, prec="fp32")
-            num_periods, cr = ew.ew_choose_num_periods(g, ew.filter_params(150.0), 8, 32, max_periods=1024)
-            cr_est = float(cr[num_periods.bit_length() - 1])
-            g.close()
-        # the plain arm stops on the Ritz residual of S: 2e-11 brings every eig-res below 1e-8
-        arms = [("fp32_fp64_refine", "fp32", 1, 0.0), ("fp32_pair_refine", "fp32", 3, 0.0),
-                ("plain_fp64", "fp64", 0, 2e-11)]
-        if args.eigs_arm == "pair_and_plain":
-            arms = [a for a in arms if a[0] != "fp32_fp64_refine"]
-        else:
-            arms = [a for a in arms if a[0].startswith(args.eigs_arm)]
-        for name, prec, refine, tol in arms:
-            g = ew.ew_grid_create(2, n, L, order=4, prec=prec)
-            p = ew.filter_params(150.0, num_periods=num_periods)
-            e = ew.eigs_params(8, krylov_dim=32, block=4, tol=tol, seed=7, refine_fp64=refine,
-                               max_wave_solves=600)
-            torch.cuda.synchronize()
-            t0 = time.time()
-            lam, rep, st = ew.ew_arnoldi_eigs(g, p, e, allow_noconv=True)
-            torch.cuda.synchronize()
-            sec = time.time() - t0
-            exact = closed_form_lambdas(n, L, 4, 150.0, 40)
-            err = [float(np.min(np.abs(exact - x)) / x) for x in lam]
-            runs[name] = dict(seconds=sec, status=int(st), wave_solves=rep["wave_solves"],
-                              wave_solves_fp64=rep["wave_solves_fp64"], max_eig_res=float(rep["eig_res"].max()),
-                              lambda_=[float(x) for x in lam], rel_err_vs_closed_form=err,
-                              max_rel_err=max(err))
-            g.close()
-        line = dict(workload="eigs_rect2d_2047x3071_order4_8_nearest_omega150", unit="s",
-                    num_periods=num_periods, cr_estimate=cr_est, metric="s to 8 eigenpairs at 1e-8 resid vs plain", runs=runs,
-                    speedup={k: runs["plain_fp64"]["seconds"] / r["seconds"] for k, r in runs.items()
-                             if k != "plain_fp64"} if "plain_fp64" in runs else None)
+        line = measure_eigs2d(ew, args.eigs_arm, args.num_periods)
     else:
         raise SystemExit("unknown workload %s" % w)
     line.update(dict(n_gpus=1, steps=args.steps, warmup=args.warmup, dtype="f32", data="synthetic",

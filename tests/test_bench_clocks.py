@@ -1,6 +1,6 @@
 """bench.py's clock record on a host without a GPU: a stand-in `nvidia-smi`
 on PATH prints the CSV rows the real one prints under
-`--query-gpu=... --format=csv,noheader,nounits -lms 200`, and the sampler
+`--query-gpu=... --format=csv,noheader,nounits -lms 100`, and the sampler
 must turn them into the median SM clock, the maximum, and the active
 throttle reasons; without any nvidia-smi it records nothing."""
 import os
