@@ -77,8 +77,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="headline line only: skip the 3D roofline and the time-to-eigenpairs runs")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-eigenpairs runs")
-    ap.add_argument("--workload", choices=["rect2d", "cube3d", "batched", "implicit3d", "mg3d", "eigs2d", "scaling2d",
-                                           "mgtol", "mapped2d"],
+    ap.add_argument("--nvec", type=int, default=NVEC, help="vectors per wave-solve of the headline workload")
+    ap.add_argument("--workload", choices=["rect2d", "cube3d", "batched", "batched_eigs", "implicit3d", "mg3d", "eigs2d",
+                                           "eigs3d", "scaling2d", "mgtol", "mapped2d", "sweeps2d"],
                     default="rect2d",
                     help="rect2d is the headline line; the others print their own line")
     ap.add_argument("--eigs-arm", choices=["pair_and_plain", "fp32_fp64", "fp32_pair", "plain"],
@@ -314,6 +315,7 @@ def run_ours(args):
     import torch
 
     import ew_inputs
+    WORKLOAD["nvec"] = args.nvec
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
@@ -474,6 +476,177 @@ def measure_cube3d(ew, flush, pk, pk_kind, steps, warmup):
                 peak_source=pk_kind, share_of_step_time=prof["fused_ms"] / max(ms, 1e-9))
 
 
+def box_closed_form_near(n, length, order, omega, width):
+    """Closed-form discrete Dirichlet eigenvalues lambda of a 2D box within
+    `width` of omega (per-axis symbols as in closed_form_lambdas), sorted."""
+    import numpy as np
+    per_axis = []
+    for nd, ld in zip(n, length):
+        h = ld / (nd + 1)
+        s = np.sin(np.arange(1, nd + 1) * np.pi / (2 * (nd + 1))) ** 2
+        per_axis.append(4.0 / h ** 2 * (s + s * s / 3.0 if order == 4 else s))
+    lam = np.sqrt(per_axis[0][:, None] + per_axis[1][None, :])
+    return np.sort(lam[np.abs(lam - omega) < width])
+
+
+def measure_batched_eigs(ew, krylov_dim=24, block=2):
+    """The 64-box workload (order 2, FP32, each box its own omega): the 4
+    eigenpairs nearest each box's omega, all boxes' eigen-solves at once with
+    batched filter applications (ew_arnoldi_eigs_batched), against the same 64
+    solves one after the other (ew_arnoldi_eigs); N_p per box from the
+    simultaneous-iteration estimate; every eigenvalue against its box's closed
+    form."""
+    import numpy as np
+    import torch
+
+    import ew_inputs
+    boxes = ew_inputs.batched_boxes(ew_inputs.BASE_SEED + 3)
+    grids, params, eigs, nps = [], [], [], []
+    t0 = time.time()
+    for q, b in enumerate(boxes):
+        g = ew.ew_grid_create(2, b["n"], b["length"], order=2, prec="fp32")
+        npd, _ = ew.ew_choose_num_periods(g, ew.filter_params(b["omega"]), 4, krylov_dim, max_periods=1024)
+        grids.append(g)
+        nps.append(npd)
+        params.append(ew.filter_params(b["omega"], num_periods=npd))
+        eigs.append(ew.eigs_params(4, krylov_dim=krylov_dim, block=block, seed=1000 + q, max_wave_solves=1200))
+    plan_s = time.time() - t0
+    cells = sum(g.size * ew.ew_filter_setup(g, p)[0]["Nt"] for g, p in zip(grids, params))
+    torch.cuda.synchronize()
+    t0 = time.time()
+    lams, reps, sts, rounds = ew.ew_arnoldi_eigs_batched(grids, params, eigs, allow_noconv=True)
+    torch.cuda.synchronize()
+    batched_s = time.time() - t0
+    t0 = time.time()
+    seq = [ew.ew_arnoldi_eigs(g, p, e, allow_noconv=True) for g, p, e in zip(grids, params, eigs)]
+    torch.cuda.synchronize()
+    seq_s = time.time() - t0
+    errs, same = [], True
+    for q, b in enumerate(boxes):
+        exact = box_closed_form_near(b["n"], b["length"], 2, b["omega"], 0.25 * b["omega"])
+        for x in lams[q]:
+            errs.append(float(np.min(np.abs(exact - x)) / x))
+        same = same and np.array_equal(lams[q], seq[q][0])
+    for g in grids:
+        g.close()
+    ws = [r["wave_solves"] for r in reps]
+    return dict(workload="batched_eigs_64_boxes_255_to_2047_order2_fp32_4_pairs", unit="s",
+                problems=len(boxes), krylov_dim=krylov_dim, block=block, pairs_per_problem=4,
+                num_periods={"min": int(min(nps)), "max": int(max(nps)), "median": float(np.median(nps))},
+                cell_steps_per_all_box_wave_solve=int(cells), planning_seconds=plan_s,
+                batched=dict(seconds=batched_s, rounds=rounds, statuses=sorted(set(int(x) for x in sts))),
+                sequential=dict(seconds=seq_s, statuses=sorted(set(int(x[2]) for x in seq))),
+                speedup=seq_s / batched_s, batched_equals_sequential=bool(same),
+                wave_solves={"total": int(sum(ws)), "max": int(max(ws)), "min": int(min(ws))},
+                converged=int(sum(r["n_converged"] >= 4 for r in reps)),
+                max_rel_err_vs_closed_form=max(errs), median_rel_err_vs_closed_form=float(np.median(errs)),
+                max_eig_res_fp32=float(max(r["eig_res"].max() for r in reps)))
+
+
+def closed_form_cube(m, order, lo, hi):
+    """Closed-form discrete Dirichlet eigenvalues lambda of the unit cube with m
+    interior points per axis within [lo, hi], with multiplicity, sorted."""
+    import numpy as np
+    h = 1.0 / (m + 1)
+    s = np.sin(np.arange(1, m + 1) * np.pi / (2 * (m + 1))) ** 2
+    mu = 4.0 / h ** 2 * (s + s * s / 3.0 if order == 4 else s)
+    out = []
+    for a in mu:
+        if a > hi * hi:
+            break
+        rest = a + mu[:, None] + mu[None, :]
+        sel = rest[(rest >= lo * lo) & (rest <= hi * hi)]
+        out.append(np.sqrt(sel))
+    return np.sort(np.concatenate(out)) if out else np.zeros(0)
+
+
+def measure_eigs3d(ew, num_periods):
+    """The 511^3 order-2 FP32 cube: the 12 eigenpairs nearest omega = 60, Krylov
+    dimension 48, CGS2 in FP64, block 6 (the cube's largest multiplicity near
+    omega), N_p from the simultaneous-iteration estimate; FP32 first stage only
+    (an FP64 wave-solve of this grid costs about a minute per vector).  Each
+    eigenvalue against the closed form; time and wave-solves."""
+    import numpy as np
+    import torch
+    m = 511
+    g = ew.ew_grid_create(3, (m, m, m), (1.0, 1.0, 1.0), order=2, prec="fp32")
+    cr_est = None
+    if num_periods <= 0:
+        num_periods, cr = ew.ew_choose_num_periods(g, ew.filter_params(60.0), 12, 48, max_periods=1024)
+        cr_est = float(cr[num_periods.bit_length() - 1])
+    p = ew.filter_params(60.0, num_periods=num_periods)
+    info, _ = ew.ew_filter_setup(g, p)
+    e = ew.eigs_params(12, krylov_dim=48, block=6, seed=7, max_wave_solves=240, lock=True)
+    ew.ew_profile_enable(True)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    lam, rep, st = ew.ew_arnoldi_eigs(g, p, e, allow_noconv=True)
+    torch.cuda.synchronize()
+    sec = time.time() - t0
+    prof = ew.ew_profile_read()
+    ew.ew_profile_enable(False)
+    g.close()
+    exact = closed_form_cube(m, 2, 55.0, 65.0)
+    err = [float(np.min(np.abs(exact - x)) / x) for x in lam]
+    return dict(workload="eigs_cube3d_511_order2_fp32_12_nearest_omega60", unit="s", seconds=sec, status=int(st),
+                num_periods=num_periods, cr_estimate=cr_est, krylov_dim=48, block=6, time_steps_per_wave_solve=info["Nt"],
+                wave_solves=int(rep["wave_solves"]), restarts=int(rep["restarts"]),
+                converged=int(rep["n_converged"]), lambda_=[float(x) for x in lam], rel_err_vs_closed_form=err,
+                max_rel_err=max(err), eig_res_fp32=[float(x) for x in rep["eig_res"][:12]],
+                gcell_steps_per_s=prof["fused_cell_steps"] / max(prof["fused_ms"], 1e-9) / 1e6,
+                wave_solve_share_of_time=prof["fused_ms"] / 1e3 / sec)
+
+
+def measure_sweeps2d(ew):
+    """The paper's two sweeps on square128 (127 x 127 unit square, order 2,
+    implicit scheme with multigrid to 1e-10, FP64), against the box's closed
+    form, each with and without locking of converged pairs:
+      * requested pairs N_r = 1 .. 64 with N_a = 2 N_r + 2 Arnoldi vectors
+        (block 2), omega = 12, N_p = 1, 10 steps per period: wave-solves per
+        eigenpair (Section "Changing the number of requested eigenpairs");
+      * implicit steps per period N_its = 5 .. 15, omega = 10, N_p = 1, 12
+        pairs: time-steps per eigenpair (Section "Changing the number of
+        implicit time-steps per period")."""
+    import numpy as np
+    m = 127
+    exact = np.sort(closed_form_all((m, m), (1.0, 1.0), 2))
+
+    def solve(omega, nits, nr, na, lock):
+        g = ew.ew_grid_create(2, (m, m), (1.0, 1.0), order=2, prec="fp64")
+        mg = ew.mg_params(pre=2, post=2, max_cycles=40, rtol=1e-10)
+        p = ew.filter_params(omega, num_periods=1, steps_per_period=nits, scheme="implicit", adjust_omega=True, mg=mg)
+        e = ew.eigs_params(nr, krylov_dim=na, block=2, tol=1e-10, seed=7, max_wave_solves=4000, lock=lock)
+        lam, rep, st = ew.ew_arnoldi_eigs(g, p, e, allow_noconv=True)
+        # CR of simultaneous iteration for this N_r, N_a (the library's estimate)
+        try:
+            _, cr = ew.ew_choose_num_periods(g, ew.filter_params(omega, num_periods=1, steps_per_period=nits,
+                                                                 scheme="implicit", adjust_omega=True, mg=mg),
+                                             nr, na, max_periods=1)
+            cr = float(cr[0])
+        except ew.EWError:
+            cr = None
+        g.close()
+        err = max(_nearest_rel_err(exact, x) for x in lam)
+        return dict(requested=nr, arnoldi_vectors=na, converged=int(rep["n_converged"]), status=int(st),
+                    wave_solves=int(rep["wave_solves"]), wave_solves_per_eig=rep["wave_solves"] / max(nr, 1),
+                    time_steps_per_eig=rep["wave_solves"] * nits / max(nr, 1), cr_estimate=cr,
+                    max_rel_err_vs_closed_form=err, max_eig_res=float(rep["eig_res"][:nr].max()))
+
+    nr_rows, nits_rows = [], []
+    for lock in (False, True):
+        for nr in (1, 2, 4, 8, 16, 32, 64):
+            row = solve(12.0, 10, nr, 2 * nr + 2, lock)
+            row["lock"] = lock
+            nr_rows.append(row)
+        for nits in range(5, 16):
+            row = solve(10.0, nits, 12, 26, lock)
+            row["lock"] = lock
+            row["steps_per_period"] = nits
+            nits_rows.append(row)
+    return dict(workload="sweeps_square128_order2_implicit", unit="wave-solves", requested_sweep=nr_rows,
+                steps_per_period_sweep=nits_rows)
+
+
 def measure_eigs2d(ew, which, num_periods):
     """Time to the 8 eigenpairs nearest omega = 150 on the 2047 x 3071 order-4
     rectangle at eig-res <= 1e-8: FP32 wave-solves + refinement against FP64
@@ -628,6 +801,12 @@ def run_extra(args):
         line = dict(workload="batched_64_boxes_255_to_2047_order2_fp32", metric=METRIC, unit=UNIT,
                     value=cells * args.steps / (ms / 1e3) / 1e9, ms_per_step=ms / args.steps,
                     problems=len(boxes), cell_steps_per_step=cells)
+    elif w == "batched_eigs":
+        line = measure_batched_eigs(ew)
+    elif w == "sweeps2d":
+        line = measure_sweeps2d(ew)
+    elif w == "eigs3d":
+        line = measure_eigs3d(ew, args.num_periods)
     elif w == "implicit3d":
         n, L = (255, 255, 255), (1.0, 1.0, 1.0)
         g = ew.ew_grid_create(3, n, L, order=4, prec="fp32")

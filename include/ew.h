@@ -330,6 +330,9 @@ typedef struct {
                                  remaining images are FP64 */
     double refine_tol;     /* refine_fp64 1, 3: eig-res target of every wanted pair, 0: 5e-9;
                               refine_fp64 2: FP64 Ritz residual target, 0: 1e-10 */
+    int lock;              /* 1: lock converged pairs at each thick restart (a wanted Ritz pair whose
+                              residual is below tol keeps its vector and value, and its coupling to the
+                              residual block is set to zero, so later expansions leave it as it is) */
 } ew_eigs_params;
 
 #define EW_MAX_EIGS 64

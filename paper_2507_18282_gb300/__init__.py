@@ -219,9 +219,9 @@ def ew_power_iteration(grid: Grid, params, v, iters, tol=0.0, stream=None):
 
 
 def eigs_params(n_wanted, krylov_dim=0, block=1, tol=0.0, max_wave_solves=0, seed=0, refine_fp64=False,
-                refine_tol=0.0):
+                refine_tol=0.0, lock=False):
     return _lib.ew_eigs_params(int(n_wanted), int(krylov_dim), int(block), float(tol), int(max_wave_solves),
-                               int(seed), int(refine_fp64), float(refine_tol))
+                               int(seed), int(refine_fp64), float(refine_tol), int(bool(lock)))
 
 
 def ew_arnoldi_eigs(grid: Grid, params, eigs, start=None, vecs=None, stream=None, allow_noconv=False):

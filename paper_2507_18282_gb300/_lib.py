@@ -65,7 +65,7 @@ EW_MAX_EIGS = 64
 class ew_eigs_params(ctypes.Structure):
     _fields_ = [("n_wanted", ctypes.c_int), ("krylov_dim", ctypes.c_int), ("block", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_wave_solves", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("refine_fp64", ctypes.c_int), ("refine_tol", ctypes.c_double)]
+                ("refine_fp64", ctypes.c_int), ("refine_tol", ctypes.c_double), ("lock", ctypes.c_int)]
 
 
 class ew_eigs_report(ctypes.Structure):

@@ -158,6 +158,7 @@ struct KSRun {
     std::vector<double> H;   // (m + 3b) x (m + 2b), row-major, ldh = m + 2b
     int ldh = 0, mcur = 0;
     int wave_solves = 0, restarts = 0;
+    bool lock = false;  // lock converged wanted pairs at restarts
     std::vector<void*> allocs;
 
     ~KSRun() {
@@ -377,8 +378,12 @@ struct KSRun {
         }
     }
 
-    // thick restart keeping k Ritz vectors and the residual block
-    ew_status restart(int k, const std::vector<double>& theta, const std::vector<double>& Y) {
+    // thick restart keeping k Ritz vectors and the residual block; with `lock`,
+    // the wanted pairs whose residual is below tol are locked: their coupling to
+    // the residual block (of norm below tol) is set to zero, so the next
+    // Rayleigh-Ritz steps keep their vectors and values as they are
+    ew_status restart(int k, const std::vector<double>& theta, const std::vector<double>& Y,
+                      const std::vector<double>& resid) {
         int n = mcur;
         std::vector<double> Yk((size_t)n * k);
         for (int r = 0; r < n; ++r)
@@ -386,6 +391,7 @@ struct KSRun {
         std::vector<double> coup((size_t)b * k, 0.0);
         for (int i = 0; i < b; ++i)
             for (int c = 0; c < k; ++c) {
+                if (lock && c < nw && resid[c] <= tol) continue;  // locked: no coupling
                 double s = 0.0;
                 for (int r = 0; r < n; ++r) s += h(n + i, r) * Y[(size_t)r * n + c];
                 coup[(size_t)i * k + c] = s;
@@ -427,7 +433,7 @@ struct KSRun {
                 return EW_OK;
             }
             int k = std::max(nw, std::min(mcur - b, nw + (mcur - nw) / 2));
-            EW_TRY(restart(k, theta, Y));
+            EW_TRY(restart(k, theta, Y, resid));
         }
     }
 };
@@ -713,6 +719,7 @@ ew_status arnoldi_eigs_impl(const ew_grid* grid, const ew_filter_params* params,
     ks.m = m;
     ks.nw = nw;
     ks.tol = ep->tol > 0 ? ep->tol : (g->prec == EW_FP32 ? 1e-4 : 1e-10);
+    ks.lock = ep->lock != 0;
     ks.max_ws = ep->max_wave_solves > 0 ? ep->max_wave_solves : 2000;
     ks.st = st;
     EW_TRY(ks.setup());

@@ -79,7 +79,9 @@ struct Tma2dShape {
     static constexpr int NT = NTC + 32;                  // + the producer warp
     static constexpr int BUF = BOXW * RY;                // floats of one copied box
     static constexpr int BUFP = (BUF + 31) & ~31;        // buffer stride: copy destinations 128-byte aligned
-    static constexpr size_t SMEM = sizeof(float) * 4 * (size_t)BUFP + 64;  // two slots x (D, W) + four mbarriers
+    static constexpr size_t SMEM = sizeof(float) * 4 * (size_t)BUFP + 128;  // two slots x (D, W), four mbarriers,
+                                                                             // the launch's B filter weights
+    static_assert(B <= 16, "the weights of one launch live in the shared-memory tail");
     static_assert(TX > 0 && TY > 0, "halo larger than the tile");
     static_assert(TX % 4 == 0 && (H - R) % 2 == 0, "owned rows 16-byte aligned, column pairs 8-byte aligned");
     static_assert(BOXW <= 256 && RY <= 256, "tensor-map box dimensions are at most 256");
@@ -215,6 +217,7 @@ __global__ void __launch_bounds__(32 * NWX * NTY + 32, 1)
     float* slots = reinterpret_cast<float*>(smem_raw);  // [2 slots][D, W][BUFP]
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + sizeof(float) * 4 * (size_t)BUFP);
     uint64_t* done = full + 2;
+    float* cws = reinterpret_cast<float*>(done + 2);  // c_{n+1} .. c_{n+b}: one shared copy for every tile
     const int tid = threadIdx.x;
     const int64_t N = (int64_t)nx * ny;
     if ((int)blockIdx.x >= ntiles) return;
@@ -225,6 +228,7 @@ __global__ void __launch_bounds__(32 * NWX * NTY + 32, 1)
         tma_mbar_init(&done[1], NTC / 32);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
+    if (tid < b) cws[tid] = cw[tid];
     __syncthreads();  // the only CTA-wide barrier: from here on the two roles synchronise by mbarriers
 
     if (tid >= NTC) {
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(32 * NWX * NTY + 32, 1)
             float2 w1 = *reinterpret_cast<const float2*>(col + (sy0 - 1) * BOXW);
             float2 w2 = *reinterpret_cast<const float2*>(col + sy0 * BOXW);
             float2 w3 = *reinterpret_cast<const float2*>(col + (sy0 + 1) * BOXW);
-            const float cs = cw[step];
+            const float cs = cws[step];
             const float2 CS{cs, cs};
 #pragma unroll
             for (int kk = 0; kk < KY; ++kk) {

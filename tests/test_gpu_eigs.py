@@ -226,3 +226,24 @@ def test_rectangle_2047x3071_eight_pairs_full_size(ew):
         assert np.min(np.abs(near - x)) <= 1e-9 * x, x
     assert np.all(rep["eig_res"] <= 1e-8), rep["eig_res"]
     assert len(set(np.round(lam, 9))) == 8  # eight distinct pairs (the levels are simple here)
+
+
+def test_locking_keeps_the_converged_pairs(ew):
+    """Krylov-Schur with locking of converged pairs (eigs.lock): the same eigenvalues
+    as without it (closed form of the box, FP64), in no more wave-solves than
+    twice as many (locking only changes which restart directions are kept)."""
+    n, L, omega = (127, 127), (1.0, 1.0), 12.0
+    og = O.Grid(n, L, 2)
+    res = {}
+    for lock in (False, True):
+        g = ew.ew_grid_create(2, n, L, order=2, prec="fp64")
+        p = ew.filter_params(omega, num_periods=2)
+        info, _ = ew.ew_filter_setup(g, p)
+        e = ew.eigs_params(16, krylov_dim=34, block=2, tol=1e-11, seed=3, max_wave_solves=2000, lock=lock)
+        lam, rep, st = ew.ew_arnoldi_eigs(g, p, e)
+        g.close()
+        res[lock] = (np.sort(lam), rep)
+    want, _, _ = _wanted(og, O.filter_params(omega, 2, info["steps_per_period"]), 16)
+    for lock in (False, True):
+        np.testing.assert_allclose(res[lock][0], np.sort(want), rtol=1e-10)
+    assert res[True][1]["wave_solves"] <= 2 * res[False][1]["wave_solves"]
