@@ -611,28 +611,36 @@ def measure_sweeps2d(ew):
     m = 127
     exact = np.sort(closed_form_all((m, m), (1.0, 1.0), 2))
 
-    def solve(omega, nits, nr, na, lock):
+    def solve(omega, nits, nr, na, lock, auto_np=False):
         g = ew.ew_grid_create(2, (m, m), (1.0, 1.0), order=2, prec="fp64")
         mg = ew.mg_params(pre=2, post=2, max_cycles=40, rtol=1e-10)
-        p = ew.filter_params(omega, num_periods=1, steps_per_period=nits, scheme="implicit", adjust_omega=True, mg=mg)
+        np_ = 1
+        if auto_np:  # N_p from the simultaneous-iteration estimate for this N_r, N_a
+            np_, _ = ew.ew_choose_num_periods(g, ew.filter_params(omega, steps_per_period=nits, scheme="implicit",
+                                                                  adjust_omega=True, mg=mg), nr, na, max_periods=64)
+        p = ew.filter_params(omega, num_periods=np_, steps_per_period=nits, scheme="implicit", adjust_omega=True,
+                             mg=mg)
         e = ew.eigs_params(nr, krylov_dim=na, block=2, tol=1e-10, seed=7, max_wave_solves=4000, lock=lock)
         lam, rep, st = ew.ew_arnoldi_eigs(g, p, e, allow_noconv=True)
         # CR of simultaneous iteration for this N_r, N_a (the library's estimate)
         try:
             _, cr = ew.ew_choose_num_periods(g, ew.filter_params(omega, num_periods=1, steps_per_period=nits,
                                                                  scheme="implicit", adjust_omega=True, mg=mg),
-                                             nr, na, max_periods=1)
-            cr = float(cr[0])
+                                             nr, na, max_periods=np_)
+            cr = float(cr[np_.bit_length() - 1])
         except ew.EWError:
             cr = None
         g.close()
         err = max(_nearest_rel_err(exact, x) for x in lam)
-        return dict(requested=nr, arnoldi_vectors=na, converged=int(rep["n_converged"]), status=int(st),
-                    wave_solves=int(rep["wave_solves"]), wave_solves_per_eig=rep["wave_solves"] / max(nr, 1),
-                    time_steps_per_eig=rep["wave_solves"] * nits / max(nr, 1), cr_estimate=cr,
+        return dict(requested=nr, arnoldi_vectors=na, num_periods=np_, converged=int(rep["n_converged"]),
+                    status=int(st), wave_solves=int(rep["wave_solves"]),
+                    wave_solves_per_eig=rep["wave_solves"] / max(nr, 1),
+                    time_steps_per_eig=rep["wave_solves"] * nits * np_ / max(nr, 1), cr_estimate=cr,
                     max_rel_err_vs_closed_form=err, max_eig_res=float(rep["eig_res"][:nr].max()))
 
-    nr_rows, nits_rows = [], []
+    nr_rows, nits_rows, auto_rows = [], [], []
+    for nr in (1, 2, 4, 8, 16, 32, 64):  # N_p tuned by the estimate (time-steps per pair is then the cost)
+        auto_rows.append(solve(12.0, 10, nr, 2 * nr + 2, True, auto_np=True))
     for lock in (False, True):
         for nr in (1, 2, 4, 8, 16, 32, 64):
             row = solve(12.0, 10, nr, 2 * nr + 2, lock)
@@ -644,7 +652,7 @@ def measure_sweeps2d(ew):
             row["steps_per_period"] = nits
             nits_rows.append(row)
     return dict(workload="sweeps_square128_order2_implicit", unit="wave-solves", requested_sweep=nr_rows,
-                steps_per_period_sweep=nits_rows)
+                requested_sweep_auto_num_periods=auto_rows, steps_per_period_sweep=nits_rows)
 
 
 def measure_eigs2d(ew, which, num_periods):
