@@ -370,7 +370,8 @@ ew_status ew_arnoldi_eigs(const ew_grid* grid, const ew_filter_params* params, c
  * ew_filter_apply_batched call (its CUDA graph kept per batch and replayed;
  * the tile variant tuned on the first round and then kept); the rest of each
  * solver (orthogonalisation, small eigenproblems, Rayleigh quotients,
- * refinement) runs per problem between those rounds.
+ * refinement) runs per problem between those rounds.  At most 1024 problems
+ * (one host thread each; EW_EINVAL beyond).
  *   lambda_host[q]  receives problem q's n_wanted eigenvalues (host)
  *   vecs_dev        may be NULL, else vecs_dev[q] (may be NULL) receives
  *                   problem q's eigenvectors as in ew_arnoldi_eigs (device)

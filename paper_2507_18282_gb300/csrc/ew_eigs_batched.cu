@@ -175,6 +175,8 @@ extern "C" ew_status ew_arnoldi_eigs_batched(int nprob, const ew_grid* const* gr
                                              int* rounds_host, cudaStream_t stream) try {
     clear_error();
     if (nprob < 1 || !grids || !params || !eigs || !lambda_host) return set_error(EW_EINVAL, "null argument");
+    // one host thread per problem (each solver blocks at the rendezvous until the round's batched call)
+    if (nprob > 1024) return set_error(EW_EINVAL, "ew_arnoldi_eigs_batched takes at most 1024 problems");
     for (int q = 0; q < nprob; ++q)
         if (!grids[q] || !lambda_host[q]) return set_error(EW_EINVAL, "null grid or lambda pointer");
     int dev = -1;
