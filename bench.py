@@ -33,6 +33,7 @@ import argparse
 import atexit
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -816,9 +817,12 @@ def run_extra(args):
     elif w == "eigs3d":
         line = measure_eigs3d(ew, args.num_periods)
     elif w == "implicit3d":
+        # 255^3 order 4 FP32, implicit scheme at 10 steps per period (omega = 80 adjusted): the learned
+        # smoother trained on the GPU against plain Jacobi multigrid; its V-cycle factor, its cost per cycle
+        # (composed stencil inside the cycle, and the two-layer tensor-core form for comparison), the cost
+        # per decade of residual reduction, and whole wave-solves at fixed cycles and at a common tolerance
         n, L = (255, 255, 255), (1.0, 1.0, 1.0)
         g = ew.ew_grid_create(3, n, L, order=4, prec="fp32")
-        res = {}
         wts = torch.tensor(ew_inputs.learned_init(36, 0.05), dtype=torch.float32, device="cuda")
         probe = ew.filter_params(80.0, num_periods=1, steps_per_period=10, scheme="implicit", adjust_omega=True,
                                  mg=ew.mg_params())
@@ -829,19 +833,42 @@ def run_extra(args):
         train_s = time.time() - t0
         v = torch.tensor(ew_inputs.uniform_pm1(ew_inputs.BASE_SEED + 4, g.size), dtype=torch.float32, device="cuda")
         o = torch.empty_like(v)
-        for name, learned, cyc in [("plain", 0, 4), ("learned", 1 if rep["accepted"] else 0, 2)]:
-            mg = ew.mg_params(pre=2, post=2, max_cycles=cyc, learned_levels=learned,
+        nsteps = max(1, args.steps // 4)
+
+        def wave_solve_ms(learned, cyc, rtol=0.0):
+            mg = ew.mg_params(pre=2, post=2, max_cycles=cyc, rtol=rtol, learned_levels=learned,
                               weights=wts if learned else None)
-            p = ew.filter_params(80.0, num_periods=1, steps_per_period=10, scheme="implicit", adjust_omega=True, mg=mg)
-            ms = _timed(lambda: ew.ew_filter_apply(g, p, v, o), max(1, args.steps // 4), 1, flush)
+            p = ew.filter_params(80.0, num_periods=1, steps_per_period=10, scheme="implicit", adjust_omega=True,
+                                 mg=mg)
+            ew.ew_profile_enable(True)
+            ms = _timed(lambda: ew.ew_filter_apply(g, p, v, o), nsteps, 1, flush)
+            prof = ew.ew_profile_read()
+            ew.ew_profile_enable(False)
+            return ms / nsteps, prof["mg_cycles"] / max(prof["mg_solves"], 1)
+
+        def cycle_ms(learned):
             x = torch.zeros_like(v)
             one = ew.mg_params(pre=2, post=2, max_cycles=1, learned_levels=learned, weights=wts if learned else None)
-            t = _timed(lambda: ew.ew_implicit_step_mg(g, a, v, x, one), 5, 1, flush)
-            res[name] = dict(ms_per_wave_solve=ms / max(1, args.steps // 4), cycles_per_system=cyc,
-                             ms_per_vcycle=t / 5,
-                             gcell_steps_per_s=g.size * info["Nt"] / (ms / max(1, args.steps // 4) / 1e3) / 1e9)
+            return _timed(lambda: ew.ew_implicit_step_mg(g, a, v, x, one), 5, 1, flush) / 5
+
+        lrn = 1 if rep["accepted"] else 0
+        res = {"plain": dict(factor=rep["conv_plain"], ms_per_vcycle=cycle_ms(0)),
+               "learned": dict(factor=rep["conv_learned"], ms_per_vcycle=cycle_ms(lrn))}
+        os.environ["EW_SMOOTHER_TWO_LAYER"] = "1"
+        res["learned_two_layer"] = dict(factor=rep["conv_learned"], ms_per_vcycle=cycle_ms(lrn))
+        del os.environ["EW_SMOOTHER_TWO_LAYER"]
+        for k in res:
+            res[k]["ms_per_decade"] = res[k]["ms_per_vcycle"] / max(-math.log10(res[k]["factor"]), 1e-12)
+        ws = {}
+        for name, learned, cyc in [("plain_4_cycles", 0, 4), ("learned_2_cycles", lrn, 2), ("learned_3_cycles", lrn, 3)]:
+            ms, c = wave_solve_ms(learned, cyc)
+            ws[name] = dict(ms_per_wave_solve=ms, cycles_per_system=c,
+                            gcell_steps_per_s=g.size * info["Nt"] / (ms / 1e3) / 1e9)
+        for name, learned in [("plain_rtol_1e-6", 0), ("learned_rtol_1e-6", lrn)]:
+            ms, c = wave_solve_ms(learned, 40, 1e-6)
+            ws[name] = dict(ms_per_wave_solve=ms, cycles_per_system=c)
         line = dict(workload="implicit3d_255_order4_fp32_mg_v22", unit="ms", train=rep, train_seconds=train_s,
-                    plain=res["plain"], learned=res["learned"])
+                    vcycle=res, wave_solve=ws, time_steps_per_wave_solve=info["Nt"])
     elif w == "mg3d":
         # one V(2,2) cycle of M = I - (dt^2/2) L_h on 255^3 order 4 FP32 (the implicit
         # step of the 10-steps-per-period scheme at omega = 80): plain Jacobi smoothing

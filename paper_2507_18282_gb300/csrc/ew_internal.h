@@ -283,6 +283,15 @@ template <typename T>
 int64_t tb2d_field_pitch(const GridGeom& g, const FilterPlan& plan, const T* cdev, T* const* F, T* acc, int nvec,
                          int64_t fstride, int tb, cudaStream_t st);
 
+// --- learned smoother as its composed 5x5x5 stencil (ew_smoother_comp.cu) ----
+// built from one level's 432 weights (device); applies x += N(r) on FP32 3D fields
+struct ComposedSmoother {
+    std::vector<float> interior;  // the interior stencil (125 values)
+    DeviceBuffer dev;             // the 64 class stencils (wall classes per axis)
+    ew_status build(const float* weights_dev, cudaStream_t st);
+    ew_status apply(const GridGeom& g, const float* r, float* x, cudaStream_t st) const;
+};
+
 // --- eigen-solver (ew_arnoldi.cu) ------------------------------------------
 // S v for nvec vectors, routed by the caller: the batched eigen-solver gathers
 // the filter applications of several solvers into one batched call

@@ -21,6 +21,7 @@
 // Each system gets `max_cycles` V-cycles from the initial guess y = 2 W^n
 // (W^1 = W^0 for the first step).
 #include <math.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <vector>
@@ -268,6 +269,11 @@ struct MGSolver {
     const ew_mg_params* p = nullptr;
     double wJ = 0.8;
     cudaStream_t st = nullptr;
+    // FP32 fields: the learned levels' smoother as its composed stencil (one
+    // build per solver set-up); EW_SMOOTHER_TWO_LAYER=1 keeps the two-layer
+    // tensor-core form instead (a comparison hook)
+    ComposedSmoother comp[16];
+    bool use_comp = false;
 
     ew_status setup(ew_grid* g, double a_, const ew_mg_params* params, cudaStream_t s) {
         gr = g;
@@ -291,6 +297,10 @@ struct MGSolver {
             return set_error(EW_EUNSUPPORTED, "the learned smoother is three-dimensional");
         if (params->learned_levels > 0 && !params->weights_dev)
             return set_error(EW_EINVAL, "learned_levels > 0 needs weights_dev");
+        use_comp = sizeof(T) == 4 && params->learned_levels > 0 && !getenv("EW_SMOOTHER_TWO_LAYER");
+        if (use_comp)
+            for (int L = 0; L < std::min(params->learned_levels, nlev); ++L)
+                EW_TRY(comp[L].build(params->weights_dev + (size_t)L * 432, st));
         size_t total = 0;
         for (int L = 0; L < nlev; ++L) total += 4 * (size_t)lv[L].N;
         EW_TRY(g->mgh.reserve(total * sizeof(T)));
@@ -328,6 +338,12 @@ struct MGSolver {
         for (int s = 0; s < steps; ++s) {
             if (L < p->learned_levels) {
                 EW_MG_DISPATCH(k_mg_resid, lv[L], X[L], B[L], R[L], sa);
+                if constexpr (sizeof(T) == 4) {
+                    if (use_comp) {
+                        EW_TRY(comp[L].apply(lv[L], R[L], X[L], st));
+                        continue;
+                    }
+                }
                 EW_TRY(smoother_apply<T>(lv[L], p->weights_dev + (size_t)L * 432, R[L], X[L], st));
             } else if (p->red_black) {
                 // M_ii = 1 - c0 of the stored (consistent) stencil of a L_h

@@ -1,0 +1,223 @@
+// ew_smoother_comp.cu -- the learned smoother inside the V-cycle, applied as
+// its composed stencil.
+//
+// The network has no activation (the smoothing step must stay linear), so
+// its two 3x3x3 convolutions compose into one 5x5x5 stencil:
+//   N(r)(x) = sum_c sum_{o2} W2[c][o2] h_c(x + o2),  h_c(y) = sum_{o1} W1[c][o1] r(y + o1)
+//           = sum_d K(d) r(x + d),   K(d) = sum_c sum_{o1 + o2 = d} W2[c][o2] W1[c][o1],
+// with one exception at the walls: the hidden activations are zero outside
+// the active box, so for an output point on the first or last plane of an
+// axis the hidden points beyond the wall drop out of its sum.  Per axis an
+// output is "low" (index 0), "high" (index n - 1), "both" (n = 1) or
+// interior; each of the 4^3 classes has its own composed stencil.  The
+// weights are rounded to BF16 as in the tensor-core kernels and composed in
+// FP64; the stencil runs in FP32 without the BF16 rounding of the hidden
+// activations (the same operator, with rounding below the two-layer form's).
+//
+// Why: the two-layer tensor-core forward (ew_smoother.cu) is bound by its
+// im2col gather (about 420 us per application on 255^3), while the composed
+// stencil is 125 multiply-adds per point with the interior weights as
+// constant operands, on data staged plane by plane in shared memory.
+// Training and the ABI forward/backward keep the two-layer form (the
+// gradient needs the layers).
+//
+// Kernel: a CTA owns 128 x 8 output columns and kZ planes of them; a thread
+// owns four consecutive x outputs of one row and streams along z, keeping the
+// partial sums of the five output planes an input plane feeds in registers.
+// Input planes (with a halo of 2) are staged in a double-buffered shared
+// tile, one barrier per plane.  Wall outputs are recomputed from global
+// memory with their class's stencil.
+#include <math.h>
+
+#include <cstring>
+#include <vector>
+
+#include "ew_internal.h"
+
+namespace ew {
+
+constexpr int kCompTX = 128;  // outputs per CTA row (32 threads x 4)
+constexpr int kCompTY = 8;    // rows per CTA
+constexpr int kCompZ = 32;    // planes per CTA
+constexpr int kCompSX = kCompTX + 4;  // staged width (halo 2), a multiple of 4
+constexpr int kCompSY = kCompTY + 4;
+constexpr int kCompPlane = kCompSX * kCompSY;
+
+struct K125 {
+    float k[125];  // index (dz + 2) 25 + (dy + 2) 5 + (dx + 2)
+};
+
+// class of an output coordinate on an axis: 0 low wall, 1 interior, 2 high wall, 3 both (n = 1)
+__host__ __device__ __forceinline__ int comp_class(int i, int n) {
+    return n == 1 ? 3 : (i == 0 ? 0 : (i == n - 1 ? 2 : 1));
+}
+
+// value of one wall output from global memory with its class's stencil
+__device__ __forceinline__ float comp_point(const float* __restrict__ r, const float* __restrict__ kc, int x, int y,
+                                            int z, int nx, int ny, int nz) {
+    float s = 0.f;
+    for (int dz = -2; dz <= 2; ++dz) {
+        const int zz = z + dz;
+        if (zz < 0 || zz >= nz) continue;
+        for (int dy = -2; dy <= 2; ++dy) {
+            const int yy = y + dy;
+            if (yy < 0 || yy >= ny) continue;
+            for (int dx = -2; dx <= 2; ++dx) {
+                const int xx = x + dx;
+                if (xx < 0 || xx >= nx) continue;
+                s = fmaf(kc[(dz + 2) * 25 + (dy + 2) * 5 + (dx + 2)], r[((int64_t)zz * ny + yy) * nx + xx], s);
+            }
+        }
+    }
+    return s;
+}
+
+// x += N(r) with the composed stencil (FP32 fields)
+__global__ void __launch_bounds__(256)
+    k_smoother_comp(int nx, int ny, int nz, const float* __restrict__ r, float* __restrict__ x, const K125 K,
+                    const float* __restrict__ kall) {
+    __shared__ __align__(16) float sp[2][kCompPlane];
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    const int x0 = blockIdx.x * kCompTX, y0 = blockIdx.y * kCompTY, z0 = blockIdx.z * kCompZ;
+    const int z1 = min(nz, z0 + kCompZ);
+    const int ox = x0 + 4 * lx, oy = y0 + ly;  // first output of the thread
+    auto stage = [&](int zr, float* dst) {      // input plane zr (zero outside the box)
+        for (int q = threadIdx.x; q < kCompPlane; q += 256) {
+            const int c = q % kCompSX, rr = q / kCompSX;
+            const int gx = x0 - 2 + c, gy = y0 - 2 + rr;
+            float v = 0.f;
+            if (zr >= 0 && zr < nz && gx >= 0 && gx < nx && gy >= 0 && gy < ny)
+                v = r[((int64_t)zr * ny + gy) * nx + gx];
+            dst[q] = v;
+        }
+    };
+    // acc[j][i]: output plane (input plane - 2 + j), x output ox + i
+    float acc[5][4];
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
+    stage(z0 - 2, sp[0]);
+    __syncthreads();
+    int buf = 0;
+    for (int zi = z0 - 2; zi <= z1 + 1; ++zi) {
+        if (zi + 1 <= z1 + 1) stage(zi + 1, sp[buf ^ 1]);
+        // input plane zi feeds output planes zi - 2 .. zi + 2 (acc[0] .. acc[4]) with dz = 2 - j
+        const float* p = sp[buf] + ly * kCompSX + 4 * lx;
+#pragma unroll
+        for (int dy = 0; dy < 5; ++dy) {
+            const float4 a = *reinterpret_cast<const float4*>(p + dy * kCompSX);
+            const float4 bq = *reinterpret_cast<const float4*>(p + dy * kCompSX + 4);
+            const float w[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                const int dz = 2 - j;
+#pragma unroll
+                for (int dx = 0; dx < 5; ++dx) {
+                    const float kv = K.k[(dz + 2) * 25 + dy * 5 + dx];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[j][i] = fmaf(kv, w[i + dx], acc[j][i]);
+                }
+            }
+        }
+        // output plane zi - 2 is complete
+        const int zo = zi - 2;
+        if (zo >= z0 && zo < z1 && oy < ny) {
+            const int cz = comp_class(zo, nz), cy = comp_class(oy, ny);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int gx = ox + i;
+                if (gx >= nx) continue;
+                const int cx = comp_class(gx, nx);
+                float v = acc[0][i];
+                if (cx != 1 || cy != 1 || cz != 1)  // a wall output: its own stencil
+                    v = comp_point(r, kall + (size_t)((cz * 4 + cy) * 4 + cx) * 125, gx, oy, zo, nx, ny, nz);
+                float* px = x + ((int64_t)zo * ny + oy) * nx + gx;
+                *px += v;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[j][i] = acc[j + 1][i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[4][i] = 0.f;
+        __syncthreads();  // the next plane is staged; this one may be overwritten
+        buf ^= 1;
+    }
+}
+
+// round to the nearest BF16 (ties to even), as the tensor-core kernels do
+static float bf16_host(float v) {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    float o;
+    std::memcpy(&o, &u, 4);
+    return o;
+}
+
+// the 64 class stencils of weights w (432 values [W1 8x27 | W2 8x27], taps dz slowest)
+static void compose_classes(const float* w, std::vector<float>& kall) {
+    double W1[8][27], W2[8][27];
+    for (int c = 0; c < 8; ++c)
+        for (int t = 0; t < 27; ++t) {
+            W1[c][t] = bf16_host(w[c * 27 + t]);
+            W2[c][t] = bf16_host(w[216 + c * 27 + t]);
+        }
+    kall.assign(64 * 125, 0.f);
+    auto allowed = [](int cls, int o) {  // hidden offset o of an output of this class stays in the box
+        if (cls == 3) return o == 0;
+        if (cls == 0) return o >= 0;
+        if (cls == 2) return o <= 0;
+        return true;
+    };
+    for (int cz = 0; cz < 4; ++cz)
+        for (int cy = 0; cy < 4; ++cy)
+            for (int cx = 0; cx < 4; ++cx) {
+                double K[125] = {0};
+                for (int c = 0; c < 8; ++c)
+                    for (int z2 = -1; z2 <= 1; ++z2)
+                        for (int y2 = -1; y2 <= 1; ++y2)
+                            for (int x2 = -1; x2 <= 1; ++x2) {
+                                if (!allowed(cz, z2) || !allowed(cy, y2) || !allowed(cx, x2)) continue;
+                                const double w2 = W2[c][(z2 + 1) * 9 + (y2 + 1) * 3 + (x2 + 1)];
+                                for (int z1 = -1; z1 <= 1; ++z1)
+                                    for (int y1 = -1; y1 <= 1; ++y1)
+                                        for (int x1 = -1; x1 <= 1; ++x1) {
+                                            const double w1 = W1[c][(z1 + 1) * 9 + (y1 + 1) * 3 + (x1 + 1)];
+                                            K[(z1 + z2 + 2) * 25 + (y1 + y2 + 2) * 5 + (x1 + x2 + 2)] += w2 * w1;
+                                        }
+                            }
+                float* dst = kall.data() + (size_t)((cz * 4 + cy) * 4 + cx) * 125;
+                for (int q = 0; q < 125; ++q) dst[q] = (float)K[q];
+            }
+}
+
+ew_status ComposedSmoother::build(const float* weights_dev, cudaStream_t st) {
+    float w[432];
+    EW_CUDA_TRY(cudaMemcpyAsync(w, weights_dev, sizeof(w), cudaMemcpyDeviceToHost, st));
+    EW_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<float> kall;
+    compose_classes(w, kall);
+    interior.assign(kall.begin() + (size_t)((1 * 4 + 1) * 4 + 1) * 125, kall.begin() + (size_t)((1 * 4 + 1) * 4 + 2) * 125);
+    EW_TRY(dev.alloc(sizeof(float) * kall.size()));
+    EW_CUDA_TRY(cudaMemcpyAsync(dev.p, kall.data(), sizeof(float) * kall.size(), cudaMemcpyHostToDevice, st));
+    // the host vector must outlive the copy
+    EW_CUDA_TRY(cudaStreamSynchronize(st));
+    return EW_OK;
+}
+
+ew_status ComposedSmoother::apply(const GridGeom& g, const float* r, float* x, cudaStream_t st) const {
+    if (g.dim != 3 || interior.size() != 125) return set_error(EW_EINVAL, "composed smoother: not built for a 3D grid");
+    K125 K;
+    std::memcpy(K.k, interior.data(), sizeof(K.k));
+    dim3 grid((unsigned)((g.n[0] + kCompTX - 1) / kCompTX), (unsigned)((g.n[1] + kCompTY - 1) / kCompTY),
+              (unsigned)((g.n[2] + kCompZ - 1) / kCompZ));
+    k_smoother_comp<<<grid, 256, 0, st>>>((int)g.n[0], (int)g.n[1], (int)g.n[2], r, x, K, dev.as<float>());
+    EW_CUDA_TRY(cudaGetLastError());
+    count_launch();
+    return EW_OK;
+}
+
+}  // namespace ew

@@ -223,3 +223,30 @@ def test_learned_implicit_mode_amplification_cube_255(ew):
     err = np.linalg.norm(vout.cpu().double().numpy() - beta * phi) / np.linalg.norm(phi)
     assert err < 1e-3, (err, beta)
     g.close()
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_composed_smoother_vcycle_to_fp32_rounding(ew, levels):
+    """Inside the V-cycle on FP32 grids the learned smoother runs as its composed
+    5x5x5 stencil (the layers are linear, so W2 after W1 is one stencil; outputs
+    on a wall plane use the stencil of their wall class, since hidden points
+    beyond the wall are zero).  With the hidden activations no longer rounded to
+    BF16, the cycle matches the oracle's two-layer FP64 cycle to FP32 rounding:
+    within 1e-5 of the cycle's correction, element by element (39 x 31 x 71 and
+    19 x 15 x 35: ragged 128 x 8 x 32 tiles, every wall class)."""
+    L = (1.0, 1.0, 1.0)
+    og = O.Grid(MG_N, L, 4)
+    g = ew.ew_grid_create(3, MG_N, L, order=4, prec="fp32")
+    a = _config5_a()
+    nets = np.stack([_jacobi_like(og.h, a, 81, 0.03),
+                     _jacobi_like(tuple(2 * x for x in og.h), a, 82, 0.03)])[:levels]
+    b = ew_inputs.uniform_pm1(83, og.size).astype(np.float32).astype(np.float64)
+    x0 = ew_inputs.uniform_pm1(84, og.size).astype(np.float32).astype(np.float64)
+    wts = torch.tensor(nets.reshape(-1), dtype=torch.float32, device="cuda")
+    x = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    mg = ew.mg_params(pre=2, post=2, max_cycles=1, learned_levels=levels, weights=wts)
+    ew.ew_implicit_step_mg(g, a, torch.tensor(b, dtype=torch.float32, device="cuda"), x, mg)
+    ref, _ = O.mg_solve(og, a, b, x0=x0, ncycles=1, net=nets)
+    got = x.cpu().double().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref - x0))
+    g.close()
