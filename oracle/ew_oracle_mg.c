@@ -14,12 +14,14 @@
  *     even n; the coarsest system is solved by CG to 1e-14;
  *   - smoother: damped Jacobi x += wJ (b - M x) / D with the constant interior
  *     diagonal D = 1 + a sum_i d0 / h_i^2, d0 = 2 (order 2) or 5/2 (order 4);
- *     or, for the second-order stencil, red-black Gauss-Seidel (one of the
- *     smoothers the paper names): each sweep updates first the points with
- *     i + j + k even, then the others, each by x += (b - M x) / D with the
- *     current values (the neighbours of a point are of the other colour, so
- *     a colour's updates are independent); or, on the finest `nlev_learned`
- *     levels, the learned correction x += N(b - M x);
+ *     or multi-colour Gauss-Seidel (red-black is one of the smoothers the
+ *     paper names): each sweep updates the points colour by colour, each by
+ *     x += (b - M x) / D with the current values; the colours are chosen so
+ *     that no point's stencil reaches another point of its colour, so a
+ *     colour's updates are independent: for the second-order stencil the
+ *     parity of i + j + k (red-black), for the fourth-order one (offsets of
+ *     1 and 2 along one axis) (i + j + k) mod 3, three colours; or, on the finest
+ *     `nlev_learned` levels, the learned correction x += N(b - M x);
  *   - restriction: full weighting, the tensor product of (1/4, 1/2, 1/4);
  *   - prolongation: (multi)linear interpolation, zero on the boundary.
  *
@@ -271,19 +273,52 @@ static double og_Mx_point2(const og_mg* m, const og_level* l, const double* x, l
     return xc - m->a * s;
 }
 
+/* value at index p of an axis of length n under the odd (Dirichlet) closure:
+ * the wall points -1 and n are 0, beyond them the mirror with a minus sign */
+static double og_axis_ext(const double* x, long base, long stride, long p, long n) {
+    if (p >= 0 && p < n) return x[base + p * stride];
+    if (p == -1 || p == n) return 0.0;
+    if (p < -1) return -x[base + (-2 - p) * stride];
+    return -x[base + (2 * n - p) * stride];
+}
+
+/* (M x)_q at point (i, j, k) of the fourth-order system with the odd-reflection
+ * closure: x_q - a sum_i (-x(-2) + 16 x(-1) - 30 x_q + 16 x(+1) - x(+2)) / (12 h_i^2) */
+static double og_Mx_point4(const og_mg* m, const og_level* l, const double* x, long i, long j, long k) {
+    const long* n = l->n;
+    const long q = og_idx3(n, i, j, k);
+    const long pos[3] = {i, j, k}, stride[3] = {1, n[0], n[0] * n[1]};
+    double s = 0.0;
+    for (int a = 0; a < m->dim; ++a) {
+        const long base = q - pos[a] * stride[a];
+        const double xm2 = og_axis_ext(x, base, stride[a], pos[a] - 2, n[a]);
+        const double xm1 = og_axis_ext(x, base, stride[a], pos[a] - 1, n[a]);
+        const double xp1 = og_axis_ext(x, base, stride[a], pos[a] + 1, n[a]);
+        const double xp2 = og_axis_ext(x, base, stride[a], pos[a] + 2, n[a]);
+        s += (-xm2 + 16.0 * xm1 - 30.0 * x[q] + 16.0 * xp1 - xp2) / (12.0 * l->h[a] * l->h[a]);
+    }
+    return x[q] - m->a * s;
+}
+
+static int og_colour(int order, long i, long j, long k) {
+    return order == 2 ? (int)((i + j + k) & 1) : (int)((i + j + k) % 3);
+}
+
 static void og_smooth(const og_mg* m, int L, const double* b, double* x, double* r, int nu) {
     const og_level* l = &m->lv[L];
     double D = og_jacobi_diag(m, l);
     if (m->red_black && L >= m->nlearn) {
         const long* n = l->n;
+        const int ncol = m->order == 2 ? 2 : 3;
         for (int s = 0; s < nu; ++s)
-            for (int colour = 0; colour < 2; ++colour)
+            for (int colour = 0; colour < ncol; ++colour)
                 for (long k = 0; k < n[2]; ++k)
                     for (long j = 0; j < n[1]; ++j)
                         for (long i = 0; i < n[0]; ++i) {
-                            if (((i + j + k) & 1) != colour) continue;
+                            if (og_colour(m->order, i, j, k) != colour) continue;
                             long q = og_idx3(n, i, j, k);
-                            x[q] += (b[q] - og_Mx_point2(m, l, x, i, j, k)) / D;
+                            double mx = m->order == 2 ? og_Mx_point2(m, l, x, i, j, k) : og_Mx_point4(m, l, x, i, j, k);
+                            x[q] += (b[q] - mx) / D;
                         }
         return;
     }
@@ -331,7 +366,7 @@ static double og_norm2(long N, const double* v) {
 }
 
 /* `ncycles` V(nu1, nu2) cycles on M x = b starting from the x passed in
- * (red_black: the red-black Gauss-Seidel smoother instead of damped Jacobi).
+ * (red_black: the multi-colour Gauss-Seidel smoother instead of damped Jacobi).
  * res_hist (ncycles + 1 entries, may be NULL) receives ||b - M x||_2 before
  * the first and after every cycle.  Returns the number of levels, < 0 on bad
  * arguments. */
@@ -340,7 +375,6 @@ int og_mg_solve(int dim, const long* n, const double* h, int order, double a, co
                 int nlev_learned, double* res_hist, int red_black) {
     og_mg m;
     if ((dim != 2 && dim != 3) || (order != 2 && order != 4) || ncycles < 0) return -1;
-    if (red_black && order != 2) return -1; /* the wide stencil couples points of one colour */
     m.red_black = red_black;
     if (net_w && nlev_learned > 0 && dim != 3) return -1;
     m.dim = dim;

@@ -88,10 +88,13 @@ def _interior_diag(M, n):
     return M[q, q]
 
 
-def _colour_masks(n):
+def _colour_masks(n, order):
+    """Gauss-Seidel colours: (i + j + k) mod 2 at second order, mod 3 at
+    fourth order (points flattened x fastest)."""
     grids = np.meshgrid(*[np.arange(m) for m in reversed(n)], indexing="ij")
-    par = sum(grids).reshape(-1) % 2
-    return par == 0, par == 1
+    ncol = 2 if order == 2 else 3
+    col = sum(grids).reshape(-1) % ncol
+    return [col == c for c in range(ncol)]
 
 
 class DenseCycle:
@@ -101,7 +104,7 @@ class DenseCycle:
         self.R = [_kron_x_fastest([_restrict_1d(x) for x in m]) for m, _ in self.lv[:-1]]
         self.P = [_kron_x_fastest([_prolong_1d(x) for x in m]) for m, _ in self.lv[:-1]]
         self.D = [_interior_diag(M, m) for M, (m, _) in zip(self.M, self.lv)]
-        self.col = [_colour_masks(m) for m, _ in self.lv]
+        self.col = [_colour_masks(m, order) for m, _ in self.lv]
         self.wJ, self.red_black = wJ, red_black
 
     def smooth(self, L, b, x, nu):
@@ -131,6 +134,8 @@ CASES = [
     ((15, 31), (1.0, 1.7), 4, False),
     ((15, 15), (1.0, 1.0), 2, True),
     ((7, 7, 7), (1.0, 1.0, 1.0), 2, True),
+    ((15, 31), (1.0, 1.7), 4, True),           # three colours
+    ((7, 15, 7), (1.0, 0.8, 1.2), 4, True),
 ]
 
 
@@ -173,3 +178,19 @@ def test_dense_M_is_the_oracle_operator():
         M = _dense_M(n, g.h, order, a)
         x = np.random.default_rng(3).uniform(-1, 1, g.size)
         assert np.max(np.abs(O.apply_M(g, a, x) - M @ x)) <= 1e-11 * np.max(np.abs(M @ x))
+
+
+@pytest.mark.parametrize("n,order", [((15, 31), 2), ((9, 7, 11), 2), ((15, 31), 4), ((9, 7, 11), 4)])
+def test_colours_do_not_couple(n, order):
+    """No entry of M joins two distinct points of one colour, so updating a
+    colour point by point (the oracle) equals updating it at once (the dense
+    cycle, and the GPU's one launch per colour)."""
+    g = O.Grid(n, tuple(1.0 for _ in n), order)
+    M = _dense_M(n, g.h, order, 0.3)
+    for mask in _colour_masks(n, order):
+        blk = M[np.ix_(mask, mask)]
+        off = blk - np.diag(np.diag(blk))
+        assert np.max(np.abs(off)) <= 1e-12 * np.max(np.abs(M))
+    # and the colouring is not vacuous: M does join points of different colours
+    masks = _colour_masks(n, order)
+    assert np.max(np.abs(M[np.ix_(masks[0], masks[1])])) > 0.1 * np.max(np.abs(M))
