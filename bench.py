@@ -88,7 +88,8 @@ def parse():
                     help="eigs2d: the mixed arm with pair-arithmetic images and the plain FP64 arm (default), "
                          "or one arm")
     ap.add_argument("--red-black", action="store_true",
-                    help="scaling2d: red-black Gauss-Seidel smoothing on the second-order grids")
+                    help="scaling2d: multi-colour Gauss-Seidel smoothing (red-black at second order, "
+                         "three colours at fourth order)")
     ap.add_argument("--num-periods", type=int, default=0,
                     help="N_p of the eigs2d workload (0: the library's choice, ew_choose_num_periods)")
     return ap.parse_args()
@@ -929,7 +930,7 @@ def run_extra(args):
             for k in range(5, 12):
                 m = 2 ** k - 1
                 g = ew.ew_grid_create(2, (m, m), (1.0, 1.0), order=order, prec="fp64")
-                rb = bool(args.red_black and order == 2)
+                rb = bool(args.red_black)
                 mg = ew.mg_params(pre=2, post=2, max_cycles=40, rtol=1e-10, red_black=rb)
                 p = ew.filter_params(12.0, num_periods=1, steps_per_period=10, scheme="implicit", adjust_omega=True,
                                      mg=mg)
@@ -946,7 +947,8 @@ def run_extra(args):
                 exact = np.sort(closed_form_all((m, m), (1.0, 1.0), order))
                 err = max(_nearest_rel_err(exact, x) for x in lam)
                 rows[order].append(dict(
-                    smoother="red-black Gauss-Seidel" if rb else "damped Jacobi",
+                    smoother=("red-black Gauss-Seidel" if order == 2 else "three-colour Gauss-Seidel") if rb
+                    else "damped Jacobi",
                     h="1/%d" % (m + 1), points=m * m, eigenpairs=int(rep["n_converged"]),
                     wave_solves=int(rep["wave_solves"]),
                     mg_cycles_per_solve=prof["mg_cycles"] / max(prof["mg_solves"], 1), seconds=sec,

@@ -142,10 +142,12 @@ typedef struct {
     const float* weights_dev; /* learned weights, learned_levels x 432 FP32 values (device), each
                                  rounded to BF16 by the kernels; layout [W1 8x27 | W2 8x27],
                                  taps (dz,dy,dx) with dz slowest */
-    int red_black;            /* 1: red-black Gauss-Seidel smoothing instead of damped Jacobi on the
-                                 non-learned levels: each sweep updates the points with i + j + k
-                                 even, then the others, by x += (b - M x) / M_ii; second-order
-                                 grids only (EW_EINVAL otherwise) */
+    int red_black;            /* 1: multi-colour Gauss-Seidel smoothing instead of damped Jacobi on
+                                 the non-learned levels: each sweep updates the points colour by
+                                 colour by x += (b - M x) / M_ii (M_ii of an interior point).
+                                 Second order: red-black, colour (i + j + k) mod 2; fourth order:
+                                 three colours, (i + j + k) mod 3, so that no stencil offset
+                                 joins two points of one colour */
 } ew_mg_params;
 
 /* Filter parameters (Section "Discrete approximations").

@@ -98,18 +98,26 @@ __global__ void k_mg_jacobi(int64_t nx, int64_t ny, int64_t nz, const T* __restr
     xo[q] = x[q] + wd * r;
 }
 
-// red-black Gauss-Seidel, second order, in place: the points of one colour
-// ((i + j + k) & 1 == colour) take x += (b - M x) * inv_d, M_ii = 1 / inv_d;
-// their neighbours are all of the other colour, so the colour's updates are
-// independent and the sweep is exact Gauss-Seidel in red-black order
-template <typename T, int DIM>
+// multi-colour Gauss-Seidel, in place: the points of one colour take
+// x += (b - M x) * inv_d, M_ii = 1 / inv_d.  Second order: red-black, colour
+// (i + j + k) & 1.  Fourth order (offsets of 1 and 2 along one axis): three
+// colours, (i + j + k) mod 3; an offset changes the colour by +-1 or +-2, never
+// 0 mod 3.  So no point of a colour reads another point of its colour, the
+// colour's updates are independent, and the sweep is exact Gauss-Seidel in
+// colour order
+template <int ORDER>
+__device__ __forceinline__ int mg_colour(int64_t i, int64_t j, int64_t k) {
+    return ORDER == 2 ? (int)((i + j + k) & 1) : (int)((i + j + k) % 3);
+}
+
+template <typename T, int DIM, int ORDER>
 __global__ void k_mg_rbgs(int64_t nx, int64_t ny, int64_t nz, T* __restrict__ x, const T* __restrict__ b,
                           Stencil<T> sa, T inv_d, int colour) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nx) return;
     const int64_t j = blockIdx.y, k = blockIdx.z, q = (k * ny + j) * nx + i;
-    if (((i + j + k) & 1) != colour) return;
-    const T r = (b[q] - x[q]) + lap_global<T, DIM, 2>(x, sa, q, i, j, k, nx, ny, nz);
+    if (mg_colour<ORDER>(i, j, k) != colour) return;
+    const T r = (b[q] - x[q]) + lap_global<T, DIM, ORDER>(x, sa, q, i, j, k, nx, ny, nz);
     x[q] = x[q] + inv_d * r;
 }
 
@@ -284,8 +292,6 @@ struct MGSolver {
         if (g->geom.bc)
             return set_error(EW_EUNSUPPORTED, "multigrid: boxes with Neumann faces are not implemented");
         if (g->geom.map) return set_error(EW_EUNSUPPORTED, "multigrid: mapped grids are not implemented");
-        if (params->red_black && g->geom.order != 2)
-            return set_error(EW_EINVAL, "red-black smoothing needs the second-order stencil");
         if (g->prec == EW_FP32X2) return set_error(EW_EUNSUPPORTED, "multigrid: FP32 or FP64 grids only");
         nlev = mg_levels(g->geom, lv, 16);
         if (g->geom.n[1] > 65535 || g->geom.n[2] > 65535)
@@ -351,12 +357,19 @@ struct MGSolver {
                 const GridGeom& g_ = lv[L];
                 const int nz_ = g_.dim == 3 ? (int)g_.n[2] : 1;
                 dim3 grid_ = pt_grid(g_.n[0], g_.n[1], nz_), blk_(pt_threads(g_.n[0]));
-                for (int colour = 0; colour < 2; ++colour) {
-                    if (g_.dim == 2)
-                        k_mg_rbgs<T, 2><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], 1, X[L], B[L], sa, inv_d, colour);
+                const int ncol = g_.order == 2 ? 2 : 3;
+                for (int colour = 0; colour < ncol; ++colour) {
+                    const int64_t nz3 = g_.dim == 3 ? g_.n[2] : 1;
+                    if (g_.dim == 2 && g_.order == 2)
+                        k_mg_rbgs<T, 2, 2><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], 1, X[L], B[L], sa, inv_d, colour);
+                    else if (g_.dim == 2)
+                        k_mg_rbgs<T, 2, 4><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], 1, X[L], B[L], sa, inv_d, colour);
+                    else if (g_.order == 2)
+                        k_mg_rbgs<T, 3, 2><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], nz3, X[L], B[L], sa, inv_d,
+                                                                  colour);
                     else
-                        k_mg_rbgs<T, 3><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], g_.n[2], X[L], B[L], sa, inv_d,
-                                                               colour);
+                        k_mg_rbgs<T, 3, 4><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], nz3, X[L], B[L], sa, inv_d,
+                                                                  colour);
                     count_launch();
                 }
             } else {

@@ -21,14 +21,19 @@
 // Training and the ABI forward/backward keep the two-layer form (the
 // gradient needs the layers).
 //
-// Kernel: a CTA owns 128 x 8 output columns and kZ planes of them; a thread
+// Kernels: the interior stencil is applied at every output, on the residual
+// zero-padded outside the box; a second launch then adds, at each output on
+// a wall plane, the difference between its class's stencil and the interior
+// one (one thread per wall output, about 2.3 % of the points on 255^3).  In
+// the first, a CTA owns 128 x 8 output columns and kZ planes of them; a thread
 // owns four consecutive x outputs of one row and streams along z, keeping the
 // partial sums of the five output planes an input plane feeds in registers.
-// Input planes (with a halo of 2) are staged in a double-buffered shared
-// tile, one barrier per plane.  Wall outputs are recomputed from global
-// memory with their class's stencil.
+// Input planes (with a halo of 2) are staged in a double-buffered shared tile,
+// one barrier per plane; the global loads of plane z + 2 are issued into
+// registers before plane z + 1 is computed, so their latency is hidden.
 #include <math.h>
 
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -52,43 +57,37 @@ __host__ __device__ __forceinline__ int comp_class(int i, int n) {
     return n == 1 ? 3 : (i == 0 ? 0 : (i == n - 1 ? 2 : 1));
 }
 
-// value of one wall output from global memory with its class's stencil
-__device__ __forceinline__ float comp_point(const float* __restrict__ r, const float* __restrict__ kc, int x, int y,
-                                            int z, int nx, int ny, int nz) {
-    float s = 0.f;
-    for (int dz = -2; dz <= 2; ++dz) {
-        const int zz = z + dz;
-        if (zz < 0 || zz >= nz) continue;
-        for (int dy = -2; dy <= 2; ++dy) {
-            const int yy = y + dy;
-            if (yy < 0 || yy >= ny) continue;
-            for (int dx = -2; dx <= 2; ++dx) {
-                const int xx = x + dx;
-                if (xx < 0 || xx >= nx) continue;
-                s = fmaf(kc[(dz + 2) * 25 + (dy + 2) * 5 + (dx + 2)], r[((int64_t)zz * ny + yy) * nx + xx], s);
-            }
-        }
-    }
-    return s;
-}
-
-// x += N(r) with the composed stencil (FP32 fields)
-__global__ void __launch_bounds__(256)
-    k_smoother_comp(int nx, int ny, int nz, const float* __restrict__ r, float* __restrict__ x, const K125 K,
-                    const float* __restrict__ kall) {
+// x += K_int * r at every output (FP32 fields, r zero outside the box)
+__global__ void __launch_bounds__(256, 4)
+    k_smoother_comp(int nx, int ny, int nz, const float* __restrict__ r, float* __restrict__ x, const K125 K) {
+    constexpr int kPer = (kCompPlane + 255) / 256;  // staged elements per thread and plane
     __shared__ __align__(16) float sp[2][kCompPlane];
     const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
     const int x0 = blockIdx.x * kCompTX, y0 = blockIdx.y * kCompTY, z0 = blockIdx.z * kCompZ;
     const int z1 = min(nz, z0 + kCompZ);
     const int ox = x0 + 4 * lx, oy = y0 + ly;  // first output of the thread
-    auto stage = [&](int zr, float* dst) {      // input plane zr (zero outside the box)
-        for (int q = threadIdx.x; q < kCompPlane; q += 256) {
-            const int c = q % kCompSX, rr = q / kCompSX;
-            const int gx = x0 - 2 + c, gy = y0 - 2 + rr;
-            float v = 0.f;
-            if (zr >= 0 && zr < nz && gx >= 0 && gx < nx && gy >= 0 && gy < ny)
-                v = r[((int64_t)zr * ny + gy) * nx + gx];
-            dst[q] = v;
+    const int64_t plane = (int64_t)nx * ny;
+    // the staged elements of this thread: offset within a plane, or -1 outside the box
+    int off[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int q = threadIdx.x + 256 * u;
+        const int c = q % kCompSX, rr = q / kCompSX;
+        const int gx = x0 - 2 + c, gy = y0 - 2 + rr;
+        off[u] = (q < kCompPlane && gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? gy * nx + gx : -1;
+    }
+    float pre[kPer];
+    auto fetch = [&](int zr) {  // global loads of input plane zr into registers
+        const bool zin = zr >= 0 && zr < nz;
+        const float* rp = r + (int64_t)zr * plane;
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) pre[u] = (zin && off[u] >= 0) ? rp[off[u]] : 0.f;
+    };
+    auto put = [&](float* dst) {
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int q = threadIdx.x + 256 * u;
+            if (q < kCompPlane) dst[q] = pre[u];
         }
     };
     // acc[j][i]: output plane (input plane - 2 + j), x output ox + i
@@ -97,11 +96,12 @@ __global__ void __launch_bounds__(256)
     for (int j = 0; j < 5; ++j)
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
-    stage(z0 - 2, sp[0]);
+    fetch(z0 - 2);
+    put(sp[0]);
+    fetch(z0 - 1);
     __syncthreads();
     int buf = 0;
     for (int zi = z0 - 2; zi <= z1 + 1; ++zi) {
-        if (zi + 1 <= z1 + 1) stage(zi + 1, sp[buf ^ 1]);
         // input plane zi feeds output planes zi - 2 .. zi + 2 (acc[0] .. acc[4]) with dz = 2 - j
         const float* p = sp[buf] + ly * kCompSX + 4 * lx;
 #pragma unroll
@@ -123,18 +123,10 @@ __global__ void __launch_bounds__(256)
         // output plane zi - 2 is complete
         const int zo = zi - 2;
         if (zo >= z0 && zo < z1 && oy < ny) {
-            const int cz = comp_class(zo, nz), cy = comp_class(oy, ny);
+            float* px = x + (int64_t)zo * plane + (int64_t)oy * nx + ox;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int gx = ox + i;
-                if (gx >= nx) continue;
-                const int cx = comp_class(gx, nx);
-                float v = acc[0][i];
-                if (cx != 1 || cy != 1 || cz != 1)  // a wall output: its own stencil
-                    v = comp_point(r, kall + (size_t)((cz * 4 + cy) * 4 + cx) * 125, gx, oy, zo, nx, ny, nz);
-                float* px = x + ((int64_t)zo * ny + oy) * nx + gx;
-                *px += v;
-            }
+            for (int i = 0; i < 4; ++i)
+                if (ox + i < nx) px[i] += acc[0][i];
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -142,9 +134,64 @@ __global__ void __launch_bounds__(256)
             for (int i = 0; i < 4; ++i) acc[j][i] = acc[j + 1][i];
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[4][i] = 0.f;
-        __syncthreads();  // the next plane is staged; this one may be overwritten
+        // plane zi + 1 (in registers) into the other buffer: its last readers
+        // (plane zi - 1) passed the previous barrier
+        if (zi + 1 <= z1 + 1) put(sp[buf ^ 1]);
+        __syncthreads();
+        if (zi + 2 <= z1 + 1) fetch(zi + 2);
         buf ^= 1;
     }
+}
+
+// Wall outputs, in three disjoint parts: the z-wall planes (all x, y), then
+// the y-wall rows of the other planes (all x), then the x-wall points of the
+// remaining rows.  Each adds sum_d (K_class - K_int)(d) r(p + d).
+__global__ void __launch_bounds__(256)
+    k_smoother_comp_walls(int nx, int ny, int nz, const float* __restrict__ r, float* __restrict__ x,
+                          const float* __restrict__ kdiff, int64_t nz_part, int64_t ny_part, int64_t nwall) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nwall) return;
+    const int cyn = ny == 1 ? 1 : 2, cxn = nx == 1 ? 1 : 2;
+    int gx, gy, gz;
+    if (idx < nz_part) {
+        const int64_t pl = (int64_t)nx * ny;
+        gz = (idx / pl) ? nz - 1 : 0;
+        const int64_t rem = idx % pl;
+        gy = (int)(rem / nx);
+        gx = (int)(rem % nx);
+    } else if ((idx -= nz_part) < ny_part) {
+        const int64_t per = (int64_t)cyn * nx;
+        gz = 1 + (int)(idx / per);
+        const int64_t rem = idx % per;
+        gy = (rem / nx) ? ny - 1 : 0;
+        gx = (int)(rem % nx);
+    } else {
+        idx -= ny_part;
+        const int64_t per = (int64_t)(ny - 2) * cxn;
+        gz = 1 + (int)(idx / per);
+        const int64_t rem = idx % per;
+        gy = 1 + (int)(rem / cxn);
+        gx = (rem % cxn) ? nx - 1 : 0;
+    }
+    const int cls = (comp_class(gz, nz) * 4 + comp_class(gy, ny)) * 4 + comp_class(gx, nx);
+    const float* kd = kdiff + (size_t)cls * 125;
+    float s = 0.f;
+#pragma unroll
+    for (int dz = -2; dz <= 2; ++dz) {
+        const int zz = gz + dz;
+#pragma unroll
+        for (int dy = -2; dy <= 2; ++dy) {
+            const int yy = gy + dy;
+#pragma unroll
+            for (int dx = -2; dx <= 2; ++dx) {
+                const int xx = gx + dx;
+                if (zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx)
+                    s = fmaf(__ldg(kd + (dz + 2) * 25 + (dy + 2) * 5 + (dx + 2)),
+                             r[((int64_t)zz * ny + yy) * nx + xx], s);
+            }
+        }
+    }
+    x[((int64_t)gz * ny + gy) * nx + gx] += s;
 }
 
 // round to the nearest BF16 (ties to even), as the tensor-core kernels do
@@ -200,7 +247,11 @@ ew_status ComposedSmoother::build(const float* weights_dev, cudaStream_t st) {
     EW_CUDA_TRY(cudaStreamSynchronize(st));
     std::vector<float> kall;
     compose_classes(w, kall);
-    interior.assign(kall.begin() + (size_t)((1 * 4 + 1) * 4 + 1) * 125, kall.begin() + (size_t)((1 * 4 + 1) * 4 + 2) * 125);
+    const size_t ci = (size_t)((1 * 4 + 1) * 4 + 1) * 125;  // the interior class
+    interior.assign(kall.begin() + ci, kall.begin() + ci + 125);
+    std::vector<float> kint(interior);
+    for (size_t c = 0; c < 64; ++c)  // difference stencils, K_class - K_int (rounded once from FP32 values)
+        for (int q = 0; q < 125; ++q) kall[c * 125 + q] -= kint[q];
     EW_TRY(dev.alloc(sizeof(float) * kall.size()));
     EW_CUDA_TRY(cudaMemcpyAsync(dev.p, kall.data(), sizeof(float) * kall.size(), cudaMemcpyHostToDevice, st));
     // the host vector must outlive the copy
@@ -212,11 +263,19 @@ ew_status ComposedSmoother::apply(const GridGeom& g, const float* r, float* x, c
     if (g.dim != 3 || interior.size() != 125) return set_error(EW_EINVAL, "composed smoother: not built for a 3D grid");
     K125 K;
     std::memcpy(K.k, interior.data(), sizeof(K.k));
-    dim3 grid((unsigned)((g.n[0] + kCompTX - 1) / kCompTX), (unsigned)((g.n[1] + kCompTY - 1) / kCompTY),
-              (unsigned)((g.n[2] + kCompZ - 1) / kCompZ));
-    k_smoother_comp<<<grid, 256, 0, st>>>((int)g.n[0], (int)g.n[1], (int)g.n[2], r, x, K, dev.as<float>());
+    const int nx = (int)g.n[0], ny = (int)g.n[1], nz = (int)g.n[2];
+    dim3 grid((unsigned)((nx + kCompTX - 1) / kCompTX), (unsigned)((ny + kCompTY - 1) / kCompTY),
+              (unsigned)((nz + kCompZ - 1) / kCompZ));
+    k_smoother_comp<<<grid, 256, 0, st>>>(nx, ny, nz, r, x, K);
     EW_CUDA_TRY(cudaGetLastError());
-    count_launch();
+    const int64_t nz_part = (int64_t)(nz == 1 ? 1 : 2) * nx * ny;
+    const int64_t ny_part = (int64_t)std::max(nz - 2, 0) * (ny == 1 ? 1 : 2) * nx;
+    const int64_t nx_part = (int64_t)std::max(nz - 2, 0) * std::max(ny - 2, 0) * (nx == 1 ? 1 : 2);
+    const int64_t nwall = nz_part + ny_part + nx_part;
+    k_smoother_comp_walls<<<(unsigned)((nwall + 255) / 256), 256, 0, st>>>(nx, ny, nz, r, x, dev.as<float>(), nz_part,
+                                                                          ny_part, nwall);
+    EW_CUDA_TRY(cudaGetLastError());
+    count_launch(2);
     return EW_OK;
 }
 
