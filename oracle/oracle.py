@@ -524,7 +524,8 @@ NET_WEIGHTS = 2 * 8 * 27   # [W1 (8 x 27) | W2 (8 x 27)], taps (dz, dy, dx), dz 
 def mg_solve(g: Grid, a, b, x0=None, nu1=2, nu2=2, wJ=0.8, ncycles=1, net=None, red_black=False):
     """``ncycles`` multigrid V(nu1, nu2) cycles on (I - a L_h) x = b (eq. impMatrix).
 
-    The cycle (Jacobi, red-black Gauss-Seidel (order 2) or learned smoother,
+    The cycle (Jacobi, multi-colour Gauss-Seidel (red-black at order 2, three
+    colours at order 4) or learned smoother,
     full weighting, linear interpolation, CG on the coarsest level) is spelled
     out in ew_oracle_mg.c.
     ``net`` is None or an array (levels x NET_WEIGHTS) of learned-smoother
@@ -545,24 +546,41 @@ def mg_solve(g: Grid, a, b, x0=None, nu1=2, nu2=2, wJ=0.8, ncycles=1, net=None, 
     return x, hist
 
 
-def filter_implicit_mg(g: Grid, prm, v, nu1=2, nu2=2, wJ=0.8, ncycles=2, net=None):
+def filter_implicit_mg(g: Grid, prm, v, nu1=2, nu2=2, wJ=0.8, ncycles=2, net=None, guess="rhs",
+                       return_hist=False):
     """S v with the implicit scheme (eqs. implicitScheme, implicitStep1) where
-    every system M y = rhs gets `ncycles` multigrid V-cycles (ew_oracle_mg.c)
-    from the initial guess y = rhs (so W^0 for the first step and 2 W^n
-    after).  With ncycles large this tends to filter_implicit."""
+    every system M y = rhs gets `ncycles` multigrid V-cycles (ew_oracle_mg.c).
+    The systems are M W^1 = W^0 and, for n >= 1, M y = 2 W^n with
+    y = W^{n+1} + W^{n-1}.  The paper does not state the initial guess:
+      guess="rhs"       y = rhs (W^0 for the first system, 2 W^n after);
+      guess="previous"  from the third system on, the previous system's
+                        solution y_{n-1} = W^n + W^{n-2} (the second system
+                        starts from 2 W^1, which is y_0 = W^1 + W^{-1} under
+                        the initial condition W^{-1} = W^1).  When that system
+                        was solved exactly, M y_{n-1} = 2 W^{n-1}, so the
+                        initial residual is 2 (W^n - W^{n-1}), whatever h.
+    With ncycles large both tend to filter_implicit.  return_hist: also return
+    each system's residual history (before and after each cycle)."""
     v = np.asarray(v, dtype=np.float64).reshape(-1)
+    if guess not in ("rhs", "previous"):
+        raise ValueError("guess must be 'rhs' or 'previous'")
     a = 0.5 * prm["dt"] ** 2
     c = prm["c"]
     wm = v.copy()
-    w0, _ = mg_solve(g, a, wm, x0=wm, nu1=nu1, nu2=nu2, wJ=wJ, ncycles=ncycles, net=net)
+    w0, h = mg_solve(g, a, wm, x0=wm, nu1=nu1, nu2=nu2, wJ=wJ, ncycles=ncycles, net=net)
+    hists = [h]
     out = c[0] * wm + c[1] * w0
+    y_prev = None
     for n in range(1, prm["Nt"]):
         rhs = 2.0 * w0
-        y, _ = mg_solve(g, a, rhs, x0=rhs, nu1=nu1, nu2=nu2, wJ=wJ, ncycles=ncycles, net=net)
+        x0 = y_prev if (guess == "previous" and y_prev is not None) else rhs
+        y, h = mg_solve(g, a, rhs, x0=x0, nu1=nu1, nu2=nu2, wJ=wJ, ncycles=ncycles, net=net)
+        hists.append(h)
+        y_prev = y
         wp = y - wm
         wm, w0 = w0, wp
         out = out + c[n + 1] * wp
-    return out
+    return (out, hists) if return_hist else out
 
 
 def conv_net_forward(n3, w, r):

@@ -81,26 +81,21 @@ def test_multigrid_converges_to_exact_solve(dim, order):
     assert np.max(np.abs(x - exact)) < 1e-9 * np.max(np.abs(exact))
 
 
-@pytest.mark.parametrize("dim", [2, 3])
-def test_red_black_multigrid_converges_to_exact_solve_and_beats_jacobi(dim):
-    """Red-black Gauss-Seidel smoothing (second order): the same exact solve
-    (the sine-basis closed form of M^-1), and a smaller contraction per cycle
-    than damped Jacobi on a strongly elliptic system (a / h^2 >> 1)."""
+@pytest.mark.parametrize("dim,order", [(2, 2), (3, 2), (2, 4), (3, 4)])
+def test_red_black_multigrid_converges_to_exact_solve_and_beats_jacobi(dim, order):
+    """Multi-colour Gauss-Seidel smoothing (red-black at second order, three
+    colours at fourth order): the same exact solve (the sine-basis closed form
+    of M^-1), and a smaller contraction per cycle than damped Jacobi on a
+    strongly elliptic system (a / h^2 >> 1)."""
     n = (63, 63) if dim == 2 else (31, 31, 31)
-    g = O.Grid(n, (1.0,) * dim, 2)
+    g = O.Grid(n, (1.0,) * dim, order)
     a = 0.5 * (2 * math.pi / (12.0 * 10)) ** 2   # the 2D scaling runs' implicit step
     b = ew_inputs.uniform_pm1(8, g.size)
     exact = O.implicit_solve_closed_form(g, a, b)
-    xr, hr = O.mg_solve(g, a, b, ncycles=10, red_black=True)
-    xj, hj = O.mg_solve(g, a, b, ncycles=10)
+    xr, hr = O.mg_solve(g, a, b, ncycles=12, red_black=True)
+    xj, hj = O.mg_solve(g, a, b, ncycles=12)
     assert np.max(np.abs(xr - exact)) < 1e-9 * np.max(np.abs(exact))
     assert (hr[-1] / hr[0]) < 0.25 * (hj[-1] / hj[0])
-
-
-def test_red_black_refuses_the_wide_stencil():
-    g = O.Grid((15, 15), (1.0, 1.0), 4)
-    with pytest.raises(AssertionError):
-        O.mg_solve(g, 1e-3, np.ones(g.size), red_black=True)
 
 
 def _jacobi_as_net(g, a, wJ=0.8):
@@ -168,3 +163,28 @@ def test_implicit_filter_with_multigrid_tends_to_exact():
     e2 = np.max(np.abs(O.filter_implicit_mg(g, prm, v, ncycles=2) - exact))
     e12 = np.max(np.abs(O.filter_implicit_mg(g, prm, v, ncycles=12) - exact))
     assert e12 < 1e-9 and e12 < e2 / 1e5
+
+
+def test_previous_solution_guess_starts_from_the_closed_form_residual():
+    """With the previous system's solution as the initial guess (reading of the
+    unstated guess), system n starts from the residual 2 (W^n - W^{n-1}) when
+    the systems are solved (nearly) exactly, independent of h; the converged
+    wave-solve is the exactly solved one either way."""
+    g = O.Grid((15, 31), (1.0, 1.7), 4)
+    prm = O.filter_params(12.0, 1, 10, adjust=True)
+    v = ew_inputs.uniform_pm1(42, g.size)
+    exact = O.filter_implicit(g, prm, v)
+    a = 0.5 * prm["dt"] ** 2
+    out, hists = O.filter_implicit_mg(g, prm, v, ncycles=25, guess="previous", return_hist=True)
+    assert np.max(np.abs(out - exact)) < 1e-10 * np.max(np.abs(exact))
+    # the time levels of the exactly solved scheme, from its own recurrence
+    w = [v.copy(), O.cg_solve_M(g, a, v)]
+    for n in range(1, 5):
+        y = O.cg_solve_M(g, a, 2.0 * w[n])
+        w.append(y - w[n - 1])
+    for n in range(2, 5):     # the second system starts from 2 W^1 (y_0 under W^{-1} = W^1)
+        want = np.linalg.norm(2.0 * (w[n] - w[n - 1]))
+        assert hists[n][0] == pytest.approx(want, rel=1e-8)
+    # and the rhs guess starts much higher on this grid (residual a L_h 2 W^n)
+    _, hr = O.filter_implicit_mg(g, prm, v, ncycles=25, return_hist=True)
+    assert hr[3][0] > 3.0 * hists[3][0]
