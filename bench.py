@@ -87,6 +87,9 @@ def parse():
                     default="pair_and_plain",
                     help="eigs2d: the mixed arm with pair-arithmetic images and the plain FP64 arm (default), "
                          "or one arm")
+    ap.add_argument("--mg-guess", default="rhs", choices=["rhs", "previous"],
+                    help="scaling2d: initial guess of the implicit systems (the right-hand side, or the "
+                         "previous system's solution)")
     ap.add_argument("--red-black", action="store_true",
                     help="scaling2d: multi-colour Gauss-Seidel smoothing (red-black at second order, "
                          "three colours at fourth order)")
@@ -931,7 +934,7 @@ def run_extra(args):
                 m = 2 ** k - 1
                 g = ew.ew_grid_create(2, (m, m), (1.0, 1.0), order=order, prec="fp64")
                 rb = bool(args.red_black)
-                mg = ew.mg_params(pre=2, post=2, max_cycles=40, rtol=1e-10, red_black=rb)
+                mg = ew.mg_params(pre=2, post=2, max_cycles=40, rtol=1e-10, red_black=rb, guess=args.mg_guess)
                 p = ew.filter_params(12.0, num_periods=1, steps_per_period=10, scheme="implicit", adjust_omega=True,
                                      mg=mg)
                 e = ew.eigs_params(16, krylov_dim=48, block=2, tol=1e-10, seed=7, max_wave_solves=1000)
@@ -949,7 +952,7 @@ def run_extra(args):
                 rows[order].append(dict(
                     smoother=("red-black Gauss-Seidel" if order == 2 else "three-colour Gauss-Seidel") if rb
                     else "damped Jacobi",
-                    h="1/%d" % (m + 1), points=m * m, eigenpairs=int(rep["n_converged"]),
+                    guess=args.mg_guess, h="1/%d" % (m + 1), points=m * m, eigenpairs=int(rep["n_converged"]),
                     wave_solves=int(rep["wave_solves"]),
                     mg_cycles_per_solve=prof["mg_cycles"] / max(prof["mg_solves"], 1), seconds=sec,
                     ratio=(sec / prev) if prev else None,

@@ -148,6 +148,15 @@ typedef struct {
                                  Second order: red-black, colour (i + j + k) mod 2; fourth order:
                                  three colours, (i + j + k) mod 3, so that no stencil offset
                                  joins two points of one colour */
+    int guess;                /* initial guess of the implicit wave-solve's systems (the paper does
+                                 not state one; 0 or 1, EW_EINVAL otherwise).  The systems are
+                                 M W^1 = W^0 and, for n >= 1, M y = 2 W^n with y = W^{n+1} + W^{n-1}.
+                                 0: y = rhs (W^0 for the first system, 2 W^n after); its residual
+                                 is 2 a L_h W^n, which grows as 1/h^2 for rough W^n.
+                                 1: from the third system on, the previous system's solution
+                                 W^n + W^{n-2}; when that system was solved exactly its residual
+                                 is 2 (W^n - W^{n-1}), independent of h.  ew_implicit_step_mg
+                                 ignores it (its x is the guess) */
 } ew_mg_params;
 
 /* Filter parameters (Section "Discrete approximations").

@@ -121,12 +121,14 @@ def ew_grid_destroy(grid: Grid):
 
 
 def mg_params(pre=2, post=2, max_cycles=1, rtol=0.0, jacobi_weight=0.8, learned_levels=0, weights=None,
-              red_black=False):
+              red_black=False, guess="rhs"):
+    """guess: "rhs" (0) or "previous" (1), the implicit wave-solve's initial guess."""
     wp = None
     if weights is not None:
         import torch
         wp = _ptr(weights, torch.float32, 432 * max(int(learned_levels), 1))
-    m = ew_mg_params(pre, post, max_cycles, rtol, jacobi_weight, learned_levels, wp, int(bool(red_black)))
+    gs = {"rhs": 0, "previous": 1}.get(guess, guess)
+    m = ew_mg_params(pre, post, max_cycles, rtol, jacobi_weight, learned_levels, wp, int(bool(red_black)), int(gs))
     m._keep = weights
     return m
 

@@ -43,7 +43,8 @@ lib = _load()
 class ew_mg_params(ctypes.Structure):
     _fields_ = [("pre", ctypes.c_int), ("post", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("rtol", ctypes.c_double), ("jacobi_weight", ctypes.c_double),
-                ("learned_levels", ctypes.c_int), ("weights_dev", ctypes.c_void_p), ("red_black", ctypes.c_int)]
+                ("learned_levels", ctypes.c_int), ("weights_dev", ctypes.c_void_p), ("red_black", ctypes.c_int),
+                ("guess", ctypes.c_int)]
 
 
 class ew_filter_params(ctypes.Structure):

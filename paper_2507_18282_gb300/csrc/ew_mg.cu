@@ -241,7 +241,7 @@ __global__ void k_guess_rhs(int64_t N, const T* __restrict__ w, T* __restrict__ 
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
         T v = sc * w[q];
         b[q] = v;
-        x[q] = v;
+        if (x) x[q] = v;  // x == nullptr: keep the iterate as the guess
     }
 }
 
@@ -487,6 +487,7 @@ static ew_status check_mg(const ew_mg_params* mg) {
     if (mg->max_cycles < 1) return set_error(EW_EINVAL, "max_cycles must be >= 1");
     if (mg->learned_levels < 0) return set_error(EW_EINVAL, "learned_levels < 0");
     if (mg->red_black != 0 && mg->red_black != 1) return set_error(EW_EINVAL, "red_black must be 0 or 1");
+    if (mg->guess != 0 && mg->guess != 1) return set_error(EW_EINVAL, "guess must be 0 or 1");
     return EW_OK;
 }
 
@@ -516,8 +517,10 @@ static ew_status implicit_wave_solve_t(ew_grid* g, const FilterPlan& plan, const
         k_implicit_first<T><<<blocks, 256, 0, st>>>(N, Wm, W0, acc, (T)plan.c[0], (T)plan.c[1]);
         count_launch();
         for (int64_t n = 1; n < plan.Nt; ++n) {
-            // M y = 2 W^n from y = 2 W^n; W^{n+1} = y - W^{n-1} over W^{n-1}
-            k_guess_rhs<T><<<blocks, 256, 0, st>>>(N, W0, mg.B[0], mg.X[0], T(2));
+            // M y = 2 W^n from y = 2 W^n, or (guess 1, n >= 2) from the previous
+            // system's solution, which X[0] still holds; W^{n+1} = y - W^{n-1} over W^{n-1}
+            const bool keep = p->mg->guess == 1 && n >= 2;
+            k_guess_rhs<T><<<blocks, 256, 0, st>>>(N, W0, mg.B[0], keep ? nullptr : mg.X[0], T(2));
             count_launch();
             EW_TRY(mg.solve(p->mg->max_cycles, p->mg->rtol, &used));
             count_mg_solve(used);

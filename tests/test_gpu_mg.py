@@ -99,14 +99,16 @@ def test_mg_refuses_grids_that_do_not_coarsen(ew):
     g.close()
 
 
-@pytest.mark.parametrize("n,order", [((31, 31, 31), 4), ((63, 31), 2)])
-def test_implicit_wave_solve_parity_fp64(ew, n, order):
+@pytest.mark.parametrize("n,order,guess", [((31, 31, 31), 4, "rhs"), ((63, 31), 2, "rhs"),
+                                           ((31, 15, 31), 4, "previous"), ((63, 31), 2, "previous")])
+def test_implicit_wave_solve_parity_fp64(ew, n, order, guess):
     """Implicit wave-solve (adjusted omega, 10 steps per period, 2 V-cycles per
-    system) equals the oracle's implicit scheme with its own multigrid."""
+    system) equals the oracle's implicit scheme with its own multigrid, for
+    either initial guess of the systems."""
     L = tuple(1.0 for _ in n)
     g = ew.ew_grid_create(len(n), n, L, order=order, prec="fp64")
     og = O.Grid(n, L, order)
-    mg = ew.mg_params(pre=2, post=2, max_cycles=2)
+    mg = ew.mg_params(pre=2, post=2, max_cycles=2, guess=guess)
     p = ew.filter_params(12.0, num_periods=2, steps_per_period=10, scheme="implicit", adjust_omega=True, mg=mg)
     v = ew_inputs.uniform_pm1(24, og.size)
     vin = torch.tensor(v, device="cuda")
@@ -114,7 +116,7 @@ def test_implicit_wave_solve_parity_fp64(ew, n, order):
     ew.ew_filter_apply(g, p, vin, vout)
     torch.cuda.synchronize()
     prm = O.filter_params(12.0, 2, 10, adjust=True)
-    ref = O.filter_implicit_mg(og, prm, v, ncycles=2)
+    ref = O.filter_implicit_mg(og, prm, v, ncycles=2, guess=guess)
     np.testing.assert_allclose(vout.cpu().numpy(), ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
     g.close()
 
@@ -199,4 +201,13 @@ def test_learned_smoother_beats_plain_multigrid(ew):
     assert rep["loss_last"] < rep["loss_first"]
     assert rep["accepted"], rep
     assert rep["conv_learned"] < rep["conv_plain"], rep
+    g.close()
+
+
+def test_mg_guess_must_be_0_or_1(ew):
+    g = ew.ew_grid_create(2, (31, 31), (1.0, 1.0), order=2, prec="fp64")
+    p = ew.filter_params(12.0, steps_per_period=10, scheme="implicit", mg=ew.mg_params(guess=2))
+    x = torch.zeros(g.size, dtype=torch.float64, device="cuda")
+    with pytest.raises(ew.EWError, match="EW_EINVAL"):
+        ew.ew_filter_apply(g, p, x, torch.empty_like(x))
     g.close()
