@@ -43,7 +43,7 @@ namespace ew {
 
 constexpr int kCompTX = 128;  // outputs per CTA row (32 threads x 4)
 constexpr int kCompTY = 8;    // rows per CTA
-constexpr int kCompZ = 32;    // planes per CTA
+constexpr int kCompZMin = 16;  // fewest planes per CTA (the grid's z chunks are chosen at launch)
 constexpr int kCompSX = kCompTX + 4;  // staged width (halo 2), a multiple of 4
 constexpr int kCompSY = kCompTY + 4;
 constexpr int kCompPlane = kCompSX * kCompSY;
@@ -57,16 +57,18 @@ __host__ __device__ __forceinline__ int comp_class(int i, int n) {
     return n == 1 ? 3 : (i == 0 ? 0 : (i == n - 1 ? 2 : 1));
 }
 
-// x += K_int * r at every output (FP32 fields, r zero outside the box)
+// x += K_int * r at every output (FP32 fields, r zero outside the box); a
+// CTA owns planes [z0, z0 + zc) of its 128 x 8 columns
 __global__ void __launch_bounds__(256, 4)
-    k_smoother_comp(int nx, int ny, int nz, const float* __restrict__ r, float* __restrict__ x, const K125 K) {
+    k_smoother_comp(int nx, int ny, int nz, int zc, const float* __restrict__ r, float* __restrict__ x, const K125 K) {
     constexpr int kPer = (kCompPlane + 255) / 256;  // staged elements per thread and plane
     __shared__ __align__(16) float sp[2][kCompPlane];
     const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
-    const int x0 = blockIdx.x * kCompTX, y0 = blockIdx.y * kCompTY, z0 = blockIdx.z * kCompZ;
-    const int z1 = min(nz, z0 + kCompZ);
+    const int x0 = blockIdx.x * kCompTX, y0 = blockIdx.y * kCompTY, z0 = blockIdx.z * zc;
+    const int z1 = min(nz, z0 + zc);
     const int ox = x0 + 4 * lx, oy = y0 + ly;  // first output of the thread
     const int64_t plane = (int64_t)nx * ny;
+    const bool orow = oy < ny;
     // the staged elements of this thread: offset within a plane, or -1 outside the box
     int off[kPer];
 #pragma unroll
@@ -102,7 +104,19 @@ __global__ void __launch_bounds__(256, 4)
     __syncthreads();
     int buf = 0;
     for (int zi = z0 - 2; zi <= z1 + 1; ++zi) {
-        // input plane zi feeds output planes zi - 2 .. zi + 2 (acc[0] .. acc[4]) with dz = 2 - j
+        // x of the output plane completed in this iteration, loaded now so that
+        // the plane's multiply-adds hide the latency
+        const int zo = zi - 2;
+        const bool ostore = zo >= z0 && zo < z1 && orow;
+        float xo[4];
+        float* px = x + (int64_t)zo * plane + (int64_t)oy * nx + ox;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xo[i] = (ostore && ox + i < nx) ? px[i] : 0.f;
+        // input plane zi feeds output planes zi - 2 .. zi + 2 (acc[0] .. acc[4]) with dz = 2 - j;
+        // output planes outside [z0, z1) are skipped (the same for the whole CTA)
+        bool need[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) need[j] = zi - 2 + j >= z0 && zi - 2 + j < z1;
         const float* p = sp[buf] + ly * kCompSX + 4 * lx;
 #pragma unroll
         for (int dy = 0; dy < 5; ++dy) {
@@ -111,6 +125,7 @@ __global__ void __launch_bounds__(256, 4)
             const float w[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
 #pragma unroll
             for (int j = 0; j < 5; ++j) {
+                if (!need[j]) continue;
                 const int dz = 2 - j;
 #pragma unroll
                 for (int dx = 0; dx < 5; ++dx) {
@@ -121,12 +136,10 @@ __global__ void __launch_bounds__(256, 4)
             }
         }
         // output plane zi - 2 is complete
-        const int zo = zi - 2;
-        if (zo >= z0 && zo < z1 && oy < ny) {
-            float* px = x + (int64_t)zo * plane + (int64_t)oy * nx + ox;
+        if (ostore) {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                if (ox + i < nx) px[i] += acc[0][i];
+                if (ox + i < nx) px[i] = xo[i] + acc[0][i];
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -145,7 +158,12 @@ __global__ void __launch_bounds__(256, 4)
 
 // Wall outputs, in three disjoint parts: the z-wall planes (all x, y), then
 // the y-wall rows of the other planes (all x), then the x-wall points of the
-// remaining rows.  Each adds sum_d (K_class - K_int)(d) r(p + d).
+// remaining rows.  Each adds sum_d (K_class - K_int)(d) r(p + d).  On a wall
+// axis a the difference is made of hidden offsets beyond the wall, whose taps
+// reach r at offsets d_a in {-2, -1, 0} (low wall) or {0, 1, 2} (high wall),
+// all outside the box but d_a = 0 (and only d_a = 0 for n = 1): so only the
+// taps with d_a = 0 on some wall axis a are summed (25 on a face, 45 on an
+// edge, 61 at a corner), each once.
 __global__ void __launch_bounds__(256)
     k_smoother_comp_walls(int nx, int ny, int nz, const float* __restrict__ r, float* __restrict__ x,
                           const float* __restrict__ kdiff, int64_t nz_part, int64_t ny_part, int64_t nwall) {
@@ -173,25 +191,40 @@ __global__ void __launch_bounds__(256)
         gy = 1 + (int)(rem / cxn);
         gx = (rem % cxn) ? nx - 1 : 0;
     }
-    const int cls = (comp_class(gz, nz) * 4 + comp_class(gy, ny)) * 4 + comp_class(gx, nx);
-    const float* kd = kdiff + (size_t)cls * 125;
+    const int cz = comp_class(gz, nz), cy = comp_class(gy, ny), cx = comp_class(gx, nx);
+    const bool wz = cz != 1, wy = cy != 1, wx = cx != 1;
+    const float* kd = kdiff + (size_t)((cz * 4 + cy) * 4 + cx) * 125;
+    const int64_t q = ((int64_t)gz * ny + gy) * nx + gx;
     float s = 0.f;
+    // taps with dz = 0 (z wall)
+    if (wz) {
 #pragma unroll
-    for (int dz = -2; dz <= 2; ++dz) {
-        const int zz = gz + dz;
+        for (int dy = -2; dy <= 2; ++dy)
 #pragma unroll
-        for (int dy = -2; dy <= 2; ++dy) {
-            const int yy = gy + dy;
-#pragma unroll
-            for (int dx = -2; dx <= 2; ++dx) {
-                const int xx = gx + dx;
-                if (zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx)
-                    s = fmaf(__ldg(kd + (dz + 2) * 25 + (dy + 2) * 5 + (dx + 2)),
-                             r[((int64_t)zz * ny + yy) * nx + xx], s);
-            }
-        }
+            for (int dx = -2; dx <= 2; ++dx)
+                if (gy + dy >= 0 && gy + dy < ny && gx + dx >= 0 && gx + dx < nx)
+                    s = fmaf(__ldg(kd + 50 + (dy + 2) * 5 + (dx + 2)), r[q + (int64_t)dy * nx + dx], s);
     }
-    x[((int64_t)gz * ny + gy) * nx + gx] += s;
+    // taps with dy = 0 (y wall), dz = 0 already summed on a z wall
+    if (wy) {
+#pragma unroll
+        for (int dz = -2; dz <= 2; ++dz)
+#pragma unroll
+            for (int dx = -2; dx <= 2; ++dx)
+                if (!(wz && dz == 0) && gz + dz >= 0 && gz + dz < nz && gx + dx >= 0 && gx + dx < nx)
+                    s = fmaf(__ldg(kd + (dz + 2) * 25 + 10 + (dx + 2)), r[q + (int64_t)dz * ny * nx + dx], s);
+    }
+    // taps with dx = 0 (x wall), dz = 0 or dy = 0 already summed on those walls
+    if (wx) {
+#pragma unroll
+        for (int dz = -2; dz <= 2; ++dz)
+#pragma unroll
+            for (int dy = -2; dy <= 2; ++dy)
+                if (!(wz && dz == 0) && !(wy && dy == 0) && gz + dz >= 0 && gz + dz < nz && gy + dy >= 0 &&
+                    gy + dy < ny)
+                    s = fmaf(__ldg(kd + (dz + 2) * 25 + (dy + 2) * 5 + 2), r[q + ((int64_t)dz * ny + dy) * nx], s);
+    }
+    x[q] += s;
 }
 
 // round to the nearest BF16 (ties to even), as the tensor-core kernels do
@@ -264,9 +297,16 @@ ew_status ComposedSmoother::apply(const GridGeom& g, const float* r, float* x, c
     K125 K;
     std::memcpy(K.k, interior.data(), sizeof(K.k));
     const int nx = (int)g.n[0], ny = (int)g.n[1], nz = (int)g.n[2];
-    dim3 grid((unsigned)((nx + kCompTX - 1) / kCompTX), (unsigned)((ny + kCompTY - 1) / kCompTY),
-              (unsigned)((nz + kCompZ - 1) / kCompZ));
-    k_smoother_comp<<<grid, 256, 0, st>>>(nx, ny, nz, r, x, K);
+    // z chunks: as many as fill the resident CTA slots once (four a SM), at
+    // least kCompZMin planes each (each chunk restages two planes on each side)
+    int cdev = 0, nsm = 0;
+    EW_CUDA_TRY(cudaGetDevice(&cdev));
+    EW_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, cdev));
+    const int bx = (nx + kCompTX - 1) / kCompTX, by = (ny + kCompTY - 1) / kCompTY;
+    const int nzc = std::max(1, (4 * nsm) / std::max(1, bx * by));
+    const int zc = std::max(std::min(kCompZMin, nz), (nz + nzc - 1) / nzc);
+    dim3 grid((unsigned)bx, (unsigned)by, (unsigned)((nz + zc - 1) / zc));
+    k_smoother_comp<<<grid, 256, 0, st>>>(nx, ny, nz, zc, r, x, K);
     EW_CUDA_TRY(cudaGetLastError());
     const int64_t nz_part = (int64_t)(nz == 1 ? 1 : 2) * nx * ny;
     const int64_t ny_part = (int64_t)std::max(nz - 2, 0) * (ny == 1 ? 1 : 2) * nx;

@@ -263,12 +263,12 @@ __global__ void __launch_bounds__(32 * NWX * NTY + 32, 1)
         }
         warm_acc(blockIdx.x);
         if ((int)(blockIdx.x + gridDim.x) < ntiles) warm_acc(blockIdx.x + gridDim.x);
-        unsigned ph[2] = {0u, 0u};
+        unsigned ph = 0u;  // bit s: the parity to wait for on slot s (a register, not an indexed array)
         int k = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
             const int s = k & 1;
-            const bool ok = tma_mbar_wait_bounded(&done[s], ph[s]);
-            ph[s] ^= 1u;
+            const bool ok = tma_mbar_wait_bounded(&done[s], (ph >> s) & 1u);
+            ph ^= 1u << s;
             if (!__all_sync(0xffffffffu, ok)) {
                 if (lane == 0) {
                     bulk_wait_all();
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(32 * NWX * NTY + 32, 1)
     const int sy0 = R + ty * KY;              // first staged row of its segment
     const float2 C0{st.c0, st.c0}, C1X{st.c1[0], st.c1[0]}, C1Y{st.c1[1], st.c1[1]};
     const float2 C2X{st.c2[0], st.c2[0]}, C2Y{st.c2[1], st.c2[1]};
-    unsigned ph[2] = {0u, 0u};
+    unsigned ph = 0u;  // bit s: the parity to wait for on slot s
     int k = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
         const int s = k & 1;
@@ -337,8 +337,8 @@ __global__ void __launch_bounds__(32 * NWX * NTY + 32, 1)
                 accp[kk].y = (own_b && oy) ? acc[base + (int64_t)kk * nx + 1] : 0.f;
             }
         }
-        const bool ok = tma_mbar_wait_bounded(&full[s], ph[s]);
-        ph[s] ^= 1u;
+        const bool ok = tma_mbar_wait_bounded(&full[s], (ph >> s) & 1u);
+        ph ^= 1u << s;
         if (cbar_or<NTC>(!ok)) {
             if (tid == 0) atomicExch(&g_tma2d_timeout, 1);
             return;  // the producer gives up on its wait for this tile
