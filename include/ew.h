@@ -243,8 +243,11 @@ ew_status ew_filter_apply(const ew_grid* grid, const ew_filter_params* params, c
  * every problem is cut into rounds of a few time steps, each round is one
  * persistent launch over all unfinished problems' tiles, and the whole
  * sequence is one CUDA graph replayed on `stream`; the tile shape is
- * autotuned once per batch shape.  Other mixes run one ew_filter_apply per
- * problem.  The batched workspace is process-wide: calls must not overlap. */
+ * autotuned once per batch shape.  In FP32, a problem whose N x nvec reaches
+ * three waves of 116 x 88 tiles over the GPU's SMs runs alone first, through
+ * ew_filter_apply's tuned kernel (the results are the same bits either way).
+ * Other mixes run one ew_filter_apply per problem.  The batched workspace is
+ * process-wide: calls must not overlap. */
 ew_status ew_filter_apply_batched(int nprob, const ew_grid* const* grids, const ew_filter_params* params,
                                   const void* const* v_in_dev, void* const* v_out_dev, const int* nvec,
                                   cudaStream_t stream);

@@ -454,7 +454,26 @@ ew_status filter_apply_batched_impl(int nprob, const ew_grid* const* grids, cons
             EW_TRY(ew_filter_apply(grids[q], &params[q], v_in[q], v_out[q], nvec ? nvec[q] : 1, stream));
         return EW_OK;
     }
-    if (g0->prec == EW_FP32) return batched_t<float>(P, g0->geom.order, stream, variant);
+    if (g0->prec == EW_FP32) {
+        // FP32: a problem whose own tiles fill the GPU three times over runs alone, on
+        // the tuned single-problem kernel (TMA-staged, faster than the batched tile
+        // form on large boxes); the others share the batched launch.  Every tile form
+        // gives the same bits, so the split changes no result.
+        int nsm = 0;
+        EW_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const int64_t alone_cells = 3ll * nsm * 116 * 88;  // three waves of the headline tile
+        std::vector<BProblem> rest;
+        size_t k = 0;
+        for (int q = 0; q < nprob; ++q) {
+            const int nv = nvec ? nvec[q] : 1;
+            const bool alone = grids[q]->geom.N * nv >= alone_cells;
+            if (alone) EW_TRY(ew_filter_apply(grids[q], &params[q], v_in[q], v_out[q], nv, stream));
+            for (int v = 0; v < nv; ++v, ++k)
+                if (!alone) rest.push_back(P[k]);
+        }
+        if (rest.empty()) return EW_OK;
+        return batched_t<float>(rest, g0->geom.order, stream, variant);
+    }
     return batched_t<double>(P, g0->geom.order, stream, variant);
 }
 

@@ -121,6 +121,178 @@ __global__ void k_mg_rbgs(int64_t nx, int64_t ny, int64_t nz, T* __restrict__ x,
     x[q] = x[q] + inv_d * r;
 }
 
+// ---------------------------------------------------------------------------
+// 3D stencil operations of the cycle, 2.5D blocked: a CTA owns 64 x 8 columns
+// and a chunk of planes and streams along z through a ring of kPlS staged
+// planes (each with a halo of R = ORDER / 2 in x and y).  The planes are
+// filled by asynchronous copies kPlD planes ahead of the one the stencil needs
+// next, so the loads of several planes are in flight while a plane is
+// computed, and every value of x is read from memory about once.  b goes
+// through a ring of its own (no halo).  Dirichlet box closure (the multigrid
+// levels have no Neumann faces): a wall point is 0, a point beyond it the
+// negated mirror; each staged cell is either 0 or a copy of one point of the
+// box, negated by the thread that copied it once the copy has landed.
+// MODE 0: out = r = b - M x; MODE 1: out = x + wd (b - M x) (Jacobi); MODE 2:
+// the colour sweep in place (out == x), x += wd (b - M x) at the points of
+// colour `colour` (mg_colour).  The Laplacian sums its terms in the order of
+// lap_global.
+constexpr int kPlBX = 64, kPlBY = 8, kPlNT = 256, kPlD = 2;
+
+// index of coordinate i on an axis of n points under the odd closure
+// (|i - clamp| <= 2): -1 for a wall point, else the mirror with sg negated
+__device__ __forceinline__ int mg_ext(int i, int n, int& sg) {
+    if (i >= 0 && i < n) return i;
+    if (i == -1 || i == n) return -1;
+    sg = -sg;
+    return i < 0 ? -2 - i : 2 * n - i;
+}
+
+template <typename T>
+__device__ __forceinline__ void mg_cp_async(T* dst, const T* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (sizeof(T) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void mg_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void mg_cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename T, int ORDER>
+struct PlaneRing {
+    static constexpr int R = ORDER == 2 ? 1 : 2;
+    static constexpr int SX = kPlBX + 2 * R, SY = kPlBY + 2 * R, CELLS = SX * SY;
+    static constexpr int S = 2 * R + 1 + kPlD;                 // planes z - R .. z + R + kPlD
+    static constexpr int PER = (CELLS + kPlNT - 1) / kPlNT;    // staged cells per thread and plane
+    static constexpr int BPER = kPlBX * kPlBY / kPlNT;         // b cells per thread and plane
+    static constexpr size_t SMEM = sizeof(T) * (size_t)S * (CELLS + kPlBX * kPlBY);
+    static_assert(PER * S <= 32, "negation flags of the ring fit one word");
+};
+
+template <typename T, int ORDER, int MODE>
+__global__ void __launch_bounds__(kPlNT)
+    k_mg_plane3d(int nx, int ny, int nz, int zc, const T* x, const T* __restrict__ b, T* out, Stencil<T> sa, T wd,
+                 int colour) {
+    using PR = PlaneRing<T, ORDER>;
+    constexpr int R = PR::R, SX = PR::SX, CELLS = PR::CELLS, S = PR::S, PER = PR::PER, BPER = PR::BPER;
+    extern __shared__ __align__(16) unsigned char mg_smem[];
+    T* ring = reinterpret_cast<T*>(mg_smem);  // [S][CELLS]
+    T* bring = ring + (size_t)S * CELLS;      // [S][kPlBX * kPlBY]
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * kPlBX, y0 = blockIdx.y * kPlBY;
+    const int z0 = blockIdx.z * zc, z1 = min(nz, z0 + zc);
+    const int64_t plane = (int64_t)nx * ny;
+    unsigned neg = 0;  // bit (slot * PER + u): this thread's cell u of ring slot `slot` awaits negation
+    // the thread's staged cells, the same in every plane: offset of the source
+    // column in a plane (-1: 0 for every plane), and which are negated mirrors
+    int coff[PER];
+    unsigned cneg = 0;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int c = tid + kPlNT * u;
+        const int sy = c / SX, sx = c - sy * SX;
+        const int hx = x0 - R + sx, hy = y0 - R + sy;
+        int sg = 1;
+        const int ex = hx < nx + R ? mg_ext(hx, nx, sg) : -1;  // past a ragged tile's reach: never read
+        const int ey = hy < ny + R ? mg_ext(hy, ny, sg) : -1;
+        coff[u] = (c < CELLS && ex >= 0 && ey >= 0) ? ey * nx + ex : -1;
+        if (sg < 0) cneg |= 1u << u;
+    }
+    int boff[BPER];
+#pragma unroll
+    for (int u = 0; u < BPER; ++u) {
+        const int c = tid + kPlNT * u;
+        const int cy = c / kPlBX, cx = c - cy * kPlBX;
+        boff[u] = (x0 + cx < nx && y0 + cy < ny) ? (y0 + cy) * nx + x0 + cx : -1;
+    }
+    // stage plane p (any integer in [z0 - R, z1 + R)) into its slot, and b of plane p (when inside [z0, z1))
+    auto issue = [&](int p) {
+        if (p >= z1 + R) {  // past the chunk's last stencil plane: an empty group keeps the count
+            mg_cp_commit();
+            return;
+        }
+        const int slot = ((p % S) + S) % S;
+        T* dst = ring + (size_t)slot * CELLS;
+        int sgz = 1;
+        const int ez = mg_ext(p, nz, sgz);
+        const T* xp = x + (int64_t)(ez < 0 ? 0 : ez) * plane;
+        const unsigned flip = sgz < 0 ? (1u << PER) - 1 : 0u;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int c = tid + kPlNT * u;
+            if (c >= CELLS) break;
+            if (ez < 0 || coff[u] < 0) {
+                dst[c] = T(0);
+            } else {
+                mg_cp_async(dst + c, xp + coff[u]);
+                if (((cneg ^ flip) >> u) & 1u) neg |= 1u << (slot * PER + u);
+            }
+        }
+        if (p >= z0 && p < z1) {
+            T* bd = bring + (size_t)slot * (kPlBX * kPlBY);
+            const T* bp = b + (int64_t)p * plane;
+#pragma unroll
+            for (int u = 0; u < BPER; ++u)
+                if (boff[u] >= 0) mg_cp_async(bd + tid + kPlNT * u, bp + boff[u]);
+        }
+        mg_cp_commit();
+    };
+    auto negate = [&](int p) {  // after its copies landed: this thread's negated cells of plane p
+        const int slot = ((p % S) + S) % S;
+        T* dst = ring + (size_t)slot * CELLS;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const unsigned bit = 1u << (slot * PER + u);
+            if (neg & bit) {
+                dst[tid + kPlNT * u] = -dst[tid + kPlNT * u];
+                neg &= ~bit;
+            }
+        }
+    };
+    // prologue: planes z0 - R .. z0 + R + kPlD - 1, one group each
+    for (int p = z0 - R; p < z0 + R + kPlD; ++p) issue(p);
+    const T c1x = sa.c1[0], c1y = sa.c1[1], c1z = sa.c1[2], c2x = sa.c2[0], c2y = sa.c2[1], c2z = sa.c2[2];
+    const int tx = tid % kPlBX, ty0 = tid / kPlBX;  // rows ty0 and ty0 + 4
+    for (int z = z0; z < z1; ++z) {
+        // plane z + R's group and every older one have landed (kPlD - 1 younger groups may be in flight)
+        mg_cp_wait<kPlD - 1>();
+        if (z == z0)
+            for (int p = z0 - R; p <= z0 + R; ++p) negate(p);
+        else
+            negate(z + R);
+        __syncthreads();  // plane z + R visible to all; every read of iteration z - 1 done
+        issue(z + R + kPlD);  // into the slot of plane z - R - 1, last read in iteration z - 1
+        const T* pc = ring + (size_t)(z % S) * CELLS;
+        const T* bz = bring + (size_t)(z % S) * (kPlBX * kPlBY);
+#pragma unroll
+        for (int rr = 0; rr < kPlBY / 4; ++rr) {
+            const int ty = ty0 + 4 * rr;
+            const int gx = x0 + tx, gy = y0 + ty;
+            if (gx >= nx || gy >= ny) continue;
+            const int cc = (ty + R) * SX + tx + R;
+            const T xc = pc[cc];
+            T lap = sa.c0 * xc;
+            lap += c1x * (pc[cc - 1] + pc[cc + 1]);
+            lap += c1y * (pc[cc - SX] + pc[cc + SX]);
+            lap += c1z * (ring[(size_t)((z - 1 + S) % S) * CELLS + cc] + ring[(size_t)((z + 1) % S) * CELLS + cc]);
+            if (ORDER == 4) {
+                lap += c2x * (pc[cc - 2] + pc[cc + 2]);
+                lap += c2y * (pc[cc - 2 * SX] + pc[cc + 2 * SX]);
+                lap += c2z * (ring[(size_t)((z - 2 + S) % S) * CELLS + cc] + ring[(size_t)((z + 2) % S) * CELLS + cc]);
+            }
+            const T r = (bz[ty * kPlBX + tx] - xc) + lap;
+            const int64_t qi = (int64_t)z * plane + (int64_t)gy * nx + gx;
+            if (MODE == 0) out[qi] = r;
+            if (MODE == 1) out[qi] = xc + wd * r;
+            if (MODE == 2 && mg_colour<ORDER>(gx, gy, z) == colour) out[qi] = xc + wd * r;
+        }
+    }
+    mg_cp_wait<0>();  // no copy outlives the CTA
+}
+
 template <typename T>
 __device__ __forceinline__ T get0(const T* __restrict__ v, int64_t i, int64_t j, int64_t k, int64_t nx, int64_t ny,
                                   int64_t nz) {
@@ -294,6 +466,36 @@ struct MGSolver {
         if (g->geom.map) return set_error(EW_EUNSUPPORTED, "multigrid: mapped grids are not implemented");
         if (g->prec == EW_FP32X2) return set_error(EW_EUNSUPPORTED, "multigrid: FP32 or FP64 grids only");
         nlev = mg_levels(g->geom, lv, 16);
+        {
+            int dev = 0;
+            EW_CUDA_TRY(cudaGetDevice(&dev));
+            EW_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+            const int s2 = (int)PlaneRing<T, 2>::SMEM, s4 = (int)PlaneRing<T, 4>::SMEM;
+            const auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+            EW_CUDA_TRY(cudaFuncSetAttribute(k_mg_plane3d<T, 2, 0>, A, s2));
+            EW_CUDA_TRY(cudaFuncSetAttribute(k_mg_plane3d<T, 2, 1>, A, s2));
+            EW_CUDA_TRY(cudaFuncSetAttribute(k_mg_plane3d<T, 2, 2>, A, s2));
+            EW_CUDA_TRY(cudaFuncSetAttribute(k_mg_plane3d<T, 4, 0>, A, s4));
+            EW_CUDA_TRY(cudaFuncSetAttribute(k_mg_plane3d<T, 4, 1>, A, s4));
+            EW_CUDA_TRY(cudaFuncSetAttribute(k_mg_plane3d<T, 4, 2>, A, s4));
+            // resident CTAs a SM (the fewest over the modes): the z chunks fill them once
+            int o = 0;
+            pl_occ[0] = pl_occ[1] = 1 << 20;
+            EW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_mg_plane3d<T, 2, 0>, kPlNT, s2));
+            pl_occ[0] = std::min(pl_occ[0], o);
+            EW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_mg_plane3d<T, 2, 1>, kPlNT, s2));
+            pl_occ[0] = std::min(pl_occ[0], o);
+            EW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_mg_plane3d<T, 2, 2>, kPlNT, s2));
+            pl_occ[0] = std::min(pl_occ[0], o);
+            EW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_mg_plane3d<T, 4, 0>, kPlNT, s4));
+            pl_occ[1] = std::min(pl_occ[1], o);
+            EW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_mg_plane3d<T, 4, 1>, kPlNT, s4));
+            pl_occ[1] = std::min(pl_occ[1], o);
+            EW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_mg_plane3d<T, 4, 2>, kPlNT, s4));
+            pl_occ[1] = std::min(pl_occ[1], o);
+            pl_occ[0] = std::max(pl_occ[0], 1);
+            pl_occ[1] = std::max(pl_occ[1], 1);
+        }
         if (g->geom.n[1] > 65535 || g->geom.n[2] > 65535)
             return set_error(EW_EUNSUPPORTED, "multigrid: axes longer than 65535 points");
         if (lv[nlev - 1].N > kCoarseMax)
@@ -339,11 +541,36 @@ struct MGSolver {
         count_launch();                                                                                  \
     } while (0)
 
+    // 3D levels: the 2.5D-blocked stencil kernel; 2D levels: one thread per point
+    int nsm = 0, pl_occ[2] = {1, 1};  // SMs; resident plane-kernel CTAs a SM (order 2, order 4)
+    template <int MODE>
+    void plane3d(const GridGeom& g_, const T* x, const T* b, T* out, const Stencil<T>& sa, T wd, int colour) {
+        const int nx = (int)g_.n[0], ny = (int)g_.n[1], nz = (int)g_.n[2];
+        const int bx = (nx + kPlBX - 1) / kPlBX, by = (ny + kPlBY - 1) / kPlBY;
+        // z chunks: enough CTAs to fill the resident slots once, at least 8 planes each
+        const int nzc = std::max(1, (pl_occ[g_.order == 2 ? 0 : 1] * nsm) / std::max(1, bx * by));
+        const int zc = std::max(std::min(8, nz), (nz + nzc - 1) / nzc);
+        const dim3 grid((unsigned)bx, (unsigned)by, (unsigned)((nz + zc - 1) / zc));
+        if (g_.order == 2)
+            k_mg_plane3d<T, 2, MODE><<<grid, kPlNT, PlaneRing<T, 2>::SMEM, st>>>(nx, ny, nz, zc, x, b, out, sa, wd,
+                                                                              colour);
+        else
+            k_mg_plane3d<T, 4, MODE><<<grid, kPlNT, PlaneRing<T, 4>::SMEM, st>>>(nx, ny, nz, zc, x, b, out, sa, wd,
+                                                                              colour);
+        count_launch();
+    }
+    void resid(int L, const Stencil<T>& sa) {
+        if (lv[L].dim == 3)
+            plane3d<0>(lv[L], X[L], B[L], R[L], sa, T(0), 0);
+        else
+            EW_MG_DISPATCH(k_mg_resid, lv[L], X[L], B[L], R[L], sa);
+    }
+
     ew_status smooth(int L, int steps) {
         Stencil<T> sa = make_stencil<T>(lv[L], a);
         for (int s = 0; s < steps; ++s) {
             if (L < p->learned_levels) {
-                EW_MG_DISPATCH(k_mg_resid, lv[L], X[L], B[L], R[L], sa);
+                resid(L, sa);
                 if constexpr (sizeof(T) == 4) {
                     if (use_comp) {
                         EW_TRY(comp[L].apply(lv[L], R[L], X[L], st));
@@ -360,6 +587,10 @@ struct MGSolver {
                 const int ncol = g_.order == 2 ? 2 : 3;
                 for (int colour = 0; colour < ncol; ++colour) {
                     const int64_t nz3 = g_.dim == 3 ? g_.n[2] : 1;
+                    if (g_.dim == 3) {
+                        plane3d<2>(g_, X[L], B[L], X[L], sa, inv_d, colour);
+                        continue;
+                    }
                     if (g_.dim == 2 && g_.order == 2)
                         k_mg_rbgs<T, 2, 2><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], 1, X[L], B[L], sa, inv_d, colour);
                     else if (g_.dim == 2)
@@ -374,7 +605,10 @@ struct MGSolver {
                 }
             } else {
                 T wd = (T)(wJ / diag(L));
-                EW_MG_DISPATCH(k_mg_jacobi, lv[L], X[L], B[L], Tm[L], sa, wd);
+                if (lv[L].dim == 3)
+                    plane3d<1>(lv[L], X[L], B[L], Tm[L], sa, wd, 0);
+                else
+                    EW_MG_DISPATCH(k_mg_jacobi, lv[L], X[L], B[L], Tm[L], sa, wd);
                 std::swap(X[L], Tm[L]);
             }
         }
@@ -404,7 +638,7 @@ struct MGSolver {
         if (L == nlev - 1) return coarse(L);
         EW_TRY(smooth(L, p->pre));
         Stencil<T> sa = make_stencil<T>(lv[L], a);
-        EW_MG_DISPATCH(k_mg_resid, lv[L], X[L], B[L], R[L], sa);
+        resid(L, sa);
         const GridGeom &f = lv[L], &c = lv[L + 1];
         const int fz = f.dim == 3 ? (int)f.n[2] : 1, cz = f.dim == 3 ? (int)c.n[2] : 1;
         if (f.dim == 2)
@@ -461,7 +695,7 @@ struct MGSolver {
         while (c < max_cycles) {
             EW_TRY(vcycle(0));
             ++c;
-            EW_MG_DISPATCH(k_mg_resid, lv[0], X[0], B[0], R[0], sa);
+            resid(0, sa);
             double rk = 0.0;
             EW_TRY(norm2(R[0], &rk));
             if (rk <= rtol * bn) break;
@@ -562,11 +796,15 @@ static ew_status step_mg_t(ew_grid* g, double a, const T* rhs, T* x, const ew_mg
         {
             const GridGeom& gg = g->geom;
             dim3 grid_ = pt_grid(gg.n[0], gg.n[1], gg.dim == 3 ? gg.n[2] : 1), blk_(pt_threads(gg.n[0]));
-            if (gg.dim == 2 && gg.order == 2) k_mg_resid<T, 2, 2><<<grid_, blk_, 0, st>>>(gg.n[0], gg.n[1], 1, mg.X[0], mg.B[0], r, sa);
-            else if (gg.dim == 2) k_mg_resid<T, 2, 4><<<grid_, blk_, 0, st>>>(gg.n[0], gg.n[1], 1, mg.X[0], mg.B[0], r, sa);
-            else if (gg.order == 2) k_mg_resid<T, 3, 2><<<grid_, blk_, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
-            else k_mg_resid<T, 3, 4><<<grid_, blk_, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
-            count_launch();
+            if (gg.dim == 3) {
+                mg.template plane3d<0>(gg, mg.X[0], mg.B[0], r, sa, T(0), 0);
+            } else {
+                if (gg.order == 2)
+                    k_mg_resid<T, 2, 2><<<grid_, blk_, 0, st>>>(gg.n[0], gg.n[1], 1, mg.X[0], mg.B[0], r, sa);
+                else
+                    k_mg_resid<T, 2, 4><<<grid_, blk_, 0, st>>>(gg.n[0], gg.n[1], 1, mg.X[0], mg.B[0], r, sa);
+                count_launch();
+            }
         }
         EW_TRY(launch_dots<T>(r, r, N, 1, dpart, dres, st));
         double h = 0.0;
@@ -625,12 +863,7 @@ ew_status mg_collect_residuals(ew_grid* g, double a, const ew_mg_params* mp, int
         for (int c = 0; c < 3 && k < nsamples && s == EW_OK; ++c) {
             float* r = out + (size_t)k * N;
             const GridGeom& gg = g->geom;
-            dim3 grid_ = pt_grid(gg.n[0], gg.n[1], gg.n[2]), blk_(pt_threads(gg.n[0]));
-            if (gg.order == 2)
-                k_mg_resid<float, 3, 2><<<grid_, blk_, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
-            else
-                k_mg_resid<float, 3, 4><<<grid_, blk_, 0, st>>>(gg.n[0], gg.n[1], gg.n[2], mg.X[0], mg.B[0], r, sa);
-            count_launch();
+            mg.template plane3d<0>(gg, mg.X[0], mg.B[0], r, sa, 0.f, 0);
             ++k;
             s = mg.vcycle(0);
         }
