@@ -478,7 +478,9 @@ def measure_cube3d(ew, flush, pk, pk_kind, steps, warmup):
                 time_steps_per_step=info["Nt"], l2="flushed between timed steps (512 MB write)",
                 bound="hbm", kernel="k_step_tb3d<float, tuned depth>", bytes_per_launch=bytes_launch,
                 mean_launch_ms=mean, achieved=achieved, peak=float(pk["hbm_gbs"]), frac=achieved / float(pk["hbm_gbs"]),
-                peak_source=pk_kind, share_of_step_time=prof["fused_ms"] / max(ms, 1e-9))
+                peak_source=pk_kind,
+                # the profile covers the warm-up wave-solves too (each has the same launches)
+                share_of_step_time=prof["fused_ms"] * steps / (steps + warmup) / max(ms, 1e-9))
 
 
 def box_closed_form_near(n, length, order, omega, width):

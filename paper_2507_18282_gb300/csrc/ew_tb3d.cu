@@ -34,6 +34,7 @@
 
 #include "ew_bc_dev.cuh"
 #include "ew_internal.h"
+#include "ew_tb2d_dev.cuh"  // p_add, p_mul, p_fma, s_add
 
 namespace ew {
 
@@ -167,6 +168,165 @@ __global__ void __launch_bounds__(kT3* kT3, 1)
     }
 }
 
+// FP32 form of the same march: 16 x 32 threads, each with two adjacent columns
+// of the 32 x 32 region, so every level's update runs in paired FP32
+// instructions (f32x2 multiply-add and add) and the shared-memory neighbours
+// come in 8-byte pairs: (x-2, x-1) and (x+2, x+3) beside the thread's own pair,
+// the rows above and below as pairs.  The operations of a level and their
+// order are those of the scalar kernel above, so both give the same values.
+// Measured reason: the scalar kernel issues an instruction on 80 % of the
+// cycles (ncu, 511^3), so it is bound by its instruction count, which pairing
+// roughly halves.
+template <int B, bool FULL>
+__global__ void __launch_bounds__(kT3* kT3 / 2, 1)
+    k_step_tb3d_f2(int nx, int ny, int nz, const float* __restrict__ Din, const float* __restrict__ Win,
+                   float* __restrict__ Dout, float* __restrict__ Wout, float* __restrict__ acc,
+                   const float* __restrict__ cw, int b, Stencil<float> st, int64_t fstride) {
+    constexpr int H = B, TO = kT3 - 2 * H;
+    extern __shared__ __align__(16) unsigned char smem_tb3d[];
+    float(*sP)[2][kT3 * kT3] = reinterpret_cast<float(*)[2][kT3 * kT3]>(smem_tb3d);
+    const int c = 2 * threadIdx.x, ty = threadIdx.y;  // columns c, c + 1 of the region, row ty
+    const int gxa = blockIdx.x * TO - H + c, gy = blockIdx.y * TO - H + ty;
+    const int64_t v = blockIdx.z;
+    const int64_t N = (int64_t)nx * ny * nz, plane = (int64_t)nx * ny;
+    Din += v * fstride;
+    Win += v * fstride;
+    Dout += v * fstride;
+    Wout += v * fstride;
+    acc += v * N;
+    // x/y extension of each column: source column and sign (0: a Dirichlet wall)
+    int sxa = 1, sxb = 1, sy = 1;
+    const int iy = ext_axis<int>(gy, ny, axis_bc(st.bc, 1), sy);
+    const int ixa = ext_axis<int>(gxa, nx, axis_bc(st.bc, 0), sxa);
+    const int ixb = ext_axis<int>(gxa + 1, nx, axis_bc(st.bc, 0), sxb);
+    const int sga = (ixa < 0 || iy < 0) ? 0 : sxa * sy, sgb = (ixb < 0 || iy < 0) ? 0 : sxb * sy;
+    const int64_t cola = sga ? (int64_t)iy * nx + ixa : 0, colb = sgb ? (int64_t)iy * nx + ixb : 0;
+    const bool rowown = ty >= H && ty < H + TO && gy < ny;
+    const bool owna = rowown && c >= H && c < H + TO && gxa < nx;
+    const bool ownb = rowown && c + 1 >= H && c + 1 < H + TO && gxa + 1 < nx;
+    const int64_t ocol = (int64_t)gy * nx + gxa;  // column a's point of a plane (b: + 1)
+    // neighbour pairs inside the region (clamped at its edge: those values are wrong but stay in the rim)
+    const int me = ty * kT3 + c;
+    const int nxm = ty * kT3 + max(c - 2, 0), nxp = ty * kT3 + min(c + 2, kT3 - 2);
+    const int nym = max(ty - 1, 0) * kT3 + c, nyp = min(ty + 1, kT3 - 1) * kT3 + c;
+
+    constexpr int kPF = 4;
+    float2 pw[kPF], pd[kPF], pa[kPF], sg[kPF];
+    auto issue = [&](int z, float2& w, float2& d, float2& a, float2& sgn) {
+        int szz = 1, iz = z;
+        if (z < 0 || z >= nz) iz = ext_axis<int>(z, nz, axis_bc(st.bc, 2), szz);
+        const bool zl = iz >= 0 && z < nz + B;
+        const int64_t zb = (int64_t)(zl ? iz : 0) * plane;
+        const bool la = zl && sga != 0, lb = zl && sgb != 0;
+        w = make_float2(0.f, 0.f);
+        d = make_float2(0.f, 0.f);
+        a = make_float2(0.f, 0.f);
+        if (la) {
+            w.x = Win[zb + cola];
+            d.x = Din[zb + cola];
+        }
+        if (lb) {
+            w.y = Win[zb + colb];
+            d.y = Din[zb + colb];
+        }
+        if (z >= 0 && z < nz) {
+            const int64_t q = (int64_t)z * plane + ocol;
+            if (owna) a.x = acc[q];
+            if (ownb) a.y = acc[q + 1];
+        }
+        sgn = make_float2(la ? (float)(sga * szz) : 0.f, lb ? (float)(sgb * szz) : 0.f);
+    };
+#pragma unroll
+    for (int q = 0; q < kPF; ++q) issue(-B + q, pw[q], pd[q], pa[q], sg[q]);
+
+    float2 Wq[B + 1][3];
+    float2 Dq[B + 1];
+    float2 accq[B];
+    float2 cwr[B];
+#pragma unroll
+    for (int k = 0; k <= B; ++k) {
+        Wq[k][0] = Wq[k][1] = Wq[k][2] = make_float2(0.f, 0.f);
+        Dq[k] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+        accq[j] = make_float2(0.f, 0.f);
+        const float w = (FULL || j < b) ? cw[j] : 0.f;
+        cwr[j] = make_float2(w, w);
+    }
+    const float2 C0 = make_float2(st.c0, st.c0), C1X = make_float2(st.c1[0], st.c1[0]);
+    const float2 C1Y = make_float2(st.c1[1], st.c1[1]), C1Z = make_float2(st.c1[2], st.c1[2]);
+    const int nb = FULL ? B : b;
+
+    for (int zb = -B; zb < nz + B; zb += kPF) {
+#pragma unroll
+        for (int j = 0; j < kPF; ++j) {
+            const int z = zb + j;
+            if (z >= nz + B) break;
+            const int buf = z & 1, obuf = buf ^ 1;
+            const float2 w0 = p_mul(sg[j], pw[j]), d0 = p_mul(sg[j], pd[j]), a0 = pa[j];
+            issue(z + kPF, pw[j], pd[j], pa[j], sg[j]);
+            *reinterpret_cast<float2*>(&sP[0][buf][me]) = w0;
+            float2 dnext = d0;
+            float2 wnext = w0;
+#pragma unroll
+            for (int k = 1; k <= B; ++k) {
+                if (!FULL && k > nb) break;
+                Wq[k][0] = Wq[k][1];
+                Wq[k][1] = Wq[k][2];
+                Wq[k][2] = wnext;
+                const float* sq = sP[k - 1][obuf];
+                const float2 u = Wq[k][1];
+                const float2 L = *reinterpret_cast<const float2*>(sq + nxm);  // columns c - 2, c - 1
+                const float2 Q = *reinterpret_cast<const float2*>(sq + nxp);  // columns c + 2, c + 3
+                const float2 YM = *reinterpret_cast<const float2*>(sq + nym);
+                const float2 YP = *reinterpret_cast<const float2*>(sq + nyp);
+                float2 sx1;
+                sx1.x = s_add(L.y, u.y);  // column c: (c - 1) + (c + 1)
+                sx1.y = s_add(u.x, Q.x);  // column c + 1: c + (c + 2)
+                float2 lap = p_mul(C0, u);
+                lap = p_fma(C1X, sx1, lap);
+                lap = p_fma(C1Y, p_add(YM, YP), lap);
+                lap = p_fma(C1Z, p_add(Wq[k][0], Wq[k][2]), lap);
+                const float2 d = p_add(Dq[k], lap);
+                const float2 wn = p_add(u, d);
+                Dq[k] = dnext;
+                accq[k - 1] = p_fma(cwr[k - 1], wn, accq[k - 1]);
+                if (k < nb) {
+                    *reinterpret_cast<float2*>(&sP[k][buf][me]) = wn;
+                    dnext = d;
+                    wnext = wn;
+                } else {
+                    const int p = z - k;
+                    if (p >= 0 && p < nz) {
+                        const int64_t gi = (int64_t)p * plane + ocol;
+                        if (owna) {
+                            Wout[gi] = wn.x;
+                            Dout[gi] = d.x;
+                        }
+                        if (ownb) {
+                            Wout[gi + 1] = wn.y;
+                            Dout[gi + 1] = d.y;
+                        }
+                    }
+                }
+            }
+            {
+                const int p = z - nb;
+                if (p >= 0 && p < nz) {
+                    const int64_t q = (int64_t)p * plane + ocol;
+                    if (owna) acc[q] = accq[nb - 1].x;
+                    if (ownb) acc[q + 1] = accq[nb - 1].y;
+                }
+#pragma unroll
+                for (int q = B - 1; q > 0; --q) accq[q] = accq[q - 1];
+                accq[0] = a0;
+            }
+            __syncthreads();
+        }
+    }
+}
+
 template <typename T, int B>
 static ew_status launch_tb3d(const GridGeom& g, const T* Din, const T* Win, T* Dout, T* Wout, T* acc, const T* cw,
                              int b, const Stencil<T>& s, int nvec, int64_t fstride, cudaStream_t st) {
@@ -174,17 +334,27 @@ static ew_status launch_tb3d(const GridGeom& g, const T* Din, const T* Win, T* D
     constexpr size_t smem = sizeof(T) * (size_t)B * 2 * kT3 * kT3;
     static bool attr = false;  // per instantiation (same value on every device)
     if (!attr) {
-        EW_CUDA_TRY(cudaFuncSetAttribute(k_step_tb3d<T, B, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-        EW_CUDA_TRY(cudaFuncSetAttribute(k_step_tb3d<T, B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
+        const auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        if constexpr (sizeof(T) == 4) {
+            EW_CUDA_TRY(cudaFuncSetAttribute(k_step_tb3d_f2<B, true>, A, (int)smem));
+            EW_CUDA_TRY(cudaFuncSetAttribute(k_step_tb3d_f2<B, false>, A, (int)smem));
+        } else {
+            EW_CUDA_TRY(cudaFuncSetAttribute(k_step_tb3d<T, B, true>, A, (int)smem));
+            EW_CUDA_TRY(cudaFuncSetAttribute(k_step_tb3d<T, B, false>, A, (int)smem));
+        }
         attr = true;
     }
     dim3 grid((unsigned)((g.n[0] + TO - 1) / TO), (unsigned)((g.n[1] + TO - 1) / TO), (unsigned)nvec);
     cudaEvent_t ev = fused_begin(st);
-    auto kern = b == B ? k_step_tb3d<T, B, true> : k_step_tb3d<T, B, false>;
-    kern<<<grid, dim3(kT3, kT3), smem, st>>>((int)g.n[0], (int)g.n[1], (int)g.n[2], Din, Win, Dout, Wout,
-                                                        acc, cw, b, s, fstride);
+    if constexpr (sizeof(T) == 4) {
+        auto kern = b == B ? k_step_tb3d_f2<B, true> : k_step_tb3d_f2<B, false>;
+        kern<<<grid, dim3(kT3 / 2, kT3), smem, st>>>((int)g.n[0], (int)g.n[1], (int)g.n[2], Din, Win, Dout, Wout,
+                                                     acc, cw, b, s, fstride);
+    } else {
+        auto kern = b == B ? k_step_tb3d<T, B, true> : k_step_tb3d<T, B, false>;
+        kern<<<grid, dim3(kT3, kT3), smem, st>>>((int)g.n[0], (int)g.n[1], (int)g.n[2], Din, Win, Dout, Wout,
+                                                 acc, cw, b, s, fstride);
+    }
     EW_CUDA_TRY(cudaGetLastError());
     fused_end(ev, st, g.N * nvec, g.N * nvec * b);
     return EW_OK;

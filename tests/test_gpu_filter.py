@@ -139,6 +139,19 @@ def test_fp64_3d_blocked_equals_simple(ew, tb):
     assert np.max(np.abs(a - b)) < 1e-13 * np.max(np.abs(b))
 
 
+@pytest.mark.parametrize("tb", [0, 2, 3, 4])
+def test_fp32_3d_blocked_equals_simple(ew, tb):
+    """FP32 3D temporal blocking (each thread two adjacent columns in paired
+    FP32 instructions) against one step per launch: the same operations per
+    point, two vectors, ragged tiles in x and y, odd x extents (column pairs
+    that straddle the box edge), the last launch shallower than the depth."""
+    n, L = (61, 51, 23), (1.0, 0.8, 0.4)
+    v, a, info = _run(ew, n, L, 2, "fp32", 30.0, Np=2, tb=tb, nvec=2)
+    _, b, _ = _run(ew, n, L, 2, "fp32", 30.0, Np=2, tb=1, nvec=2)
+    assert info["Nt"] % 4 != 0 or info["Nt"] % 3 != 0
+    assert np.max(np.abs(a - b)) <= 4 * info["Nt"] * EPS32 * np.max(np.abs(v))
+
+
 def test_multi_vector_block(ew):
     """nvec vectors in one call equal separate calls, bit for bit."""
     n, L = (150, 40), (1.0, 0.3)
