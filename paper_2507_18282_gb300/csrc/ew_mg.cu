@@ -10,16 +10,22 @@
 //               (coarse point I on fine point 2I + 1, h_c = 2 h)
 //   smoother    damped Jacobi x <- x + w (b - M x) / D with the constant
 //               interior diagonal D = 1 + a sum_i d0 / h_i^2 (d0 = 2 or 5/2),
-//               or the learned correction x <- x + N(b - M x) on the finest
-//               `learned_levels` levels (ew_smoother.cu)
+//               or multi-colour Gauss-Seidel with the same diagonal (two
+//               colours at second order, three at fourth), or the learned
+//               correction x <- x + N(b - M x) on the finest `learned_levels`
+//               levels (ew_smoother.cu, applied as its composed stencil in
+//               FP32, ew_smoother_comp.cu)
 //   restriction full weighting, tensor product of (1/4, 1/2, 1/4)
 //   prolongation (multi)linear interpolation, zero on the boundary
 //   coarsest    conjugate gradients in one CTA (M is SPD)
 //
 // Implicit wave-solve (one application of S):
 //   M W^1 = W^0;  M y = 2 W^n, W^{n+1} = y - W^{n-1};  V_out = sum c_n W^n
-// Each system gets `max_cycles` V-cycles from the initial guess y = 2 W^n
-// (W^1 = W^0 for the first step).
+// Each system gets `max_cycles` V-cycles (or stops at `rtol`) from the
+// initial guess y = 2 W^n (W^1 = W^0 for the first step) or, with
+// guess = 1, from the previous system's solution.
+// Kernels: 3D levels run their stencil operations 2.5D blocked
+// (k_mg_plane3d), 2D levels one thread per point.
 #include <math.h>
 #include <stdlib.h>
 
@@ -110,14 +116,14 @@ __device__ __forceinline__ int mg_colour(int64_t i, int64_t j, int64_t k) {
     return ORDER == 2 ? (int)((i + j + k) & 1) : (int)((i + j + k) % 3);
 }
 
-template <typename T, int DIM, int ORDER>
-__global__ void k_mg_rbgs(int64_t nx, int64_t ny, int64_t nz, T* __restrict__ x, const T* __restrict__ b,
-                          Stencil<T> sa, T inv_d, int colour) {
+template <typename T, int ORDER>
+__global__ void k_mg_rbgs(int64_t nx, int64_t ny, T* __restrict__ x, const T* __restrict__ b, Stencil<T> sa, T inv_d,
+                          int colour) {  // 2D levels (3D: k_mg_plane3d, MODE 2)
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nx) return;
-    const int64_t j = blockIdx.y, k = blockIdx.z, q = (k * ny + j) * nx + i;
-    if (mg_colour<ORDER>(i, j, k) != colour) return;
-    const T r = (b[q] - x[q]) + lap_global<T, DIM, ORDER>(x, sa, q, i, j, k, nx, ny, nz);
+    const int64_t j = blockIdx.y, q = j * nx + i;
+    if (mg_colour<ORDER>(i, j, 0) != colour) return;
+    const T r = (b[q] - x[q]) + lap_global<T, 2, ORDER>(x, sa, q, i, j, 0, nx, ny, 1);
     x[q] = x[q] + inv_d * r;
 }
 
@@ -529,15 +535,15 @@ struct MGSolver {
         return 1.0 + a * s;
     }
 
-#define EW_MG_DISPATCH(KERN, GEOM, ...)                                                                  \
+// 2D levels: one thread per point (3D levels go through k_mg_plane3d)
+#define EW_MG_DISPATCH2D(KERN, GEOM, ...)                                                                \
     do {                                                                                                 \
         const GridGeom& g_ = (GEOM);                                                                     \
-        const int nz_ = g_.dim == 3 ? (int)g_.n[2] : 1;                                                 \
-        dim3 grid_ = pt_grid(g_.n[0], g_.n[1], nz_), blk_(pt_threads(g_.n[0]));                          \
-        if (g_.dim == 2 && g_.order == 2) KERN<T, 2, 2><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], 1, __VA_ARGS__); \
-        else if (g_.dim == 2) KERN<T, 2, 4><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], 1, __VA_ARGS__);             \
-        else if (g_.order == 2) KERN<T, 3, 2><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], g_.n[2], __VA_ARGS__);     \
-        else KERN<T, 3, 4><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], g_.n[2], __VA_ARGS__);                        \
+        dim3 grid_ = pt_grid(g_.n[0], g_.n[1], 1), blk_(pt_threads(g_.n[0]));                            \
+        if (g_.order == 2)                                                                               \
+            KERN<T, 2, 2><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], 1, __VA_ARGS__);                     \
+        else                                                                                             \
+            KERN<T, 2, 4><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], 1, __VA_ARGS__);                     \
         count_launch();                                                                                  \
     } while (0)
 
@@ -563,7 +569,7 @@ struct MGSolver {
         if (lv[L].dim == 3)
             plane3d<0>(lv[L], X[L], B[L], R[L], sa, T(0), 0);
         else
-            EW_MG_DISPATCH(k_mg_resid, lv[L], X[L], B[L], R[L], sa);
+            EW_MG_DISPATCH2D(k_mg_resid, lv[L], X[L], B[L], R[L], sa);
     }
 
     ew_status smooth(int L, int steps) {
@@ -582,33 +588,24 @@ struct MGSolver {
                 // M_ii = 1 - c0 of the stored (consistent) stencil of a L_h
                 const T inv_d = (T)(1.0 / (1.0 - (double)sa.c0));
                 const GridGeom& g_ = lv[L];
-                const int nz_ = g_.dim == 3 ? (int)g_.n[2] : 1;
-                dim3 grid_ = pt_grid(g_.n[0], g_.n[1], nz_), blk_(pt_threads(g_.n[0]));
+                dim3 grid_ = pt_grid(g_.n[0], g_.n[1], 1), blk_(pt_threads(g_.n[0]));
                 const int ncol = g_.order == 2 ? 2 : 3;
                 for (int colour = 0; colour < ncol; ++colour) {
-                    const int64_t nz3 = g_.dim == 3 ? g_.n[2] : 1;
-                    if (g_.dim == 3) {
+                    // one launch per colour: 3D levels the 2.5D kernel, 2D levels one thread per point
+                    if (g_.dim == 3)
                         plane3d<2>(g_, X[L], B[L], X[L], sa, inv_d, colour);
-                        continue;
-                    }
-                    if (g_.dim == 2 && g_.order == 2)
-                        k_mg_rbgs<T, 2, 2><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], 1, X[L], B[L], sa, inv_d, colour);
-                    else if (g_.dim == 2)
-                        k_mg_rbgs<T, 2, 4><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], 1, X[L], B[L], sa, inv_d, colour);
                     else if (g_.order == 2)
-                        k_mg_rbgs<T, 3, 2><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], nz3, X[L], B[L], sa, inv_d,
-                                                                  colour);
+                        k_mg_rbgs<T, 2><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], X[L], B[L], sa, inv_d, colour);
                     else
-                        k_mg_rbgs<T, 3, 4><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], nz3, X[L], B[L], sa, inv_d,
-                                                                  colour);
-                    count_launch();
+                        k_mg_rbgs<T, 4><<<grid_, blk_, 0, st>>>(g_.n[0], g_.n[1], X[L], B[L], sa, inv_d, colour);
+                    if (g_.dim == 2) count_launch();
                 }
             } else {
                 T wd = (T)(wJ / diag(L));
                 if (lv[L].dim == 3)
                     plane3d<1>(lv[L], X[L], B[L], Tm[L], sa, wd, 0);
                 else
-                    EW_MG_DISPATCH(k_mg_jacobi, lv[L], X[L], B[L], Tm[L], sa, wd);
+                    EW_MG_DISPATCH2D(k_mg_jacobi, lv[L], X[L], B[L], Tm[L], sa, wd);
                 std::swap(X[L], Tm[L]);
             }
         }

@@ -1,9 +1,16 @@
-// ew_reduce.cu -- FP64-accumulated reductions over active-point vectors
-// (inner products of the power iteration and the Rayleigh quotient, max-norm
-// residuals).  Two passes with a fixed block count, so every result is
-// deterministic: pass 1 reduces a grid-stride slice per block (warp shuffles,
-// then shared memory), pass 2 sums the per-block partials in block order.
+// ew_reduce.cu -- reductions over active-point vectors (inner products of the
+// power iteration, the Rayleigh quotient and the multigrid residual test,
+// max-norm residuals).  Two passes with a fixed block count, so every result
+// is deterministic: pass 1 reduces a grid-stride slice per block (warp
+// shuffles, then shared memory), pass 2 sums the per-block partials in block
+// order.  A thread's own slice accumulates in FP64 for FP64 vectors and, for
+// FP32 vectors, in a pair of FP32 numbers (each product split exactly into
+// two FP32 numbers, the running sum's rounding errors gathered in the second:
+// about 48 significant bits, on the FP32 units, where FP64 accumulation of
+// FP32 data is bound by this part's FP64 rate); the partials are summed in
+// FP64.
 #include "ew_bc_dev.cuh"
+#include "ew_dd.cuh"
 #include "ew_internal.h"
 
 namespace ew {
@@ -41,8 +48,20 @@ __global__ void __launch_bounds__(256) k_dots(const T* __restrict__ x, const T* 
     x += j * N;
     y += j * N;
     double s = 0.0;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
-        s += (double)x[q] * (double)y[q];
+    if constexpr (sizeof(T) == 4) {
+        float hi = 0.f, lo = 0.f;
+        for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
+            float p, pe, t, te;
+            two_prod(x[q], y[q], p, pe);  // x y = p + pe exactly
+            two_sum(hi, p, t, te);        // hi + p = t + te exactly
+            hi = t;
+            lo = EW_DD_ADD(lo, EW_DD_ADD(te, pe));
+        }
+        s = (double)hi + (double)lo;
+    } else {
+        for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
+            s += (double)x[q] * (double)y[q];
+    }
     s = block_reduce<false>(s, sh);
     if (threadIdx.x == 0) part[j * gridDim.x + blockIdx.x] = s;
 }
