@@ -26,7 +26,8 @@
 // (ew_bc_dev.cuh).
 //
 // Kernels:
-//   k_first_step      : a3, writes D^1, W^1 and V_out = c_0 W^0 + c_1 W^1.
+//   k_first_step      : a3, writes D^1, W^1 and V_out = c_0 W^0 + c_1 W^1
+//                       (3D; k_first_step2d: the same, tiled in shared memory).
 //   k_step_simple     : one time step per launch (any dim), reads W^n and its
 //                       neighbours from global memory, updates D in place,
 //                       writes W^{n+1} to a second W buffer and
@@ -138,6 +139,63 @@ __global__ void k_first_step(int64_t nx, int64_t ny, int64_t nz, const T* __rest
     D1[qf] = d;
     W1[qf] = w1;
     vout[q] = c0 * x + c1 * w1;
+}
+
+// The same first step on 2D grids, tiled: a CTA stages its 32 x 32 outputs
+// and a halo of ORDER / 2 (with the box closure) in shared memory once,
+// so each value of V is read from memory about once instead of once per
+// stencil point; 32 x 8 threads, four rows each.  The Laplacian sums its
+// terms in the order of lap_global.
+constexpr int kFsTX = 32, kFsTY = 32;
+
+template <typename T, int ORDER>
+__global__ void __launch_bounds__(256)
+    k_first_step2d(int nx, int ny, const T* __restrict__ vin, T* __restrict__ D1, T* __restrict__ W1,
+                   T* __restrict__ vout, Stencil<T> s, T c0, T c1, int64_t fstride, int64_t fpitch) {
+    constexpr int R = ORDER / 2, SX = kFsTX + 2 * R, SY = kFsTY + 2 * R;
+    __shared__ __align__(16) unsigned char sv_raw[sizeof(T) * SY * SX];  // raw: T may be a pair type
+    T* sv = reinterpret_cast<T*>(sv_raw);
+    const int64_t N = (int64_t)nx * ny, v = blockIdx.z;
+    vin += v * N;
+    vout += v * N;
+    D1 += v * fstride;
+    W1 += v * fstride;
+    const int x0 = blockIdx.x * kFsTX, y0 = blockIdx.y * kFsTY;
+    const int cbx = axis_bc(s.bc, 0), cby = axis_bc(s.bc, 1);
+    const int tid = threadIdx.y * kFsTX + threadIdx.x;
+    for (int c = tid; c < SX * SY; c += 256) {
+        const int sy = c / SX, sx = c - sy * SX;
+        const int gx = x0 - R + sx, gy = y0 - R + sy;
+        int sgx = 1, sgy = 1;
+        const int ix = (gx >= 0 && gx < nx) ? gx : ext_axis<int>(gx, nx, cbx, sgx);
+        const int iy = (gy >= 0 && gy < ny) ? gy : ext_axis<int>(gy, ny, cby, sgy);
+        T val = T(0);
+        if (ix >= 0 && iy >= 0) {
+            val = vin[(int64_t)iy * nx + ix];
+            if (sgx * sgy < 0) val = -val;
+        }
+        sv[c] = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kFsTY / 8; ++r) {
+        const int yy = threadIdx.y + 8 * r, gx = x0 + threadIdx.x, gy = y0 + yy;
+        if (gx >= nx || gy >= ny) continue;
+        const int q = (yy + R) * SX + threadIdx.x + R;
+        const T x = sv[q];
+        T d = s.c0 * x;
+        d += s.c1[0] * (sv[q - 1] + sv[q + 1]);
+        d += s.c1[1] * (sv[q - SX] + sv[q + SX]);
+        if (ORDER == 4) {
+            d += s.c2[0] * (sv[q - 2] + sv[q + 2]);
+            d += s.c2[1] * (sv[q - 2 * SX] + sv[q + 2 * SX]);
+        }
+        const T w1 = x + d;
+        const int64_t qf = (int64_t)gy * fpitch + gx;
+        D1[qf] = d;
+        W1[qf] = w1;
+        vout[(int64_t)gy * nx + gx] = c0 * x + c1 * w1;
+    }
 }
 
 // one step: D <- D + dt^2 L W (in place), Wout <- W + D, acc += c Wout
@@ -329,11 +387,16 @@ ew_status first_step(const GridGeom& g, const T* vin, T* D1, T* W1, T* vout,
     EW_TRY(pt_check(g, nvec));
     dim3 grid = pt_grid(g, nvec), blk(pt_threads(g.n[0]));
     T c0 = T(plan.cn(0)), c1 = T(plan.cn(1));
-    if (g.dim == 2 && g.order == 2)
-        k_first_step<T, 2, 2><<<grid, blk, 0, st>>>(g.n[0], g.n[1], 1, vin, D1, W1, vout, s, c0, c1, fstride, fpitch);
-    else if (g.dim == 2)
-        k_first_step<T, 2, 4><<<grid, blk, 0, st>>>(g.n[0], g.n[1], 1, vin, D1, W1, vout, s, c0, c1, fstride, fpitch);
-    else if (g.order == 2)
+    if (g.dim == 2) {
+        const dim3 g2((unsigned)((g.n[0] + kFsTX - 1) / kFsTX), (unsigned)((g.n[1] + kFsTY - 1) / kFsTY),
+                      (unsigned)nvec);
+        if (g.order == 2)
+            k_first_step2d<T, 2><<<g2, dim3(kFsTX, 8), 0, st>>>((int)g.n[0], (int)g.n[1], vin, D1, W1, vout, s, c0,
+                                                                c1, fstride, fpitch);
+        else
+            k_first_step2d<T, 4><<<g2, dim3(kFsTX, 8), 0, st>>>((int)g.n[0], (int)g.n[1], vin, D1, W1, vout, s, c0,
+                                                                c1, fstride, fpitch);
+    } else if (g.order == 2)
         k_first_step<T, 3, 2><<<grid, blk, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, D1, W1, vout, s, c0, c1, fstride, fpitch);
     else
         k_first_step<T, 3, 4><<<grid, blk, 0, st>>>(g.n[0], g.n[1], g.n[2], vin, D1, W1, vout, s, c0, c1, fstride, fpitch);
