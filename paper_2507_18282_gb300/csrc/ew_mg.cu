@@ -336,21 +336,25 @@ __global__ void k_mg_prolong(int64_t fx, int64_t fy, int64_t fz, int64_t cx, int
         const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
         if (i >= fx) return;
         const int64_t j = blockIdx.y, k = blockIdx.z, q = (k * fy + j) * fx + i;
-        int64_t ci[2], cj[2], ck[2];
-        T wi[2], wj[2], wk[2];
-        int ni, nj, nk;
-        if (i & 1) { ci[0] = (i - 1) / 2; wi[0] = T(1); ni = 1; }
-        else { ci[0] = i / 2 - 1; ci[1] = i / 2; wi[0] = wi[1] = T(0.5); ni = 2; }
-        if (j & 1) { cj[0] = (j - 1) / 2; wj[0] = T(1); nj = 1; }
-        else { cj[0] = j / 2 - 1; cj[1] = j / 2; wj[0] = wj[1] = T(0.5); nj = 2; }
-        if (DIM == 2) { ck[0] = 0; wk[0] = T(1); nk = 1; }
-        else if (k & 1) { ck[0] = (k - 1) / 2; wk[0] = T(1); nk = 1; }
-        else { ck[0] = k / 2 - 1; ck[1] = k / 2; wk[0] = wk[1] = T(0.5); nk = 2; }
+        // per axis the coarse neighbours c, c + 1 and their weights: an odd fine index lies on
+        // coarse point (i - 1) / 2 (weight 1, the second weight 0), an even one between two
+        // (1/2 each); fixed trip counts keep everything in registers, and skipping the zero
+        // weights leaves the same terms in the same order
+        const int64_t ci = (i & 1) ? (i - 1) / 2 : i / 2 - 1;
+        const int64_t cj = (j & 1) ? (j - 1) / 2 : j / 2 - 1;
+        const int64_t ck = DIM == 2 ? 0 : ((k & 1) ? (k - 1) / 2 : k / 2 - 1);
+        const T wi[2] = {(i & 1) ? T(1) : T(0.5), (i & 1) ? T(0) : T(0.5)};
+        const T wj[2] = {(j & 1) ? T(1) : T(0.5), (j & 1) ? T(0) : T(0.5)};
+        const T wk[2] = {(DIM == 2 || (k & 1)) ? T(1) : T(0.5), (DIM == 2 || (k & 1)) ? T(0) : T(0.5)};
         T s = T(0);
-        for (int c3 = 0; c3 < nk; ++c3)
-            for (int c2 = 0; c2 < nj; ++c2)
-                for (int c1 = 0; c1 < ni; ++c1)
-                    s += wi[c1] * wj[c2] * wk[c3] * get0(ec, ci[c1], cj[c2], ck[c3], cx, cy, cz);
+#pragma unroll
+        for (int c3 = 0; c3 < (DIM == 3 ? 2 : 1); ++c3)
+#pragma unroll
+            for (int c2 = 0; c2 < 2; ++c2)
+#pragma unroll
+                for (int c1 = 0; c1 < 2; ++c1)
+                    if (wi[c1] != T(0) && wj[c2] != T(0) && wk[c3] != T(0))
+                        s += wi[c1] * wj[c2] * wk[c3] * get0(ec, ci + c1, cj + c2, ck + c3, cx, cy, cz);
         xf[q] += s;
     }
 }
