@@ -102,3 +102,32 @@ def test_batched_uneven_boxes_workload(ew):
     err = np.linalg.norm(y.cpu().double().numpy() - beta * phi) / np.linalg.norm(phi)
     assert err < 4 * info["Nt"] * np.finfo(np.float32).eps
     g.close()
+
+
+def test_batched_fp32_large_box_runs_alone_same_bits(ew):
+    """In FP32 a problem whose points x vectors fill the GPU three times over
+    with 116 x 88 tiles runs alone inside the batched call (the tuned
+    single-problem kernel) while the others share the batched launch; every
+    problem's result equals its own ew_filter_apply call bit for bit."""
+    props = torch.cuda.get_device_properties(0)
+    big = 3 * props.multi_processor_count * 116 * 88
+    probs = [((2047, 1535), (1.0, 0.75), 20.0, 2), ((300, 170), (1.0, 0.6), 35.0, 1),
+             ((511, 383), (1.2, 0.9), 50.0, 3)]
+    assert probs[0][0][0] * probs[0][0][1] * probs[0][3] >= big
+    assert all(n[0] * n[1] * k < big for n, _, _, k in probs[1:])
+    grids, params, vin, vout = [], [], [], []
+    for q, (n, L, w, k) in enumerate(probs):
+        g = ew.ew_grid_create(2, n, L, order=4, prec="fp32")
+        grids.append(g)
+        params.append(ew.filter_params(w))
+        vin.append(torch.tensor(ew_inputs.uniform_pm1(200 + q, g.size * k), dtype=torch.float32, device="cuda"))
+        vout.append(torch.full_like(vin[-1], float("nan")))
+    ew.ew_filter_apply_batched(grids, params, vin, vout, nvec=[k for *_, k in probs])
+    torch.cuda.synchronize()
+    for q, (_, _, _, k) in enumerate(probs):
+        out = torch.empty_like(vin[q])
+        ew.ew_filter_apply(grids[q], params[q], vin[q], out, nvec=k)
+        torch.cuda.synchronize()
+        assert torch.equal(out, vout[q]), q
+    for g in grids:
+        g.close()
