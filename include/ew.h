@@ -235,6 +235,26 @@ ew_status ew_choose_num_periods(const ew_grid* grid, const ew_filter_params* par
 ew_status ew_filter_apply(const ew_grid* grid, const ew_filter_params* params, const void* v_in_dev,
                           void* v_out_dev, int nvec, cudaStream_t stream);
 
+/* v_out = S v_in for nvec vectors held in HOST memory: the wave-solve of
+ * ew_filter_apply (Algorithm matVec) with the copies to and from the device
+ * overlapped with the filter applications.  The vectors are cut into chunks of
+ * `chunk` vectors (0: at least four a chunk, at most four chunks); chunk k is
+ * copied in on a copy stream while chunk k - 1 is filtered on `stream` and
+ * chunk k - 2 is copied out on a second copy stream.  The results equal those
+ * of ew_filter_apply on the same vectors bit for bit.
+ *   v_in_host, v_out_host  nvec vectors each, the layout of ew_filter_apply, in
+ *                          the grid precision (FP64 for EW_FP32X2 grids); they
+ *                          must not overlap (EW_EINVAL).  Page-locked (pinned)
+ *                          memory lets the copies overlap; pageable memory works
+ *                          but its copies do not run asynchronously.
+ * Stream-ordered like cudaMemcpyAsync: the call returns once the work is
+ * queued; work queued on `stream` afterwards sees the outputs, and the host may
+ * read v_out_host after synchronising `stream`.  Device buffers of 4 x chunk
+ * vectors are allocated on first use and kept with the grid; calls on one grid
+ * must not overlap.  EW_EINVAL for chunk < 0 or nvec outside [1, 65535]. */
+ew_status ew_filter_apply_host(const ew_grid* grid, const ew_filter_params* params, const void* v_in_host,
+                               void* v_out_host, int nvec, int chunk, cudaStream_t stream);
+
 /* v_out[q] = S_q v_in[q] for nprob independent problems (each with its own
  * grid and filter parameters: uneven boxes, their own omega, time step and
  * N_t).  nvec (may be NULL = all 1) gives the vectors per problem; v_in[q]

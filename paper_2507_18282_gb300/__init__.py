@@ -174,6 +174,31 @@ def ew_filter_apply(grid: Grid, params, v_in, v_out, nvec=None, stream=None):
     return v_out
 
 
+def _host_ptr(t, dtype, numel):
+    """Data pointer of a contiguous CPU torch tensor (pinned for overlapped copies)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("expected a CPU (host) torch tensor")
+    if t.dtype != dtype:
+        raise TypeError("expected dtype %s, got %s" % (dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if t.numel() < numel:
+        raise ValueError("tensor holds %d elements, need %d" % (t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def ew_filter_apply_host(grid: Grid, params, h_in, h_out, nvec=None, chunk=0, stream=None):
+    """v_out = S v_in for vectors in host memory (CPU tensors, ideally pinned),
+    copies overlapped with the wave-solves; stream-ordered: synchronise the
+    stream before reading h_out."""
+    nvec = nvec if nvec is not None else max(1, h_in.numel() // grid.size)
+    a = _host_ptr(h_in, grid.dtype, nvec * grid.size)
+    b = _host_ptr(h_out, grid.dtype, nvec * grid.size)
+    check(lib.ew_filter_apply_host(grid.handle, ctypes.byref(params), a, b, int(nvec), int(chunk), _stream(stream)))
+    return h_out
+
+
 def ew_filter_apply_batched(grids, params, v_in, v_out, nvec=None, stream=None):
     """v_out[q] = S_q v_in[q] for every problem q in one graph-captured launch sequence."""
     n = len(grids)

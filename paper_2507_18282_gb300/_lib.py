@@ -108,6 +108,7 @@ lib.ew_grid_destroy.argtypes = [_vp]
 lib.ew_grid_destroy.restype = None
 lib.ew_filter_setup.argtypes = [_vp, ctypes.POINTER(ew_filter_params), ctypes.POINTER(ew_filter_info), _dp, _i64]
 lib.ew_filter_apply.argtypes = [_vp, ctypes.POINTER(ew_filter_params), _vp, _vp, _i, _vp]
+lib.ew_filter_apply_host.argtypes = [_vp, ctypes.POINTER(ew_filter_params), _vp, _vp, _i, _i, _vp]
 lib.ew_choose_num_periods.argtypes = [_vp, ctypes.POINTER(ew_filter_params), _i, _i, _i, _ip, _dp]
 lib.ew_apply_L.argtypes = [_vp, _vp, _vp, _i, _vp]
 lib.ew_rayleigh.argtypes = [_vp, _vp, _i, _dp, _dp, _vp]
@@ -132,7 +133,7 @@ lib.ew_smoother_forward.argtypes = [_vp, _vp, _vp, _vp, _vp]
 lib.ew_smoother_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
 lib.ew_smoother_train.argtypes = [_vp, _d, ctypes.POINTER(ew_train_params), _vp, ctypes.POINTER(ew_train_report),
                                   _vp]
-for _name in ["ew_grid_create", "ew_grid_create_mapped", "ew_filter_setup", "ew_choose_num_periods", "ew_filter_apply", "ew_apply_L", "ew_rayleigh",
+for _name in ["ew_grid_create", "ew_grid_create_mapped", "ew_filter_setup", "ew_choose_num_periods", "ew_filter_apply", "ew_filter_apply_host", "ew_apply_L", "ew_rayleigh",
               "ew_power_iteration", "ew_profile_enable", "ew_profile_read", "ew_arnoldi_eigs",
               "ew_implicit_step_mg", "ew_smoother_forward", "ew_smoother_backward", "ew_smoother_train"]:
     getattr(lib, _name).restype = ctypes.c_int

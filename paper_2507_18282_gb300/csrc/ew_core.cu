@@ -190,7 +190,7 @@ ew_status plan_filter(const GridGeom& g, const ew_filter_params* p, FilterPlan* 
     return EW_OK;
 }
 
-static ew_status check_grid(const ew_grid* g) {
+ew_status check_grid(const ew_grid* g) {
     if (!g) return set_error(EW_EINVAL, "grid is NULL");
     int dev = -1;
     EW_CUDA_TRY(cudaGetDevice(&dev));
@@ -200,7 +200,7 @@ static ew_status check_grid(const ew_grid* g) {
     return EW_OK;
 }
 
-static size_t elem_size(const ew_grid* g) { return g->prec == EW_FP32 ? 4 : 8; }
+size_t elem_size(const ew_grid* g) { return g->prec == EW_FP32 ? 4 : 8; }
 
 static ew_status pinned(ew_grid* g, size_t bytes, void** out) {
     if (g->host_pinned_bytes < bytes) {
@@ -397,6 +397,7 @@ void ew_grid_destroy(ew_grid* g) {
     g->mg.release();
     g->pairs.release();
     g->mgh.release();
+    g->hostio.release();
     if (g->host_pinned) cudaFreeHost(g->host_pinned);
     delete g;
 }

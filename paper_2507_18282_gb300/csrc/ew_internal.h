@@ -166,6 +166,7 @@ struct ew_grid {
     ew::Scratch mg;        // power-iteration iterate
     ew::Scratch mgh;       // multigrid hierarchy
     ew::Scratch pairs;     // EW_FP32X2 grids: the input and output vectors as double-FP32 pairs
+    ew::Scratch hostio;    // ew_filter_apply_host: device buffers of two input and two output chunks
     void* host_pinned = nullptr;  // small pinned staging for reductions
     size_t host_pinned_bytes = 0;
 };
@@ -188,6 +189,9 @@ struct FilterPlan {
     }
 };
 ew_status plan_filter(const GridGeom& g, const ew_filter_params* p, FilterPlan* out, bool with_weights = true);
+// the grid is usable on the current device (binds it on first use); bytes of one vector element
+ew_status check_grid(const ew_grid* g);
+size_t elem_size(const ew_grid* g);
 
 // --- kernels launchers (ew_stencil.cu) ------------------------------------
 template <typename T>

@@ -213,6 +213,7 @@ calls = {
     "ew_grid_create_mapped": (None, None, 0, None),
     "ew_filter_setup": (None, None, None, None, 0),
     "ew_filter_apply": (None, None, None, None, 1, None),
+    "ew_filter_apply_host": (None, None, None, None, 1, 0, None),
     "ew_filter_apply_batched": (0, None, None, None, None, None, None),
     "ew_filter_apply_noalloc": (None, None, None, None, None),
     "ew_choose_num_periods": (None, None, 1, 2, 1, None, None),
@@ -239,7 +240,7 @@ print("ok", len(calls))
     import sys
     r = subprocess.run([sys.executable, "-c", script], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
-    assert r.stdout.strip() == "ok 18"
+    assert r.stdout.strip() == "ok 19"
 
 
 def test_header_is_plain_c(ew, tmp_path):

@@ -152,6 +152,33 @@ def test_fp32_3d_blocked_equals_simple(ew, tb):
     assert np.max(np.abs(a - b)) <= 4 * info["Nt"] * EPS32 * np.max(np.abs(v))
 
 
+@pytest.mark.parametrize("nvec,chunk,prec", [(16, 0, "fp32"), (5, 2, "fp32"), (7, 3, "fp64"), (2, 0, "fp32")])
+def test_host_buffers_equal_device_path(ew, nvec, chunk, prec):
+    """ew_filter_apply_host (vectors in host memory, chunked copies overlapped
+    with the wave-solves) gives the bits of ew_filter_apply on the same vectors,
+    from pinned and from pageable host buffers; a ragged last chunk."""
+    n, L = (300, 170), (1.0, 0.6)
+    g = ew.ew_grid_create(2, n, L, order=4, prec=prec)
+    p = ew.filter_params(35.0)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    v = torch.tensor(ew_inputs.uniform_pm1(31, g.size * nvec), dtype=dt)
+    h_in = v.pin_memory()
+    h_out = torch.full_like(v, float("nan")).pin_memory()
+    ew.ew_filter_apply_host(g, p, h_in, h_out, nvec=nvec, chunk=chunk)
+    torch.cuda.synchronize()
+    d_out = torch.empty(g.size * nvec, dtype=dt, device="cuda")
+    ew.ew_filter_apply(g, p, v.cuda(), d_out, nvec=nvec)
+    torch.cuda.synchronize()
+    assert torch.equal(h_out, d_out.cpu())
+    h_page = torch.full_like(v, float("nan"))
+    ew.ew_filter_apply_host(g, p, v, h_page, nvec=nvec, chunk=chunk)
+    torch.cuda.synchronize()
+    assert torch.equal(h_page, h_out)
+    with pytest.raises(ew.EWError, match="EW_EINVAL"):
+        ew.ew_filter_apply_host(g, p, h_in, h_out, nvec=nvec, chunk=-1)
+    g.close()
+
+
 def test_multi_vector_block(ew):
     """nvec vectors in one call equal separate calls, bit for bit."""
     n, L = (150, 40), (1.0, 0.3)
