@@ -81,7 +81,7 @@ def parse():
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-eigenpairs runs")
     ap.add_argument("--nvec", type=int, default=NVEC, help="vectors per wave-solve of the headline workload")
     ap.add_argument("--workload", choices=["rect2d", "cube3d", "batched", "batched_eigs", "implicit3d", "mg3d", "eigs2d",
-                                           "eigs3d", "scaling2d", "mgtol", "mapped2d", "sweeps2d"],
+                                           "eigs3d", "eigs3d_implicit", "scaling2d", "mgtol", "mapped2d", "sweeps2d"],
                     default="rect2d",
                     help="rect2d is the headline line; the others print their own line")
     ap.add_argument("--eigs-arm", choices=["pair_and_plain", "fp32_fp64", "fp32_pair", "plain"],
@@ -601,6 +601,64 @@ def measure_eigs3d(ew, num_periods):
                 wave_solve_share_of_time=prof["fused_ms"] / 1e3 / sec)
 
 
+def measure_eigs3d_implicit(ew, num_periods):
+    """The implicit order-4 cube workload with the learned smoother at half the
+    255^3 size: 127^3, omega = 40 (the 255^3 / omega = 80 case with both halved,
+    so the same points per wavelength), 10 implicit steps per period with the
+    adjusted omega, the 8 eigenpairs nearest omega, Krylov dimension 48, block 4,
+    CGS2 in FP64, FP32 wave-solves, N_p from the simultaneous-iteration
+    estimate.  Two arms: every implicit system solved by plain multigrid
+    (damped Jacobi V(2,2)) and by multigrid with the learned smoother on the
+    finest level (trained on the GPU first), each to a relative residual of
+    1e-5 from the previous system's solution.  Time, wave-solves, V-cycles per
+    system and each eigenvalue against the closed form, per arm."""
+    import numpy as np
+    import torch
+
+    import ew_inputs
+    m, w = 127, 40.0
+    g = ew.ew_grid_create(3, (m, m, m), (1.0, 1.0, 1.0), order=4, prec="fp32")
+    probe = ew.filter_params(w, num_periods=1, steps_per_period=10, scheme="implicit", adjust_omega=True,
+                             mg=ew.mg_params())
+    cr_est = None
+    if num_periods <= 0:
+        num_periods, cr = ew.ew_choose_num_periods(g, probe, 8, 48, max_periods=1024)
+        cr_est = float(cr[num_periods.bit_length() - 1])
+    info, _ = ew.ew_filter_setup(g, probe)
+    a = 0.5 * info["dt"] ** 2
+    wts = torch.tensor(ew_inputs.learned_init(36, 0.05), dtype=torch.float32, device="cuda")
+    t0 = time.time()
+    train = ew.ew_smoother_train(g, a, wts, steps=600, samples=12, lr=5e-3, seed=5)
+    train_s = time.time() - t0
+    exact = closed_form_cube(m, 4, w - 6.0, w + 6.0)
+    arms = {}
+    for name, learned in [("plain", 0), ("learned", 1 if train["accepted"] else 0)]:
+        mg = ew.mg_params(pre=2, post=2, max_cycles=40, rtol=1e-5, learned_levels=learned,
+                          weights=wts if learned else None, guess="previous")
+        p = ew.filter_params(w, num_periods=num_periods, steps_per_period=10, scheme="implicit", adjust_omega=True,
+                             mg=mg)
+        pinfo, _ = ew.ew_filter_setup(g, p)
+        e = ew.eigs_params(8, krylov_dim=48, block=4, seed=7, max_wave_solves=400, lock=True)
+        ew.ew_profile_enable(True)
+        torch.cuda.synchronize()
+        t1 = time.time()
+        lam, rep, st = ew.ew_arnoldi_eigs(g, p, e, allow_noconv=True)
+        torch.cuda.synchronize()
+        sec = time.time() - t1
+        prof = ew.ew_profile_read()
+        ew.ew_profile_enable(False)
+        err = [float(np.min(np.abs(exact - x)) / x) for x in lam]
+        arms[name] = dict(seconds=sec, status=int(st), learned_levels=learned, wave_solves=int(rep["wave_solves"]),
+                          converged=int(rep["n_converged"]), time_steps_per_wave_solve=pinfo["Nt"],
+                          mg_cycles_per_system=prof["mg_cycles"] / max(prof["mg_solves"], 1),
+                          lambda_=[float(x) for x in lam], rel_err_vs_closed_form=err, max_rel_err=max(err),
+                          eig_res_fp32=[float(x) for x in rep["eig_res"][:8]])
+    g.close()
+    return dict(workload="eigs_cube3d_127_order4_implicit_8_nearest_omega40", unit="s", num_periods=num_periods,
+                cr_estimate=cr_est, krylov_dim=48, block=4, mg_rtol=1e-5, train=train, train_seconds=train_s,
+                arms=arms, speedup_learned=arms["plain"]["seconds"] / max(arms["learned"]["seconds"], 1e-9))
+
+
 def measure_sweeps2d(ew):
     """The paper's two sweeps on square128 (127 x 127 unit square, order 2,
     implicit scheme with multigrid to 1e-10, FP64), against the box's closed
@@ -819,6 +877,8 @@ def run_extra(args):
         line = measure_sweeps2d(ew)
     elif w == "eigs3d":
         line = measure_eigs3d(ew, args.num_periods)
+    elif w == "eigs3d_implicit":
+        line = measure_eigs3d_implicit(ew, args.num_periods)
     elif w == "implicit3d":
         # 255^3 order 4 FP32, implicit scheme at 10 steps per period (omega = 80 adjusted): the learned
         # smoother trained on the GPU against plain Jacobi multigrid; its V-cycle factor, its cost per cycle
